@@ -1,0 +1,364 @@
+"""Benchmark: online IS-NMF frames/s at F=513, K=100 on GB300.
+
+Workload (the long-stream configuration): F=513, K=100, minibatch beta=1000,
+10 inner h iterations, fresh restarts, one pass over a seeded gamma-model
+stream generated on the device. One step = one onmf_push_frames call of
+1,000,000 frames (1000 minibatches) already resident in HBM; 10 steps are
+the full 10^7-frame pass. Inputs are larger than L2 (2.05 GB per step), so no
+L2 flush is needed between steps.
+
+Reported: frames/s of the mixed-precision path (value), the plain FP32 GPU
+path on the same workload, their objective agreement, the roofline of the
+step kernel, an end-to-end number through the C ABI with host buffers, the
+FP64 oracle on the host cores (cpu_baseline), SM clocks during the timed
+region, and our kernel launch count.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this build).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+F, K, BETA, N_IN = 513, 100, 1000, 10
+FLOP_PER_FRAME = (6 * N_IN + 6) * F * K  # algorithmic flops of one frame
+METRIC = "online IS-NMF frames/s (F=513,K=100)"
+WORKLOAD = "online IS-NMF long stream F=513 K=100 beta=1000 n_inner=10, 1e6 frames/step"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--frames-per-step", type=int, default=1_000_000)
+    p.add_argument("--skip-fp32", action="store_true")
+    p.add_argument("--skip-e2e", action="store_true")
+    p.add_argument("--skip-cpu", action="store_true")
+    p.add_argument("--cpu-sample-minibatches", type=int, default=6)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------- distributed
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world, backend):
+    import torch.distributed as dist
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29511")
+        dist.init_process_group(backend=backend)
+    return dist if world > 1 else None
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, x, device="cpu"):
+    """Max of a float over all ranks (x itself at world size 1)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, x, device="cpu"):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        import statistics
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- peaks
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# -------------------------------------------------------------- our arm
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1106_4198_gb300 as onmf
+    import synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = init_dist(world, "nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    fps = args.frames_per_step
+    seed = synth.DATA_SEED + 7919 * rank  # each rank: its own stream
+    Wstar = torch.as_tensor(synth.dictionary(F, K, seed), dtype=torch.float32,
+                            device=dev)
+    W0 = synth.init_dictionary(F, K)
+    # inputs resident in HBM before the timed region
+    chunks = [synth.device_frames(F, K, fps, seed=seed, chunk=c, Wstar=Wstar)
+              for c in range(args.steps)]
+    torch.cuda.synchronize()
+
+    def timed_pass(precision, record_launch_times=False):
+        m = onmf.OnlineISNMF(F, K, W0, stream=stream, beta=BETA, n_inner=N_IN,
+                             precision=precision)
+        for w in range(args.warmup):
+            m.push(chunks[w % len(chunks)])
+        m.sync()
+        zero = np.zeros((K, F))
+        m.set_state(W0, zero, zero, 0, 0.0)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        barrier(dist, local)
+        torch.cuda.synchronize()
+        l0 = onmf.onmf_kernel_launches()
+        with ClockSampler(local) as clk:
+            evs[0].record(stream)
+            for i in range(args.steps):
+                m.push(chunks[i])
+                evs[i + 1].record(stream)
+            torch.cuda.synchronize()
+        barrier(dist, local)
+        launches = onmf.onmf_kernel_launches() - l0
+        per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+        total_ms = evs[0].elapsed_time(evs[-1])
+        _, _, t, ls = m.stats()
+        m.close()
+        return dict(ms=total_ms, per_step_ms=per, launches=launches,
+                    frames=t, loss=ls / max(t, 1), clocks=clk.summary())
+
+    mixed = timed_pass(onmf.ONMF_MIXED)
+    fp32 = None if args.skip_fp32 else timed_pass(onmf.ONMF_FP32)
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.skip_e2e:
+        host = [torch.empty((fps, F), dtype=torch.float32, pin_memory=True)
+                for _ in range(2)]
+        host[0].copy_(chunks[0])
+        host[1].copy_(chunks[1 % len(chunks)])
+        m = onmf.OnlineISNMF(F, K, W0, stream=stream, beta=BETA, n_inner=N_IN,
+                             precision=onmf.ONMF_MIXED)
+        for w in range(args.warmup):
+            m.push(host[w % 2].numpy())
+        m.sync()
+        res = np.zeros(1)
+        barrier(dist, local)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            m.push(host[i % 2].numpy())
+            _, res[0] = onmf.onmf_get_stats(m.state)  # device->host read of the result
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(dist, time.perf_counter() - t0, dev)
+        m.close()
+        e2e = {"value": sum_over_ranks(dist, fps * args.steps, dev) / e2e_s,
+               "unit": "frames/s", "h2d_bytes_per_step": fps * F * 4,
+               "d2h_bytes_per_step": 8}
+        del host
+
+    ms = max_over_ranks(dist, mixed["ms"], dev)
+    total_frames = sum_over_ranks(dist, fps * args.steps, dev)
+    value = total_frames / (ms / 1e3)
+    out = None
+    if rank == 0:
+        peaks = measured_peaks()
+        launch_ms = sum(mixed["per_step_ms"]) / len(mixed["per_step_ms"])
+        achieved = FLOP_PER_FRAME * fps / (launch_ms / 1e3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "kernel": "online_kernel<mixed>",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"
+                if peaks else "fallback"}
+        out = {
+            "metric": METRIC, "value": value, "unit": "frames/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic gamma-model spectrogram generated on device",
+            "config": {"workload": WORKLOAD, "F": F, "K": K, "beta": BETA,
+                       "n_inner": N_IN, "frames_per_step": fps,
+                       "global_batch": fps * world,
+                       "l2": "inputs 2.05 GB/step > L2, no flush",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "fp32_value": (total_frames / (fp32["ms"] / 1e3)) if fp32 else None,
+            "speedup_vs_fp32": (fp32["ms"] / mixed["ms"]) if fp32 else None,
+            "objective": mixed["loss"],
+            "objective_fp32": fp32["loss"] if fp32 else None,
+            "objective_rel_diff": (abs(mixed["loss"] - fp32["loss"]) / fp32["loss"])
+            if fp32 else None,
+            "roofline": roof,
+            "e2e": e2e,
+            "gpu_launches": mixed["launches"],
+            "clocks": mixed["clocks"],
+        }
+    return out, dist
+
+
+# ----------------------------------------------------------- oracle (CPU)
+
+
+def cpu_oracle_rate(n_mb, threads):
+    """Frames/s of the FP64 oracle on a bounded sample of the workload."""
+    import numpy as np
+
+    import oracle
+    import synth
+    V = synth.spectrogram(F, K, n_mb * BETA)
+    W0 = synth.init_dictionary(F, K)
+    oracle.set_threads(threads)
+    t0 = time.perf_counter()
+    oracle.online_pass(V, W0, beta=BETA, n_in=N_IN, want_H=False)
+    dt = time.perf_counter() - t0
+    oracle.set_threads(1)
+    return n_mb * BETA / dt, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    threads = os.cpu_count() or 1
+    import oracle
+    if not oracle.have_openmp():
+        threads = 1
+    n_mb = 2
+    for _ in range(args.warmup):
+        cpu_oracle_rate(1, threads)
+    times = []
+    for _ in range(args.steps):
+        rate, dt = cpu_oracle_rate(n_mb, threads)
+        times.append(dt)
+    total = n_mb * BETA * args.steps
+    value = total / sum(times)
+    sample = "%d minibatches (%d frames) of the workload per step" % (n_mb, n_mb * BETA)
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic gamma-model spectrogram (host)",
+        "config": {"workload": WORKLOAD, "F": F, "K": K, "beta": BETA,
+                   "n_inner": N_IN},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        out = run_reference(args)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out, dist = run_ours(args)
+    rank, world, _ = dist_env()
+    if rank == 0:
+        if not args.skip_cpu and world == 1:
+            threads = os.cpu_count() or 1
+            import oracle
+            if not oracle.have_openmp():
+                threads = 1
+            rate, dt = cpu_oracle_rate(args.cpu_sample_minibatches, threads)
+            out["cpu_baseline"] = {
+                "value": rate, "unit": "frames/s", "cores": threads, "kind": "oracle",
+                "sample": "%d minibatches (%d frames) of the workload, %.1f s"
+                          % (args.cpu_sample_minibatches,
+                             args.cpu_sample_minibatches * BETA, dt)}
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * onmf.h - C ABI of libonmf: online and batch Itakura-Saito NMF on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: Lefevre, Bach, Fevotte, "Online algorithms for Nonnegative Matrix
+ * Factorization with the Itakura-Saito divergence" (arXiv:1106.4198).
+ *
+ * Matrix conventions (all entry points):
+ *   - column-major; a frame is a column. V is F x n with leading dimension
+ *     ldv >= F (frame j starts at V + j*ldv). W is F x K (ld = F).
+ *     A, B are F x K (ld = F). H is K x n with leading dimension ldh >= K.
+ *   - V, W, H are float32. A, B and the loss sums are float64.
+ *   - V must be finite and >= 0. eps (default 1e-12, Section 3) smooths the
+ *     divergence: d_IS(eps + v, eps + W h) (Section 2.3).
+ *
+ * Pointers marked "host or device" may point to either; the library asks the
+ * CUDA runtime which it is and copies host data through its own buffers.
+ * The caller always owns the memory it passes in; the library owns
+ * everything it allocates (state, staging, scratch) until onmf_destroy.
+ *
+ * Errors are returned as values; no call aborts the process. Work is
+ * asynchronous on the stream given at onmf_init: an error found by a kernel
+ * (invalid input, non-finite result, a device wait that ran out) is recorded
+ * in a per-state error word and returned by the next call that can see it
+ * (at the latest by the next call that synchronizes). Such an error is
+ * sticky: the state then refuses work until onmf_set_state restores it.
+ * Calls on one state are not thread-safe; distinct states are independent.
+ */
+#ifndef ONMF_H
+#define ONMF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ONMF_ABI_VERSION 1
+
+typedef struct onmf_state onmf_state;
+
+typedef enum {
+    ONMF_OK = 0,
+    ONMF_EINVAL = 1,   /* bad argument (null pointer, size, layout, config)    */
+    ONMF_ENOMEM = 2,   /* device or pinned host allocation failed               */
+    ONMF_EBUDGET = 3,  /* request exceeds the memory budget (serving)           */
+    ONMF_ECUDA = 4,    /* a CUDA runtime call failed                            */
+    ONMF_ENUMERIC = 5, /* a kernel saw negative/NaN/Inf input or a non-finite W */
+    ONMF_ETIMEOUT = 6, /* a bounded device-side wait ran out                    */
+    ONMF_ESTATE = 7,   /* the state holds a sticky error or is in the wrong mode */
+    ONMF_EAGAIN = 8    /* nothing ready yet / queue full (serving)              */
+} onmf_status;
+
+typedef enum {
+    ONMF_FP32 = 0,  /* FP32 everywhere on the GPU (A, B accumulate in FP64)   */
+    ONMF_MIXED = 1  /* BF16 tensor-core products with FP32 accumulation, FP32
+                       ratios y/x^2 and 1/x, FP64 A and B                      */
+} onmf_precision;
+
+/* Parameters of Algorithm 1 (Section 2.3). */
+typedef struct {
+    int32_t F;          /* frequency bins (rows of V and W), >= 1              */
+    int32_t K;          /* dictionary size, 1..256                              */
+    int32_t beta;       /* minibatch size: W is updated every beta frames       */
+    int32_t n_inner;    /* multiplicative h updates per frame (fresh restart)   */
+    double eps;         /* smoothing eps >= 0 (Section 2.3), default 1e-12      */
+    double r;           /* forgetting base in [0, 1] ("Scaling past data")     */
+    int64_t n_ref;      /* rho = r^(beta'/n_ref); n_ref <= 0 gives rho = 1      */
+    double h_exponent;  /* gamma of the h update, default 0.5 (MM); 1.0 = MU    */
+    int32_t normalize;  /* 1: rescale W columns to unit L1 norm (Algorithm 1)   */
+    int32_t rho_on_new; /* 0: A <- rho*A + sum a (past scaled, default);
+                           1: A <- A + rho*sum a (literal Algorithm 1)          */
+    int32_t precision;  /* onmf_precision                                       */
+    int32_t reserved;   /* must be 0                                            */
+} onmf_config;
+
+/* Fill *cfg with the defaults for an F x K problem: beta = 1000,
+ * n_inner = 10, eps = 1e-12, r = 1, n_ref = 0, h_exponent = 0.5,
+ * normalize = 1, rho_on_new = 0, precision = ONMF_FP32. */
+void onmf_config_default(onmf_config *cfg, int32_t F, int32_t K);
+
+/* Create an online state (Algorithm 1, "Input": W^(0), A^(0) = B^(0) = 0).
+ *   W0: F x K initial dictionary, host or device (W0_on_device is ignored
+ *       and kept for ABI stability; the pointer kind is detected). It is
+ *       copied; W0 entries must be finite and >= 0.
+ *   stream: a cudaStream_t (NULL = the legacy default stream) on which every
+ *       later call of this state runs.
+ * Allocates the device state (W, A, B, the running loss), a beta-frame
+ * staging buffer and the scratch of the step kernels.
+ * Errors: EINVAL (config out of range, W0 NULL), ENOMEM, ECUDA. */
+onmf_status onmf_init(const onmf_config *cfg, const float *W0,
+                      int32_t W0_on_device, void *stream, onmf_state **out);
+
+/* Append n frames and run one step of Algorithm 1 for every minibatch of
+ * beta frames that becomes complete (draw v_t, solve h_t with W fixed,
+ * accumulate a^(t), b^(t), then A, B and W = sqrt(A/B) with the L1 rescale;
+ * Algorithm 1, Section 2.3 "Mini-batch", "Scaling past data").
+ *   V: F x n, leading dimension ldv >= F, host or device.
+ *   H_out: NULL, or K x n with ldh >= K (host or device) that receives h_t of
+ *       every frame. Frames that stay in the staging buffer get their h
+ *       written when their minibatch runs (a later push or onmf_flush), so
+ *       H_out must stay valid until then.
+ * Asynchronous on the state's stream; V (if on the device) must stay valid
+ * until the stream reaches this call. n = 0 is a no-op.
+ * Errors: EINVAL, ESTATE (sticky error), ECUDA; kernel-detected input errors
+ * surface later as ENUMERIC. */
+onmf_status onmf_push_frames(onmf_state *s, const float *V, int64_t ldv,
+                             int64_t n, float *H_out, int64_t ldh);
+
+/* Run the partial minibatch left in the staging buffer (beta' < beta frames,
+ * rho = r^(beta'/n_ref)). No-op when the buffer is empty. */
+onmf_status onmf_flush(onmf_state *s);
+
+/* Wait for all queued work of the state and return its error status. */
+onmf_status onmf_synchronize(onmf_state *s);
+
+/* Copy the current dictionary W (F x K, normalized as Algorithm 1 leaves
+ * it) to W_out (host or device). Synchronizes the state's stream. */
+onmf_status onmf_get_W(onmf_state *s, float *W_out, int32_t on_device);
+
+/* Copy the sufficient statistics and counters to host memory. Any pointer
+ * may be NULL. A, B: F x K float64 (Eq. aux_fun, accumulated as in
+ * Algorithm 1). t: frames processed by completed minibatches. loss_sum:
+ * running sum of d_IS(eps + v_t, eps + W h_t) over those frames (the online
+ * loss of Eq. online_loss times t). Synchronizes. */
+onmf_status onmf_get_stats(onmf_state *s, double *A, double *B, int64_t *t,
+                           double *loss_sum);
+
+/* Restore a state (checkpoint/resume). W: F x K float32, A, B: F x K
+ * float64, all host memory; t and loss_sum as returned by onmf_get_stats.
+ * Clears the staging buffer and any sticky error. Synchronizes. */
+onmf_status onmf_set_state(onmf_state *s, const float *W, const double *A,
+                           const double *B, int64_t t, double loss_sum);
+
+/* Project n frames on the current W without changing the state: the h-solve
+ * of Algorithm 1 (fresh restart, n_inner multiplicative steps; n_inner < 0
+ * uses the config's value). Used for held-out evaluation (Section 3).
+ *   V: F x n (ldv), host or device.  H_out: K x n (ldh), host or device.
+ *   obj_sum: NULL, or a host double that receives
+ *       sum_n d_IS(eps + v_n, eps + W h_n) (synchronizes when non-NULL). */
+onmf_status onmf_project(onmf_state *s, const float *V, int64_t ldv, int64_t n,
+                         float *H_out, int64_t ldh, int32_t n_inner,
+                         double *obj_sum);
+
+/* Batch IS-NMF (Section 2.1): n_iter cycles, each updating all of H with W
+ * fixed (the h update of the online solver, applied once to every column),
+ * then W <- W o sqrt((P H^T)/(Q H^T)) (= sqrt(A/B) of Eq. aux_fun, with
+ * P = Y/X^2, Q = 1/X, X = eps + W H), then, if normalize, W_:k /= s_k and
+ * H_k: *= s_k with s_k = sum_f W_fk.
+ *   V: F x N (ldv) on the device. W: F x K (ld F) and H: K x N (ld K) on the
+ *   device, updated in place. obj_out: NULL or n_iter host doubles that
+ *   receive the objective (1/N) sum_n d_IS(eps+v_n, eps+W h_n) after each
+ *   cycle (synchronizes when non-NULL).
+ *   stream: cudaStream_t (NULL = legacy default stream).
+ * Allocates its scratch for the call and frees it before returning. */
+onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H,
+                           int32_t F, int32_t K, int64_t N, double eps,
+                           double h_exponent, int32_t n_iter, int32_t normalize,
+                           int32_t precision, double *obj_out, void *stream);
+
+/* Batch start point for H: every column gets the fresh-restart value
+ * sum_f (eps + V_fn) / sum_{f,k} W_fk. V, W, H on the device. */
+onmf_status nmf_batch_init_H(const float *V, int64_t ldv, const float *W,
+                             float *H, int32_t F, int32_t K, int64_t N,
+                             double eps, void *stream);
+
+/* Release the state and everything the library allocated for it. */
+void onmf_destroy(onmf_state *s);
+
+/* Static string naming a status. */
+const char *onmf_status_string(onmf_status st);
+
+/* Text of the last CUDA failure seen by this thread ("" if none). */
+const char *onmf_last_error_message(void);
+
+/* Number of kernel launches this process has issued through the library
+ * (all states), for launch accounting in benchmarks. */
+int64_t onmf_kernel_launches(void);
+
+/* ABI version (ONMF_ABI_VERSION). */
+int32_t onmf_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ONMF_H */

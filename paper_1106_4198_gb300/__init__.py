@@ -1,0 +1,323 @@
+"""Python binding of libonmf: online and batch Itakura-Saito NMF on GB300.
+
+Thin ctypes marshalling over the C ABI declared in ``include/onmf.h``; the
+functions keep the C names. Every step of the computation runs in the CUDA
+kernels of ``libonmf.so``; there is no Python or CPU fallback, and loading
+fails loudly when the library cannot be built or loaded.
+
+Arrays follow the library's memory order: a frame-major spectrogram V is a
+(n, F) array (row j = frame j = column j of the F x n matrix), W is (K, F),
+H is (n, K). Arguments may be torch tensors (CUDA or CPU) or numpy arrays;
+the library detects whether a pointer is host or device memory.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB, build as _build_lib
+
+__all__ = [
+    "OnmfError", "onmf_config", "ONMF_FP32", "ONMF_MIXED", "lib", "build",
+    "onmf_config_default", "onmf_init", "onmf_push_frames", "onmf_flush",
+    "onmf_synchronize", "onmf_get_W", "onmf_get_stats", "onmf_set_state",
+    "onmf_project", "nmf_batch_step", "nmf_batch_init_H", "onmf_destroy",
+    "onmf_status_string", "onmf_kernel_launches", "onmf_abi_version",
+    "OnlineISNMF", "EXPORTED",
+]
+
+ONMF_FP32 = 0
+ONMF_MIXED = 1
+
+# Every symbol include/onmf.h declares.
+EXPORTED = [
+    "onmf_config_default", "onmf_init", "onmf_push_frames", "onmf_flush",
+    "onmf_synchronize", "onmf_get_W", "onmf_get_stats", "onmf_set_state",
+    "onmf_project", "nmf_batch_step", "nmf_batch_init_H", "onmf_destroy",
+    "onmf_status_string", "onmf_last_error_message", "onmf_kernel_launches",
+    "onmf_abi_version",
+]
+
+
+class onmf_config(ctypes.Structure):
+    _fields_ = [
+        ("F", ctypes.c_int32), ("K", ctypes.c_int32),
+        ("beta", ctypes.c_int32), ("n_inner", ctypes.c_int32),
+        ("eps", ctypes.c_double), ("r", ctypes.c_double),
+        ("n_ref", ctypes.c_int64), ("h_exponent", ctypes.c_double),
+        ("normalize", ctypes.c_int32), ("rho_on_new", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class OnmfError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        msg = onmf_status_string(status)
+        detail = lib().onmf_last_error_message().decode(errors="replace")
+        super().__init__("%s%s%s" % (where + ": " if where else "", msg,
+                                     " (" + detail + ")" if detail else ""))
+
+
+_LIB = None
+_vp = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
+_d = ctypes.c_double
+
+
+def build(force=False):
+    """Compile libonmf.so for sm_103a (nvcc) and return its path."""
+    return _build_lib(force=force)
+
+
+def lib():
+    """Load libonmf.so, building it first if it is missing or stale."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build_lib()
+    L = ctypes.CDLL(path)
+    L.onmf_config_default.argtypes = [ctypes.POINTER(onmf_config), _i32, _i32]
+    L.onmf_config_default.restype = None
+    L.onmf_init.argtypes = [ctypes.POINTER(onmf_config), _vp, _i32, _vp,
+                            ctypes.POINTER(_vp)]
+    L.onmf_push_frames.argtypes = [_vp, _vp, _i64, _i64, _vp, _i64]
+    L.onmf_flush.argtypes = [_vp]
+    L.onmf_synchronize.argtypes = [_vp]
+    L.onmf_get_W.argtypes = [_vp, _vp, _i32]
+    L.onmf_get_stats.argtypes = [_vp, _vp, _vp, ctypes.POINTER(_i64),
+                                 ctypes.POINTER(_d)]
+    L.onmf_set_state.argtypes = [_vp, _vp, _vp, _vp, _i64, _d]
+    L.onmf_project.argtypes = [_vp, _vp, _i64, _i64, _vp, _i64, _i32,
+                               ctypes.POINTER(_d)]
+    L.nmf_batch_step.argtypes = [_vp, _i64, _vp, _vp, _i32, _i32, _i64, _d, _d,
+                                 _i32, _i32, _i32, _vp, _vp]
+    L.nmf_batch_init_H.argtypes = [_vp, _i64, _vp, _vp, _i32, _i32, _i64, _d,
+                                   _vp]
+    L.onmf_destroy.argtypes = [_vp]
+    L.onmf_destroy.restype = None
+    L.onmf_status_string.argtypes = [ctypes.c_int]
+    L.onmf_status_string.restype = ctypes.c_char_p
+    L.onmf_last_error_message.restype = ctypes.c_char_p
+    L.onmf_kernel_launches.restype = _i64
+    L.onmf_abi_version.restype = _i32
+    for name in ("onmf_init", "onmf_push_frames", "onmf_flush",
+                 "onmf_synchronize", "onmf_get_W", "onmf_get_stats",
+                 "onmf_set_state", "onmf_project", "nmf_batch_step",
+                 "nmf_batch_init_H"):
+        getattr(L, name).restype = ctypes.c_int
+    _LIB = L
+    return L
+
+
+def _check(st, where):
+    if st != 0:
+        raise OnmfError(st, where)
+
+
+# ------------------------------------------------------------ marshalling
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr_ld(x, cols):
+    """(pointer, leading dimension) of a 2-D row-major array with `cols`
+    columns whose rows may be strided (row stride = leading dimension)."""
+    if x is None:
+        return None, 0
+    if _is_torch(x):
+        import torch
+        assert x.dtype in (torch.float32, torch.float64), x.dtype
+        assert x.dim() == 2 and x.shape[1] == cols and x.stride(1) == 1, \
+            "expected (n, %d) with unit column stride" % cols
+        return x.data_ptr(), max(x.stride(0), cols)
+    assert isinstance(x, np.ndarray) and x.ndim == 2 and x.shape[1] == cols
+    assert x.strides[1] == x.itemsize, "rows must be contiguous"
+    return x.ctypes.data, max(x.strides[0] // x.itemsize, cols)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return 0
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# -------------------------------------------------------------- C names
+
+
+def onmf_status_string(st):
+    return lib().onmf_status_string(int(st)).decode()
+
+
+def onmf_kernel_launches():
+    return int(lib().onmf_kernel_launches())
+
+
+def onmf_abi_version():
+    return int(lib().onmf_abi_version())
+
+
+def onmf_config_default(F, K, **kw):
+    c = onmf_config()
+    lib().onmf_config_default(ctypes.byref(c), int(F), int(K))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def onmf_init(cfg, W0, stream=None):
+    """Create an online state from W0 (K, F) float32 (host or device)."""
+    if _is_torch(W0):
+        W0 = W0.contiguous()
+        assert W0.dtype.is_floating_point and W0.element_size() == 4
+        p = W0.data_ptr()
+        keep = W0
+    else:
+        keep = np.ascontiguousarray(W0, dtype=np.float32)
+        p = keep.ctypes.data
+    assert tuple(keep.shape) == (cfg.K, cfg.F), "W0 must be (K, F)"
+    h = _vp()
+    _check(lib().onmf_init(ctypes.byref(cfg), p, 0, _stream_handle(stream),
+                           ctypes.byref(h)), "onmf_init")
+    return h
+
+
+def onmf_push_frames(state, V, H_out=None, n=None):
+    """Push frames V (n, F) float32; optional H_out (n, K) receives h."""
+    K = H_out.shape[1] if H_out is not None else 1
+    pv, ldv = _ptr_ld(V, V.shape[1])
+    ph, ldh = _ptr_ld(H_out, K) if H_out is not None else (None, 1)
+    n = V.shape[0] if n is None else n
+    _check(lib().onmf_push_frames(state, pv, ldv, n, ph, ldh), "onmf_push_frames")
+
+
+def onmf_flush(state):
+    _check(lib().onmf_flush(state), "onmf_flush")
+
+
+def onmf_synchronize(state):
+    _check(lib().onmf_synchronize(state), "onmf_synchronize")
+
+
+def onmf_get_W(state, out):
+    """Copy W into `out` ((K, F) float32 tensor or array, host or device)."""
+    p = out.data_ptr() if _is_torch(out) else out.ctypes.data
+    _check(lib().onmf_get_W(state, p, 0), "onmf_get_W")
+    return out
+
+
+def onmf_get_stats(state, A=None, B=None):
+    """Fill A, B ((K, F) float64 host arrays, optional); return (t, loss_sum)."""
+    t = _i64(0)
+    ls = _d(0.0)
+    pa = A.ctypes.data if A is not None else None
+    pb = B.ctypes.data if B is not None else None
+    _check(lib().onmf_get_stats(state, pa, pb, ctypes.byref(t), ctypes.byref(ls)),
+           "onmf_get_stats")
+    return t.value, ls.value
+
+
+def onmf_set_state(state, W, A, B, t, loss_sum):
+    W = np.ascontiguousarray(W, dtype=np.float32)
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    _check(lib().onmf_set_state(state, W.ctypes.data, A.ctypes.data,
+                                B.ctypes.data, int(t), float(loss_sum)),
+           "onmf_set_state")
+
+
+def onmf_project(state, V, H_out, n_inner=-1, want_obj=False):
+    """h-solve of V (n, F) with W fixed into H_out (n, K); returns the d_IS
+    sum when want_obj (synchronizing), else None."""
+    pv, ldv = _ptr_ld(V, V.shape[1])
+    ph, ldh = _ptr_ld(H_out, H_out.shape[1])
+    obj = _d(0.0)
+    _check(lib().onmf_project(state, pv, ldv, V.shape[0], ph, ldh, int(n_inner),
+                              ctypes.byref(obj) if want_obj else None),
+           "onmf_project")
+    return obj.value if want_obj else None
+
+
+def nmf_batch_init_H(V, W, H, eps=1e-12, stream=None):
+    """Fresh-restart start point for every column of H (device tensors)."""
+    pv, ldv = _ptr_ld(V, V.shape[1])
+    K, F = W.shape
+    _check(lib().nmf_batch_init_H(pv, ldv, W.data_ptr(), H.data_ptr(), F, K,
+                                  V.shape[0], eps, _stream_handle(stream)),
+           "nmf_batch_init_H")
+
+
+def nmf_batch_step(V, W, H, eps=1e-12, h_exponent=0.5, n_iter=1, normalize=1,
+                   precision=ONMF_FP32, want_obj=True, stream=None):
+    """Batch IS-NMF cycles on device tensors V (N, F), W (K, F), H (N, K),
+    updated in place. Returns the objective after each cycle (or None)."""
+    pv, ldv = _ptr_ld(V, V.shape[1])
+    K, F = W.shape
+    N = V.shape[0]
+    obj = (ctypes.c_double * max(1, n_iter))() if want_obj else None
+    _check(lib().nmf_batch_step(pv, ldv, W.data_ptr(), H.data_ptr(), F, K, N, eps,
+                                h_exponent, n_iter, normalize, precision,
+                                obj, _stream_handle(stream)),
+           "nmf_batch_step")
+    return np.array(obj[:n_iter]) if want_obj else None
+
+
+def onmf_destroy(state):
+    if state:
+        lib().onmf_destroy(state)
+
+
+class OnlineISNMF:
+    """Convenience owner of one online state (same calls, fewer arguments)."""
+
+    def __init__(self, F, K, W0, stream=None, **cfg):
+        self.cfg = onmf_config_default(F, K, **cfg)
+        self.F, self.K = F, K
+        self.state = onmf_init(self.cfg, W0, stream)
+
+    def push(self, V, H_out=None):
+        onmf_push_frames(self.state, V, H_out)
+
+    def flush(self):
+        onmf_flush(self.state)
+
+    def sync(self):
+        onmf_synchronize(self.state)
+
+    def W(self):
+        out = np.empty((self.K, self.F), dtype=np.float32)
+        return onmf_get_W(self.state, out)
+
+    def stats(self):
+        A = np.empty((self.K, self.F))
+        B = np.empty((self.K, self.F))
+        t, ls = onmf_get_stats(self.state, A, B)
+        return A, B, t, ls
+
+    def set_state(self, W, A, B, t, loss_sum):
+        onmf_set_state(self.state, W, A, B, t, loss_sum)
+
+    def project(self, V, H_out, n_inner=-1, want_obj=False):
+        return onmf_project(self.state, V, H_out, n_inner, want_obj)
+
+    def close(self):
+        if self.state:
+            onmf_destroy(self.state)
+            self.state = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,723 @@
+// C ABI of libonmf (include/onmf.h): state management, the minibatch
+// staging of Algorithm 1's frame stream, host/device pointer handling and
+// the batch cycle driver. Every step of the arithmetic runs in the kernels of
+// onmf_kernels.cu; this file only allocates, copies and launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/onmf.h"
+#include "onmf_device.cuh"
+#include "onmf_kernels.cuh"
+#include "onmf_launch.h"
+
+using namespace onmf;
+
+namespace {
+
+thread_local char g_msg[512] = "";
+
+void set_msg(const char *what, cudaError_t e) {
+    snprintf(g_msg, sizeof g_msg, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) {                   \
+            set_msg(#call, e_);                    \
+            return e_ == cudaErrorMemoryAllocation ? ONMF_ENOMEM : ONMF_ECUDA; \
+        }                                          \
+    } while (0)
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+onmf_status status_from_err(int bits) {
+    if (bits & ERR_TIMEOUT) return ONMF_ETIMEOUT;
+    if (bits & (ERR_INPUT | ERR_NUMERIC)) return ONMF_ENUMERIC;
+    return ONMF_OK;
+}
+
+double rho_of(const onmf_config &c, long long nb) {
+    if (c.n_ref <= 0) return 1.0;
+    return std::pow(c.r, (double)nb / (double)c.n_ref);
+}
+
+struct Segment {
+    int off, n;      // columns of the staging buffer
+    float *dst;      // caller's H_out for these frames
+    long long ldh;
+};
+
+int g_configured = 0;
+
+onmf_status ensure_configured() {
+    if (!g_configured) {
+        CK(configure_kernels());
+        g_configured = 1;
+    }
+    return ONMF_OK;
+}
+
+}  // namespace
+
+struct onmf_state {
+    onmf_config cfg;
+    Shape s;
+    cudaStream_t stream;
+    int prec;
+    // state
+    float *Wcm = nullptr, *Wrm = nullptr, *Wn = nullptr, *swpart = nullptr;
+    __nv_bfloat16 *Wimg = nullptr;
+    double *A = nullptr, *B = nullptr, *loss_sum = nullptr;
+    // scratch
+    void *Pg = nullptr, *Qg = nullptr, *Hg = nullptr;
+    int betap = 0;
+    double *loss_part = nullptr, *tmp_sum = nullptr;
+    unsigned *bar = nullptr;
+    int *err_d = nullptr;
+    int *err_h = nullptr;  // pinned mirror of err_d
+    // staging of a partial minibatch
+    float *staging = nullptr, *Hstage = nullptr;
+    int staged = 0;
+    std::vector<Segment> segs;
+    // host-input ring
+    float *vring[2] = {nullptr, nullptr};
+    float *hring[2] = {nullptr, nullptr};
+    cudaEvent_t ring_ev[2] = {nullptr, nullptr};
+    long long ring_frames = 0;
+    double *obj_h = nullptr;  // pinned
+    long long t = 0;
+    int sticky = ONMF_OK;
+    int grid = 1, tile_grid = 1;
+    size_t smem = 0, tile_smem = 0;
+    int num_sms = 1;
+};
+
+static onmf_status check_sticky(onmf_state *s) {
+    if (s->sticky != ONMF_OK) return ONMF_ESTATE;
+    int bits = __atomic_load_n(s->err_h, __ATOMIC_ACQUIRE);
+    if (bits) {
+        s->sticky = status_from_err(bits);
+        return (onmf_status)s->sticky;
+    }
+    return ONMF_OK;
+}
+
+static onmf_status mirror_err(onmf_state *s) {
+    CK(cudaMemcpyAsync(s->err_h, s->err_d, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    return ONMF_OK;
+}
+
+static onmf_status sync_and_check(onmf_state *s) {
+    CK(cudaStreamSynchronize(s->stream));
+    int bits = *s->err_h;
+    if (bits && s->sticky == ONMF_OK) s->sticky = status_from_err(bits);
+    return s->sticky == ONMF_OK ? ONMF_OK : (onmf_status)s->sticky;
+}
+
+static onmf_status prepare_images(onmf_state *s) {
+    CK(launch_prepare(s->s, s->Wcm, s->prec == PREC_FP32 ? s->Wrm : nullptr,
+                      s->prec == PREC_MIXED ? s->Wimg : nullptr, s->swpart, s->stream));
+    return ONMF_OK;
+}
+
+extern "C" {
+
+void onmf_config_default(onmf_config *c, int32_t F, int32_t K) {
+    if (!c) return;
+    memset(c, 0, sizeof *c);
+    c->F = F;
+    c->K = K;
+    c->beta = 1000;
+    c->n_inner = 10;
+    c->eps = 1e-12;
+    c->r = 1.0;
+    c->n_ref = 0;
+    c->h_exponent = 0.5;
+    c->normalize = 1;
+    c->rho_on_new = 0;
+    c->precision = ONMF_FP32;
+}
+
+const char *onmf_status_string(onmf_status st) {
+    switch (st) {
+    case ONMF_OK: return "ONMF_OK";
+    case ONMF_EINVAL: return "ONMF_EINVAL: invalid argument";
+    case ONMF_ENOMEM: return "ONMF_ENOMEM: out of memory";
+    case ONMF_EBUDGET: return "ONMF_EBUDGET: memory budget exceeded";
+    case ONMF_ECUDA: return "ONMF_ECUDA: CUDA runtime error";
+    case ONMF_ENUMERIC: return "ONMF_ENUMERIC: invalid input value or non-finite result";
+    case ONMF_ETIMEOUT: return "ONMF_ETIMEOUT: device wait timed out";
+    case ONMF_ESTATE: return "ONMF_ESTATE: state holds a sticky error";
+    case ONMF_EAGAIN: return "ONMF_EAGAIN: not ready";
+    }
+    return "unknown onmf status";
+}
+
+const char *onmf_last_error_message(void) { return g_msg; }
+
+int64_t onmf_kernel_launches(void) { return kernel_launches(); }
+
+int32_t onmf_abi_version(void) { return ONMF_ABI_VERSION; }
+
+void onmf_destroy(onmf_state *s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    void *dev[] = {s->Wcm, s->Wrm, s->Wn, s->swpart, s->Wimg, s->A, s->B, s->loss_sum, s->Pg,
+                   s->Qg, s->Hg, s->loss_part, s->tmp_sum, s->bar, s->err_d, s->staging,
+                   s->Hstage, s->vring[0], s->vring[1], s->hring[0], s->hring[1]};
+    for (void *p : dev)
+        if (p) cudaFree(p);
+    if (s->err_h) cudaFreeHost(s->err_h);
+    if (s->obj_h) cudaFreeHost(s->obj_h);
+    for (int i = 0; i < 2; ++i)
+        if (s->ring_ev[i]) cudaEventDestroy(s->ring_ev[i]);
+    delete s;
+}
+
+onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_device,
+                      void *stream, onmf_state **out) {
+    (void)W0_on_device;
+    if (!cfg || !W0 || !out) return ONMF_EINVAL;
+    *out = nullptr;
+    const onmf_config &c = *cfg;
+    if (c.F < 1 || c.F > 8192 || c.K < 1 || c.K > 256 || c.beta < 1 || c.beta > (1 << 20) ||
+        c.n_inner < 0 || c.n_inner > 100000 || !(c.eps >= 0.0) || !std::isfinite(c.eps) ||
+        !(c.r >= 0.0 && c.r <= 1.0) || !(c.h_exponent > 0.0) || c.reserved != 0 ||
+        (c.precision != ONMF_FP32 && c.precision != ONMF_MIXED))
+        return ONMF_EINVAL;
+    if (c.precision == ONMF_MIXED && c.K > 128) {
+        snprintf(g_msg, sizeof g_msg, "mixed precision supports K <= 128");
+        return ONMF_EINVAL;
+    }
+    onmf_status st = ensure_configured();
+    if (st != ONMF_OK) return st;
+    onmf_state *s = new onmf_state();
+    s->cfg = c;
+    s->s = make_shape(c.F, c.K);
+    s->stream = reinterpret_cast<cudaStream_t>(stream);
+    s->prec = c.precision == ONMF_MIXED ? PREC_MIXED : PREC_FP32;
+    const Shape &sh = s->s;
+    const size_t FK = (size_t)c.F * c.K;
+    s->betap = (c.beta + 15) / 16 * 16;
+    const size_t elem = s->prec == PREC_MIXED ? 2 : 4;
+    const int ntiles = (c.beta + kTile - 1) / kTile;
+    auto fail = [&](onmf_status e) {
+        onmf_destroy(s);
+        return e;
+    };
+#define AL(ptr, bytes)                                                         \
+    do {                                                                       \
+        cudaError_t e_ = cudaMalloc((void **)&(ptr), (bytes));                 \
+        if (e_ != cudaSuccess) {                                               \
+            set_msg("cudaMalloc", e_);                                         \
+            return fail(ONMF_ENOMEM);                                          \
+        }                                                                      \
+    } while (0)
+    AL(s->Wcm, FK * 4);
+    AL(s->Wn, FK * 4);
+    AL(s->swpart, (size_t)c.K * 4);
+    AL(s->A, FK * 8);
+    AL(s->B, FK * 8);
+    AL(s->loss_sum, 8);
+    AL(s->tmp_sum, 8);
+    if (s->prec == PREC_FP32) {
+        AL(s->Wrm, FK * 4);
+        AL(s->Hg, (size_t)s->betap * sh.Kh * 4);
+    } else {
+        AL(s->Wimg, (size_t)sh.Kp * sh.WLD * 2);
+        AL(s->Hg, (size_t)sh.Kh * s->betap * 2);
+    }
+    AL(s->Pg, (size_t)s->betap * sh.Fp16 * elem);
+    AL(s->Qg, (size_t)s->betap * sh.Fp16 * elem);
+    AL(s->loss_part, (size_t)ntiles * 8);
+    AL(s->bar, 16);
+    AL(s->err_d, 16);
+    AL(s->staging, (size_t)c.beta * c.F * 4);
+    AL(s->Hstage, (size_t)c.beta * c.K * 4);
+#undef AL
+    if (cudaHostAlloc((void **)&s->err_h, 16, cudaHostAllocDefault) != cudaSuccess ||
+        cudaHostAlloc((void **)&s->obj_h, 16, cudaHostAllocDefault) != cudaSuccess)
+        return fail(ONMF_ENOMEM);
+    *s->err_h = 0;
+    cudaStream_t q = s->stream;
+    cudaError_t e = cudaSuccess;
+    if (s->Wimg && e == cudaSuccess) e = cudaMemsetAsync(s->Wimg, 0, (size_t)sh.Kp * sh.WLD * 2, q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->Hg, 0, (size_t)s->betap * sh.Kh * elem, q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->Pg, 0, (size_t)s->betap * sh.Fp16 * elem, q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->Qg, 0, (size_t)s->betap * sh.Fp16 * elem, q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->A, 0, FK * 8, q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->B, 0, FK * 8, q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->loss_sum, 0, 8, q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->err_d, 0, 16, q);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->Wcm, W0, FK * 4, cudaMemcpyDefault, q);
+    if (e != cudaSuccess) {
+        set_msg("init copies", e);
+        return fail(ONMF_ECUDA);
+    }
+    if ((st = prepare_images(s)) != ONMF_OK) return fail(st);
+    // launch geometry
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    s->smem = online_smem_bytes(sh, s->prec);
+    s->tile_smem = tile_smem_bytes(sh, s->prec);
+    if (s->smem > 227 * 1024) {
+        snprintf(g_msg, sizeof g_msg, "shared memory need %zu exceeds 227 KB", s->smem);
+        return fail(ONMF_EINVAL);
+    }
+    int per_sm = 0;
+    if ((e = max_coresident_blocks(s->prec, s->smem, &per_sm)) != cudaSuccess || per_sm < 1) {
+        set_msg("occupancy", e);
+        return fail(ONMF_ECUDA);
+    }
+    const int units = (sh.Fp16 / 16) * (sh.Kh / 32);
+    int want = std::max(std::max(ntiles, units), (c.K + kWarps - 1) / kWarps);
+    s->grid = std::min(want, per_sm * s->num_sms);
+    s->tile_grid = s->num_sms;
+    // sanity: all of W0 finite and >= 0 (checked on the host copy)
+    std::vector<float> w(FK);
+    if (cudaMemcpyAsync(w.data(), s->Wcm, FK * 4, cudaMemcpyDeviceToHost, q) != cudaSuccess ||
+        cudaStreamSynchronize(q) != cudaSuccess)
+        return fail(ONMF_ECUDA);
+    for (float v : w)
+        if (!(v >= 0.f) || std::isinf(v)) return fail(ONMF_EINVAL);
+    *out = s;
+    return ONMF_OK;
+}
+
+}  // extern "C"
+
+// Run nmb minibatches (all of beta frames except the last, nb_last) read
+// from device memory V (ldv), writing h to device H (ldh) when non-NULL.
+static onmf_status run_minibatches(onmf_state *s, const float *V, long long ldv, int nmb,
+                                   int nb_last, float *H, long long ldh) {
+    if (nmb <= 0) return ONMF_OK;
+    const onmf_config &c = s->cfg;
+    StepArgs a;
+    a.s = s->s;
+    a.eps = (float)c.eps;
+    a.gamma = (float)c.h_exponent;
+    a.n_in = c.n_inner;
+    a.normalize = c.normalize;
+    a.rho_on_new = c.rho_on_new;
+    a.V = V;
+    a.ldv = ldv;
+    a.nmb = nmb;
+    a.beta = c.beta;
+    a.nb_last = nb_last;
+    a.rho_full = rho_of(c, c.beta);
+    a.rho_last = rho_of(c, nb_last);
+    a.H_out = H;
+    a.ldh = ldh;
+    a.Wcm = s->Wcm;
+    a.Wrm = s->Wrm;
+    a.Wimg = s->Wimg;
+    a.Wn = s->Wn;
+    a.A = s->A;
+    a.B = s->B;
+    a.loss_sum = s->loss_sum;
+    a.swpart = s->swpart;
+    a.Pg = s->Pg;
+    a.Qg = s->Qg;
+    a.Hg = s->Hg;
+    a.betap = s->betap;
+    a.loss_part = s->loss_part;
+    a.bar = s->bar;
+    a.err = s->err_d;
+    CK(launch_online(a, s->prec, s->grid, s->smem, s->stream));
+    s->t += (long long)(nmb - 1) * c.beta + nb_last;
+    return mirror_err(s);
+}
+
+// Process the staging buffer as one minibatch of `staged` frames and hand
+// the h of its frames to the recorded destinations.
+static onmf_status run_staged(onmf_state *s) {
+    const int n = s->staged;
+    if (n == 0) return ONMF_OK;
+    bool want_h = !s->segs.empty();
+    onmf_status st = run_minibatches(s, s->staging, s->cfg.F, 1, n, want_h ? s->Hstage : nullptr,
+                                     s->cfg.K);
+    if (st != ONMF_OK) return st;
+    for (const Segment &g : s->segs) {
+        CK(cudaMemcpy2DAsync(g.dst, g.ldh * 4, s->Hstage + (size_t)g.off * s->cfg.K,
+                             (size_t)s->cfg.K * 4, (size_t)s->cfg.K * 4, g.n, cudaMemcpyDefault,
+                             s->stream));
+    }
+    s->segs.clear();
+    s->staged = 0;
+    return ONMF_OK;
+}
+
+// Frames already on the device (V) with optional H destination (host or device).
+static onmf_status push_device(onmf_state *s, const float *V, long long ldv, long long n,
+                               float *H, long long ldh) {
+    const onmf_config &c = s->cfg;
+    const bool hdev = H && is_device_ptr(H);
+    long long i = 0;
+    auto stage = [&](long long from, int count) -> onmf_status {
+        CK(cudaMemcpy2DAsync(s->staging + (size_t)s->staged * c.F, (size_t)c.F * 4,
+                             V + from * ldv, (size_t)ldv * 4, (size_t)c.F * 4, count,
+                             cudaMemcpyDeviceToDevice, s->stream));
+        if (H) s->segs.push_back(Segment{s->staged, count, H + from * ldh, ldh});
+        s->staged += count;
+        return ONMF_OK;
+    };
+    onmf_status st;
+    if (s->staged > 0) {
+        int take = (int)std::min<long long>(c.beta - s->staged, n);
+        if ((st = stage(0, take)) != ONMF_OK) return st;
+        i = take;
+        if (s->staged == c.beta && (st = run_staged(s)) != ONMF_OK) return st;
+    }
+    long long nfull = (n - i) / c.beta;
+    while (nfull > 0) {
+        // bound a single launch to ~2^20 frames so one call never monopolizes the GPU
+        int chunk = (int)std::min<long long>(nfull, std::max(1, (1 << 20) / c.beta));
+        if (H && !hdev) {
+            // device H for the chunk, then copy to the caller's host memory
+            float *Hd = nullptr;
+            size_t bytes = (size_t)chunk * c.beta * c.K * 4;
+            CK(cudaMallocAsync((void **)&Hd, bytes, s->stream));
+            st = run_minibatches(s, V + i * ldv, ldv, chunk, c.beta, Hd, c.K);
+            if (st == ONMF_OK) {
+                cudaError_t e = cudaMemcpy2DAsync(H + i * ldh, ldh * 4, Hd, (size_t)c.K * 4,
+                                                  (size_t)c.K * 4, (size_t)chunk * c.beta,
+                                                  cudaMemcpyDeviceToHost, s->stream);
+                if (e != cudaSuccess) {
+                    set_msg("H copy", e);
+                    st = ONMF_ECUDA;
+                }
+            }
+            cudaFreeAsync(Hd, s->stream);
+            if (st != ONMF_OK) return st;
+        } else {
+            st = run_minibatches(s, V + i * ldv, ldv, chunk, c.beta, H ? H + i * ldh : nullptr, ldh);
+            if (st != ONMF_OK) return st;
+        }
+        i += (long long)chunk * c.beta;
+        nfull -= chunk;
+    }
+    if (i < n) {
+        if ((st = stage(i, (int)(n - i))) != ONMF_OK) return st;
+    }
+    return ONMF_OK;
+}
+
+extern "C" {
+
+onmf_status onmf_push_frames(onmf_state *s, const float *V, int64_t ldv, int64_t n, float *H_out,
+                             int64_t ldh) {
+    if (!s) return ONMF_EINVAL;
+    onmf_status st = check_sticky(s);
+    if (st != ONMF_OK) return st;
+    if (n < 0 || (n > 0 && !V) || ldv < s->cfg.F || (H_out && ldh < s->cfg.K)) return ONMF_EINVAL;
+    if (n == 0) return ONMF_OK;
+    if (is_device_ptr(V)) return push_device(s, V, ldv, n, H_out, ldh);
+    // host frames: copy through a double-buffered device ring, chunk by chunk
+    const onmf_config &c = s->cfg;
+    if (!s->vring[0]) {
+        s->ring_frames = (long long)std::max(1, (1 << 18) / c.beta) * c.beta;
+        for (int b = 0; b < 2; ++b) {
+            CK(cudaMalloc((void **)&s->vring[b], (size_t)s->ring_frames * c.F * 4));
+            CK(cudaEventCreateWithFlags(&s->ring_ev[b], cudaEventDisableTiming));
+        }
+    }
+    long long i = 0;
+    int b = 0;
+    while (i < n) {
+        long long m = std::min(s->ring_frames, n - i);
+        CK(cudaEventSynchronize(s->ring_ev[b]));  // slot free (previous use consumed)
+        CK(cudaMemcpy2DAsync(s->vring[b], (size_t)c.F * 4, V + i * ldv, (size_t)ldv * 4,
+                             (size_t)c.F * 4, m, cudaMemcpyHostToDevice, s->stream));
+        st = push_device(s, s->vring[b], c.F, m, H_out ? H_out + i * ldh : nullptr, ldh);
+        if (st != ONMF_OK) return st;
+        CK(cudaEventRecord(s->ring_ev[b], s->stream));
+        i += m;
+        b ^= 1;
+    }
+    return ONMF_OK;
+}
+
+onmf_status onmf_flush(onmf_state *s) {
+    if (!s) return ONMF_EINVAL;
+    onmf_status st = check_sticky(s);
+    if (st != ONMF_OK) return st;
+    return run_staged(s);
+}
+
+onmf_status onmf_synchronize(onmf_state *s) {
+    if (!s) return ONMF_EINVAL;
+    return sync_and_check(s);
+}
+
+onmf_status onmf_get_W(onmf_state *s, float *W_out, int32_t on_device) {
+    (void)on_device;
+    if (!s || !W_out) return ONMF_EINVAL;
+    onmf_status st = sync_and_check(s);
+    if (st != ONMF_OK && st != ONMF_ENUMERIC) return st;
+    CK(cudaMemcpy(W_out, s->Wcm, (size_t)s->cfg.F * s->cfg.K * 4, cudaMemcpyDefault));
+    return st;
+}
+
+onmf_status onmf_get_stats(onmf_state *s, double *A, double *B, int64_t *t, double *loss_sum) {
+    if (!s) return ONMF_EINVAL;
+    onmf_status st = sync_and_check(s);
+    const size_t FK = (size_t)s->cfg.F * s->cfg.K;
+    if (A) CK(cudaMemcpy(A, s->A, FK * 8, cudaMemcpyDefault));
+    if (B) CK(cudaMemcpy(B, s->B, FK * 8, cudaMemcpyDefault));
+    if (loss_sum) CK(cudaMemcpy(loss_sum, s->loss_sum, 8, cudaMemcpyDefault));
+    if (t) *t = s->t;
+    return st;
+}
+
+onmf_status onmf_set_state(onmf_state *s, const float *W, const double *A, const double *B,
+                           int64_t t, double loss_sum) {
+    if (!s || !W || !A || !B || t < 0) return ONMF_EINVAL;
+    CK(cudaStreamSynchronize(s->stream));
+    const size_t FK = (size_t)s->cfg.F * s->cfg.K;
+    for (size_t i = 0; i < FK; ++i)
+        if (!(W[i] >= 0.f) || std::isinf(W[i]) || !(A[i] >= 0.0) || !(B[i] >= 0.0))
+            return ONMF_EINVAL;
+    CK(cudaMemcpy(s->Wcm, W, FK * 4, cudaMemcpyDefault));
+    CK(cudaMemcpy(s->A, A, FK * 8, cudaMemcpyDefault));
+    CK(cudaMemcpy(s->B, B, FK * 8, cudaMemcpyDefault));
+    CK(cudaMemcpy(s->loss_sum, &loss_sum, 8, cudaMemcpyHostToDevice));
+    CK(cudaMemset(s->err_d, 0, 16));
+    *s->err_h = 0;
+    s->sticky = ONMF_OK;
+    s->staged = 0;
+    s->segs.clear();
+    s->t = t;
+    onmf_status st = prepare_images(s);
+    if (st != ONMF_OK) return st;
+    return sync_and_check(s);
+}
+
+onmf_status onmf_project(onmf_state *s, const float *V, int64_t ldv, int64_t n, float *H_out,
+                         int64_t ldh, int32_t n_inner, double *obj_sum) {
+    if (!s) return ONMF_EINVAL;
+    onmf_status st = check_sticky(s);
+    if (st != ONMF_OK) return st;
+    const onmf_config &c = s->cfg;
+    if (n < 0 || (n > 0 && !V) || ldv < c.F || (H_out && ldh < c.K)) return ONMF_EINVAL;
+    if (obj_sum) *obj_sum = 0.0;
+    if (n == 0) return ONMF_OK;
+    const int nin = n_inner < 0 ? c.n_inner : n_inner;
+    const bool vdev = is_device_ptr(V);
+    const bool hdev = !H_out || is_device_ptr(H_out);
+    const float *Vd = V;
+    float *Vtmp = nullptr, *Htmp = nullptr;
+    double *lp = nullptr;
+    const long long ntiles = (n + kTile - 1) / kTile;
+    cudaStream_t q = s->stream;
+    if (!vdev) {
+        CK(cudaMallocAsync((void **)&Vtmp, (size_t)n * c.F * 4, q));
+        CK(cudaMemcpy2DAsync(Vtmp, (size_t)c.F * 4, V, (size_t)ldv * 4, (size_t)c.F * 4, n,
+                             cudaMemcpyHostToDevice, q));
+        Vd = Vtmp;
+    }
+    float *Hd = H_out;
+    long long ldhd = ldh;
+    if (H_out && !hdev) {
+        CK(cudaMallocAsync((void **)&Htmp, (size_t)n * c.K * 4, q));
+        Hd = Htmp;
+        ldhd = c.K;
+    }
+    if (obj_sum) CK(cudaMallocAsync((void **)&lp, (size_t)ntiles * 8, q));
+    TileArgs a;
+    memset(&a, 0, sizeof a);
+    a.s = s->s;
+    a.eps = (float)c.eps;
+    a.gamma = (float)c.h_exponent;
+    a.n_in = nin;
+    a.V = Vd;
+    a.ldv = vdev ? ldv : c.F;
+    a.n = n;
+    a.H_out = Hd;
+    a.ldh = ldhd;
+    a.final_pass = obj_sum ? 1 : 0;
+    a.Wcm = s->Wcm;
+    a.Wrm = s->Wrm;
+    a.Wimg = s->Wimg;
+    a.swpart = s->swpart;
+    a.loss_part = lp;
+    a.err = s->err_d;
+    const int grid = (int)std::min<long long>(ntiles, (long long)s->tile_grid * 2);
+    CK(launch_tiles(a, s->prec, grid, s->tile_smem, q));
+    if (Htmp)
+        CK(cudaMemcpy2DAsync(H_out, ldh * 4, Htmp, (size_t)c.K * 4, (size_t)c.K * 4, n,
+                             cudaMemcpyDeviceToHost, q));
+    if (obj_sum) {
+        CK(launch_sum(lp, ntiles, s->tmp_sum, 0, q));
+        CK(cudaMemcpyAsync(s->obj_h, s->tmp_sum, 8, cudaMemcpyDeviceToHost, q));
+    }
+    if (Vtmp) cudaFreeAsync(Vtmp, q);
+    if (Htmp) cudaFreeAsync(Htmp, q);
+    if (lp) cudaFreeAsync(lp, q);
+    if ((st = mirror_err(s)) != ONMF_OK) return st;
+    if (obj_sum || Htmp) {
+        st = sync_and_check(s);
+        if (obj_sum) *obj_sum = *s->obj_h;
+        return st;
+    }
+    return ONMF_OK;
+}
+
+onmf_status nmf_batch_init_H(const float *V, int64_t ldv, const float *W, float *H, int32_t F,
+                             int32_t K, int64_t N, double eps, void *stream) {
+    if (!V || !W || !H || F < 1 || K < 1 || K > 256 || N < 0 || ldv < F) return ONMF_EINVAL;
+    onmf_status st = ensure_configured();
+    if (st != ONMF_OK) return st;
+    if (N == 0) return ONMF_OK;
+    cudaStream_t q = reinterpret_cast<cudaStream_t>(stream);
+    Shape sh = make_shape(F, K);
+    float *sw = nullptr;
+    CK(cudaMallocAsync((void **)&sw, (size_t)K * 4, q));
+    CK(launch_prepare(sh, W, nullptr, nullptr, sw, q));
+    CK(launch_batch_h0(sh, V, ldv, N, (float)eps, sw, H, q));
+    cudaFreeAsync(sw, q);
+    return ONMF_OK;
+}
+
+onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int32_t F, int32_t K,
+                           int64_t N, double eps, double h_exponent, int32_t n_iter,
+                           int32_t normalize, int32_t precision, double *obj_out, void *stream) {
+    if (!V || !W || !H || F < 1 || F > 8192 || K < 1 || K > 256 || N < 1 || ldv < F ||
+        n_iter < 0 || !(eps >= 0.0) || !(h_exponent > 0.0) ||
+        (precision != ONMF_FP32 && precision != ONMF_MIXED))
+        return ONMF_EINVAL;
+    if (precision == ONMF_MIXED && K > 128) return ONMF_EINVAL;
+    onmf_status st = ensure_configured();
+    if (st != ONMF_OK) return st;
+    if (n_iter == 0) return ONMF_OK;
+    cudaStream_t q = reinterpret_cast<cudaStream_t>(stream);
+    const int prec = precision == ONMF_MIXED ? PREC_MIXED : PREC_FP32;
+    const Shape sh = make_shape(F, K);
+    const long long betap = (N + 15) / 16 * 16;
+    const size_t elem = prec == PREC_MIXED ? 2 : 4;
+    const long long ntiles = (N + kTile - 1) / kTile;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int units = (sh.Fp16 / 16) * (sh.Kh / 32);
+    int nchunks = std::max(1, std::min<int>((2 * nsm + units - 1) / units, (int)((N + 255) / 256)));
+    // scratch
+    float *Wrm = nullptr, *swp = nullptr, *part = nullptr, *scale = nullptr;
+    __nv_bfloat16 *Wimg = nullptr;
+    void *Pg = nullptr, *Qg = nullptr, *Hg = nullptr;
+    double *lp = nullptr, *obj_d = nullptr;
+    int *err = nullptr;
+    std::vector<void *> owned;
+    auto al = [&](void **p, size_t bytes) -> bool {
+        if (cudaMallocAsync(p, bytes, q) != cudaSuccess) return false;
+        owned.push_back(*p);
+        return true;
+    };
+    bool ok = al((void **)&swp, (size_t)K * 4) && al((void **)&scale, (size_t)K * 4) &&
+              al((void **)&part, (size_t)nchunks * 2 * sh.Fp16 * sh.Kh * 4) &&
+              al(&Pg, (size_t)betap * sh.Fp16 * elem) && al(&Qg, (size_t)betap * sh.Fp16 * elem) &&
+              al(&Hg, (size_t)betap * sh.Kh * elem) && al((void **)&lp, (size_t)ntiles * 8) &&
+              al((void **)&obj_d, (size_t)std::max(1, n_iter) * 8) && al((void **)&err, 16);
+    if (ok && prec == PREC_FP32) ok = al((void **)&Wrm, (size_t)F * K * 4);
+    if (ok && prec == PREC_MIXED) ok = al((void **)&Wimg, (size_t)sh.Kp * sh.WLD * 2);
+    auto cleanup = [&]() {
+        for (void *p : owned) cudaFreeAsync(p, q);
+    };
+    if (!ok) {
+        cleanup();
+        snprintf(g_msg, sizeof g_msg, "batch scratch allocation failed");
+        return ONMF_ENOMEM;
+    }
+    cudaError_t e = cudaSuccess;
+    if (Wimg) e = cudaMemsetAsync(Wimg, 0, (size_t)sh.Kp * sh.WLD * 2, q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(Hg, 0, (size_t)betap * sh.Kh * elem, q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 16, q);
+    const size_t tsm = tile_smem_bytes(sh, prec);
+    const int tgrid = (int)std::min<long long>(ntiles, 2LL * nsm);
+    TileArgs a;
+    memset(&a, 0, sizeof a);
+    a.s = sh;
+    a.eps = (float)eps;
+    a.gamma = (float)h_exponent;
+    a.V = V;
+    a.ldv = ldv;
+    a.n = N;
+    a.Wcm = W;
+    a.Wrm = Wrm;
+    a.Wimg = Wimg;
+    a.swpart = swp;
+    a.err = err;
+    a.betap = betap;
+    for (int it = 0; it < n_iter && e == cudaSuccess; ++it) {
+        // H step (its first X gives the objective of the previous iterate)
+        e = launch_prepare(sh, W, Wrm, Wimg, swp, q);
+        TileArgs h = a;
+        h.n_in = 1;
+        h.H_in = H;
+        h.ldh_in = K;
+        h.H_out = H;
+        h.ldh = K;
+        h.loss_first = (it > 0 && obj_out) ? 1 : 0;
+        h.final_pass = 0;
+        h.loss_part = h.loss_first ? lp : nullptr;
+        if (e == cudaSuccess) e = launch_tiles(h, prec, tgrid, tsm, q);
+        if (e == cudaSuccess && h.loss_first) e = launch_sum(lp, ntiles, obj_d + it - 1, 0, q);
+        // P, Q, H rows from the updated H, then the W step
+        TileArgs r = a;
+        r.n_in = 0;
+        r.H_in = H;
+        r.ldh_in = K;
+        r.final_pass = 1;
+        r.Pg = Pg;
+        r.Qg = Qg;
+        r.Hg = Hg;
+        if (e == cudaSuccess) e = launch_tiles(r, prec, tgrid, tsm, q);
+        if (e == cudaSuccess)
+            e = launch_batch_stats(sh, prec, Pg, Qg, Hg, betap, N, nchunks, part,
+                                   std::min(units * nchunks, 2 * nsm), q);
+        if (e == cudaSuccess) e = launch_batch_wstep(sh, part, nchunks, W, q);
+        if (e == cudaSuccess) e = launch_batch_normalize(sh, normalize, W, scale, err, q);
+        if (e == cudaSuccess) e = launch_batch_scale_h(K, N, H, scale, q);
+    }
+    if (e == cudaSuccess && obj_out) {
+        // objective of the final iterate
+        e = launch_prepare(sh, W, Wrm, Wimg, swp, q);
+        TileArgs o = a;
+        o.n_in = 0;
+        o.H_in = H;
+        o.ldh_in = K;
+        o.final_pass = 1;
+        o.loss_part = lp;
+        if (e == cudaSuccess) e = launch_tiles(o, prec, tgrid, tsm, q);
+        if (e == cudaSuccess) e = launch_sum(lp, ntiles, obj_d + n_iter - 1, 0, q);
+    }
+    int errh = 0;
+    if (e == cudaSuccess && obj_out) {
+        std::vector<double> o(n_iter);
+        e = cudaMemcpyAsync(o.data(), obj_d, (size_t)n_iter * 8, cudaMemcpyDeviceToHost, q);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&errh, err, 4, cudaMemcpyDeviceToHost, q);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(q);
+        for (int i = 0; i < n_iter; ++i) obj_out[i] = o[i] / (double)N;
+    }
+    cleanup();
+    if (e != cudaSuccess) {
+        set_msg("nmf_batch_step", e);
+        return ONMF_ECUDA;
+    }
+    return errh ? status_from_err(errh) : ONMF_OK;
+}
+
+}  // extern "C"

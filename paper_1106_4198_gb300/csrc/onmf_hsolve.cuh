@@ -1,0 +1,543 @@
+// The per-tile h-solve of Algorithm 1 (arXiv:1106.4198, Section 2.3):
+// for kTile frames at a time and W fixed, run n_in majorization-minimization
+// steps  x = eps + W h,  p = y/x^2,  q = 1/x,  h <- h * ((W^T p)/(W^T q))^gamma
+// from the fresh-restart point h0 = sum_f y_f / sum_{f,k} W_fk (or from a
+// given H for the batch H step), then one more x = eps + W h for the
+// statistics and the loss. Two implementations share the interface:
+//   hsolve_tile_fp32   FP32 SIMT (the plain form),
+//   hsolve_tile_mixed  BF16 tensor cores (mma.sync m16n8k16, FP32 accumulate)
+//                      with W^T resident in shared memory (bulk-copied) and
+//                      the frame tile staged by a bulk copy; the ratios y/x^2
+//                      and 1/x stay FP32 and are rounded to BF16 only as the
+//                      operand of the W^T product.
+#pragma once
+
+#include "onmf_device.cuh"
+#include "onmf_kernels.cuh"
+
+namespace onmf {
+
+// Everything one tile needs besides the shape and W.
+struct TileJob {
+    const float *Vt;  // first frame of the tile
+    long long ldv;
+    int nvalid;        // frames of the tile that exist (1..kTile)
+    long long j0;      // index of the tile's first frame in Pg/Qg/Hg/H_out/H_in
+    const float *H_in; // warm start (K x frames, ld ldh_in) or NULL
+    long long ldh_in;
+    float *H_out;      // K x frames (ldh) or NULL
+    long long ldh;
+    int n_in;
+    int loss_first;
+    int final_pass;
+    double *loss_slot;  // receives the tile's loss (or NULL)
+    void *Pg, *Qg, *Hg;
+    long long betap;
+};
+
+__device__ __forceinline__ float pow_gamma(float r, float gamma) {
+    if (gamma == 0.5f) return sqrtf(r);
+    if (gamma == 1.0f) return r;
+    return powf(r, gamma);
+}
+
+__device__ __forceinline__ bool bad_value(float v) { return !(v >= 0.f) || isinf(v); }
+
+// Sum of the K column sums of the normalized W (the denominator of h0).
+__device__ __forceinline__ float sum_w(const float *swpart, int K, float *s_tmp) {
+    if (threadIdx.x < 32) {
+        float a = 0.f;
+        for (int k = threadIdx.x; k < K; k += 32) a += swpart[k];
+        a = warp_sum(a);
+        if (threadIdx.x == 0) *s_tmp = a;
+    }
+    __syncthreads();
+    float r = *s_tmp;
+    return r;
+}
+
+// ------------------------------------------------------------------ FP32
+
+// Shared memory of the FP32 h-solve, in floats.
+__host__ __device__ inline size_t hsolve_fp32_smem_bytes(const Shape &s) {
+    size_t fl = 3ull * s.F * kTile + (size_t)s.Kh * kTile + (size_t)kWarps * 128 * 16 + 64;
+    return fl * sizeof(float);
+}
+
+__device__ void hsolve_tile_fp32(const Shape &s, float eps, float gamma, const float *Wcm,
+                                 const float *Wrm, float sw, const TileJob &t,
+                                 unsigned char *smem, int *err) {
+    const int F = s.F, K = s.K, Kh = s.Kh;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *y_s = reinterpret_cast<float *>(smem);  // [F][8]
+    float *p_s = y_s + (size_t)F * kTile;          // [F][8]
+    float *q_s = p_s + (size_t)F * kTile;          // [F][8]
+    float *h_s = q_s + (size_t)F * kTile;          // [Kh][8]
+    float *red = h_s + (size_t)Kh * kTile;         // [8][128][16]
+    float *misc = red + kWarps * 128 * 16;         // sy[8], lw[8]
+    float *sy = misc, *lw = misc + 8;
+
+    // frame tile -> y = eps + v (y = 1 in frames past the end of the data)
+    for (int i = tid; i < kTile * F; i += kThreads) {
+        int j = i / F, f = i - j * F;
+        float y = 1.f;
+        if (j < t.nvalid) {
+            float v = __ldg(t.Vt + (long long)j * t.ldv + f);
+            if (bad_value(v)) flag_error(err, ERR_INPUT);
+            y = eps + v;
+        }
+        y_s[f * kTile + j] = y;
+    }
+    __syncthreads();
+    if (t.H_in) {
+        for (int i = tid; i < Kh * kTile; i += kThreads) {
+            int k = i / kTile, j = i % kTile;
+            h_s[i] = (k < K && j < t.nvalid) ? t.H_in[(t.j0 + j) * t.ldh_in + k] : 0.f;
+        }
+    } else {
+        // h0 = sum_f y_f / sum W for every k (fresh restart)
+        float a = 0.f;
+        for (int f = lane; f < F; f += 32) a += y_s[f * kTile + warp];
+        a = warp_sum(a);
+        if (lane == 0) sy[warp] = a;
+        __syncthreads();
+        for (int i = tid; i < Kh * kTile; i += kThreads) {
+            int k = i / kTile, j = i % kTile;
+            h_s[i] = (k < K) ? sy[j] / sw : 0.f;
+        }
+    }
+    __syncthreads();
+
+    float lacc = 0.f;
+    const int mainF = (F / kThreads) * kThreads;
+    for (int it = 0;; ++it) {
+        const bool last = (it == t.n_in);
+        if (last && !t.final_pass) break;
+        const bool want_loss = (last && t.final_pass) || (it == 0 && t.loss_first);
+        auto finish_row = [&](int f, const float (&acc)[kTile]) {
+            float4 ya = *reinterpret_cast<const float4 *>(y_s + f * kTile);
+            float4 yb = *reinterpret_cast<const float4 *>(y_s + f * kTile + 4);
+            float ys[kTile] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
+            float pv[kTile], qv[kTile];
+#pragma unroll
+            for (int j = 0; j < kTile; ++j) {
+                float x = eps + acc[j];
+                float q = __frcp_rn(x);
+                qv[j] = q;
+                pv[j] = ys[j] * q * q;
+                if (want_loss && j < t.nvalid) {
+                    float r = ys[j] * q;
+                    lacc += (r - 1.f) - logf(r);
+                }
+            }
+            *reinterpret_cast<float4 *>(p_s + f * kTile) = make_float4(pv[0], pv[1], pv[2], pv[3]);
+            *reinterpret_cast<float4 *>(p_s + f * kTile + 4) = make_float4(pv[4], pv[5], pv[6], pv[7]);
+            *reinterpret_cast<float4 *>(q_s + f * kTile) = make_float4(qv[0], qv[1], qv[2], qv[3]);
+            *reinterpret_cast<float4 *>(q_s + f * kTile + 4) = make_float4(qv[4], qv[5], qv[6], qv[7]);
+        };
+        // x = eps + W h: rows [0, mainF) one per thread, the rest split over k by warps
+        for (int f = tid; f < mainF; f += kThreads) {
+            float acc[kTile];
+#pragma unroll
+            for (int j = 0; j < kTile; ++j) acc[j] = 0.f;
+            const float *wc = Wcm + f;
+#pragma unroll 4
+            for (int k = 0; k < K; ++k) {
+                float w = wc[(long long)k * F];
+                float4 ha = *reinterpret_cast<const float4 *>(h_s + k * kTile);
+                float4 hb = *reinterpret_cast<const float4 *>(h_s + k * kTile + 4);
+                acc[0] = fmaf(w, ha.x, acc[0]);
+                acc[1] = fmaf(w, ha.y, acc[1]);
+                acc[2] = fmaf(w, ha.z, acc[2]);
+                acc[3] = fmaf(w, ha.w, acc[3]);
+                acc[4] = fmaf(w, hb.x, acc[4]);
+                acc[5] = fmaf(w, hb.y, acc[5]);
+                acc[6] = fmaf(w, hb.z, acc[6]);
+                acc[7] = fmaf(w, hb.w, acc[7]);
+            }
+            finish_row(f, acc);
+        }
+        for (int f = mainF + warp; f < F; f += kWarps) {
+            float acc[kTile];
+#pragma unroll
+            for (int j = 0; j < kTile; ++j) acc[j] = 0.f;
+            for (int k = lane; k < K; k += 32) {
+                float w = Wcm[f + (long long)k * F];
+#pragma unroll
+                for (int j = 0; j < kTile; ++j) acc[j] = fmaf(w, h_s[k * kTile + j], acc[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < kTile; ++j) acc[j] = warp_sum(acc[j]);
+            if (lane == 0) finish_row(f, acc);
+        }
+        __syncthreads();
+        if (last) break;
+
+        // W^T p and W^T q: lanes take k, warps take contiguous row ranges
+        const int fper = (F + kWarps - 1) / kWarps;
+        const int f_lo = warp * fper, f_hi = min(F, f_lo + fper);
+        for (int k0 = 0; k0 < K; k0 += 128) {
+            float nm[4][kTile], dn[4][kTile];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < kTile; ++j) nm[i][j] = dn[i][j] = 0.f;
+            for (int f = f_lo; f < f_hi; ++f) {
+                float4 pa = *reinterpret_cast<const float4 *>(p_s + f * kTile);
+                float4 pb = *reinterpret_cast<const float4 *>(p_s + f * kTile + 4);
+                float4 qa = *reinterpret_cast<const float4 *>(q_s + f * kTile);
+                float4 qb = *reinterpret_cast<const float4 *>(q_s + f * kTile + 4);
+                float pv[kTile] = {pa.x, pa.y, pa.z, pa.w, pb.x, pb.y, pb.z, pb.w};
+                float qv[kTile] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    int k = k0 + lane + 32 * i;
+                    float w = (k < K) ? Wrm[(long long)f * K + k] : 0.f;
+#pragma unroll
+                    for (int j = 0; j < kTile; ++j) {
+                        nm[i][j] = fmaf(w, pv[j], nm[i][j]);
+                        dn[i][j] = fmaf(w, qv[j], dn[i][j]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float *r = red + ((size_t)warp * 128 + lane + 32 * i) * 16;
+#pragma unroll
+                for (int j = 0; j < kTile; j += 4) {
+                    *reinterpret_cast<float4 *>(r + j) =
+                        make_float4(nm[i][j], nm[i][j + 1], nm[i][j + 2], nm[i][j + 3]);
+                    *reinterpret_cast<float4 *>(r + 8 + j) =
+                        make_float4(dn[i][j], dn[i][j + 1], dn[i][j + 2], dn[i][j + 3]);
+                }
+            }
+            __syncthreads();
+            for (int e = tid; e < 128 * kTile; e += kThreads) {
+                int kk = e / kTile, j = e % kTile, k = k0 + kk;
+                if (k < K) {
+                    float num = 0.f, den = 0.f;
+#pragma unroll
+                    for (int w = 0; w < kWarps; ++w) {
+                        num += red[((size_t)w * 128 + kk) * 16 + j];
+                        den += red[((size_t)w * 128 + kk) * 16 + 8 + j];
+                    }
+                    float h = h_s[k * kTile + j];
+                    if (den > 0.f) h = h * pow_gamma(__fdiv_rn(num, den), gamma);
+                    h_s[k * kTile + j] = h;
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // outputs
+    if (t.final_pass) {
+        float *Pg = reinterpret_cast<float *>(t.Pg);
+        float *Qg = reinterpret_cast<float *>(t.Qg);
+        float *Hg = reinterpret_cast<float *>(t.Hg);
+        const int Fp = s.Fp16;
+        if (Pg) {
+            for (int i = tid; i < kTile * Fp; i += kThreads) {
+                int j = i / Fp, f = i - j * Fp;
+                bool ok = j < t.nvalid && f < F;
+                long long o = (t.j0 + j) * Fp + f;
+                Pg[o] = ok ? p_s[f * kTile + j] : 0.f;
+                Qg[o] = ok ? q_s[f * kTile + j] : 0.f;
+            }
+            for (int i = tid; i < kTile * Kh; i += kThreads) {
+                int j = i / Kh, k = i - j * Kh;
+                Hg[(t.j0 + j) * Kh + k] = (j < t.nvalid) ? h_s[k * kTile + j] : 0.f;
+            }
+        }
+    }
+    if (t.H_out) {
+        for (int i = tid; i < t.nvalid * K; i += kThreads) {
+            int j = i / K, k = i - j * K;
+            t.H_out[(t.j0 + j) * t.ldh + k] = h_s[k * kTile + j];
+        }
+    }
+    if (t.loss_slot) {
+        float l = warp_sum(lacc);
+        if (lane == 0) lw[warp] = l;
+        __syncthreads();
+        if (tid == 0) {
+            double d = 0.0;
+            for (int w = 0; w < kWarps; ++w) d += (double)lw[w];
+            *t.loss_slot = d;
+        }
+    }
+    __syncthreads();
+}
+
+// ----------------------------------------------------------------- MIXED
+
+struct MixedLayout {
+    size_t w, pq, h, y, misc, total;  // byte offsets
+    int HLD;
+};
+
+__host__ __device__ inline MixedLayout mixed_layout(const Shape &s) {
+    MixedLayout L;
+    L.HLD = s.Kp + 8;
+    size_t o = 0;
+    L.w = o;
+    o += (size_t)s.Kp * s.WLD * 2;
+    o = (o + 127) / 128 * 128;
+    L.pq = o;
+    o += (size_t)16 * s.WLD * 2;
+    o = (o + 127) / 128 * 128;
+    L.h = o;
+    o += (size_t)kTile * L.HLD * 2;
+    o = (o + 127) / 128 * 128;
+    L.y = o;
+    o += (size_t)kTile * s.F * 4;
+    o = (o + 127) / 128 * 128;
+    L.misc = o;
+    o += 256;
+    L.total = o;
+    return L;
+}
+
+// Stage W^T (bf16 image) into shared memory with one bulk copy.
+__device__ __forceinline__ bool stage_wimg(const Shape &s, const __nv_bfloat16 *Wimg,
+                                           unsigned char *smem, uint64_t *bar, unsigned &parity,
+                                           int *err) {
+    const MixedLayout L = mixed_layout(s);
+    const unsigned bytes = (unsigned)((size_t)s.Kp * s.WLD * 2);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        fence_proxy_async_shared();
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(smem + L.w, Wimg, bytes, bar);
+    }
+    bool ok = mbar_wait_bounded(bar, parity, err);
+    parity ^= 1u;
+    return ok;
+}
+
+// The tensor-core h-solve of one tile. W^T must already be in shared memory
+// (stage_wimg). Warps 0..Kp/16-1 own the h values of one 16-wide k slab each
+// (FP32 in registers); all warps share the x = eps + W h product.
+__device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma, float sw,
+                                  const TileJob &t, unsigned char *smem, uint64_t *vbar,
+                                  unsigned &vparity, int *err) {
+    const int F = s.F, K = s.K, Kp = s.Kp, WLD = s.WLD, Fp = s.Fp16;
+    const MixedLayout L = mixed_layout(s);
+    const int HLD = L.HLD;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, tq = lane & 3;
+    const int mi = lane >> 3, r8 = lane & 7;
+    __nv_bfloat16 *W_s = reinterpret_cast<__nv_bfloat16 *>(smem + L.w);
+    __nv_bfloat16 *PQ_s = reinterpret_cast<__nv_bfloat16 *>(smem + L.pq);
+    __nv_bfloat16 *H_s = reinterpret_cast<__nv_bfloat16 *>(smem + L.h);
+    float *y_s = reinterpret_cast<float *>(smem + L.y);  // [8][F] raw v
+    float *misc = reinterpret_cast<float *>(smem + L.misc);
+    float *sy = misc, *lw = misc + 8;
+    const int KS = Kp / 16;  // k16 steps
+    const int FT = Fp / 16;  // f16 tiles
+
+    // ---- frame tile -> shared memory (bulk copy when contiguous and aligned)
+    {
+        const size_t bytes = (size_t)t.nvalid * F * 4;
+        const bool bulk = (t.ldv == F) && ((reinterpret_cast<uintptr_t>(t.Vt) & 15) == 0) &&
+                          (bytes % 16 == 0);
+        __syncthreads();
+        if (bulk) {
+            if (tid == 0) {
+                fence_proxy_async_shared();
+                mbar_arrive_expect_tx(vbar, (unsigned)bytes);
+                bulk_g2s(y_s, t.Vt, (unsigned)bytes, vbar);
+            }
+            mbar_wait_bounded(vbar, vparity, err);
+            vparity ^= 1u;
+        } else {
+            for (int i = tid; i < t.nvalid * F; i += kThreads) {
+                int j = i / F, f = i - j * F;
+                y_s[i] = __ldg(t.Vt + (long long)j * t.ldv + f);
+            }
+            __syncthreads();
+        }
+    }
+    // frame sums (warp j sums frame j) and the input check
+    {
+        float a = 0.f;
+        if (warp < t.nvalid) {
+            for (int f = lane; f < F; f += 32) {
+                float v = y_s[warp * F + f];
+                if (bad_value(v)) flag_error(err, ERR_INPUT);
+                a += eps + v;
+            }
+        } else {
+            a = (float)F;  // placeholder frames: y = 1
+        }
+        a = warp_sum(a);
+        if (lane == 0) sy[warp] = a;
+    }
+    __syncthreads();
+
+    // ---- h in registers: warp w < KS owns k = 16w + {2tq, 2tq+1, 8+2tq, 9+2tq}, frame g
+    float hr[4];
+    const bool hown = warp < KS;
+    if (hown) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            int k = 16 * warp + 2 * tq + (e & 1) + 8 * (e >> 1);
+            float h = 0.f;
+            if (k < K) {
+                if (t.H_in)
+                    h = (g < t.nvalid) ? t.H_in[(t.j0 + g) * t.ldh_in + k] : 0.f;
+                else
+                    h = sy[g] / sw;
+            }
+            hr[e] = h;
+        }
+        *reinterpret_cast<uint32_t *>(H_s + g * HLD + 16 * warp + 2 * tq) = pack_bf16(hr[0], hr[1]);
+        *reinterpret_cast<uint32_t *>(H_s + g * HLD + 16 * warp + 8 + 2 * tq) =
+            pack_bf16(hr[2], hr[3]);
+    }
+    __syncthreads();
+
+    float lacc = 0.f;
+    for (int it = 0;; ++it) {
+        const bool last = (it == t.n_in);
+        if (last && !t.final_pass) break;
+        const bool want_loss = (last && t.final_pass) || (it == 0 && t.loss_first);
+        // ---- x = eps + W h on tensor cores; p, q -> PQ_s (bf16)
+        for (int mt = warp; mt < FT; mt += kWarps) {
+            const int f0 = 16 * mt;
+            float d[4] = {eps, eps, eps, eps};
+            for (int ks = 0; ks < KS; ++ks) {
+                uint32_t a[4];
+                const int krow = 16 * ks + r8 + 8 * (mi >> 1);
+                const int fcol = f0 + 8 * (mi & 1);
+                ldmatrix_x4_trans(a, W_s + krow * WLD + fcol);
+                uint32_t b0 = *reinterpret_cast<const uint32_t *>(H_s + g * HLD + 16 * ks + 2 * tq);
+                uint32_t b1 =
+                    *reinterpret_cast<const uint32_t *>(H_s + g * HLD + 16 * ks + 8 + 2 * tq);
+                mma_bf16_16816(d, a, b0, b1);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int f = f0 + g + 8 * (e >> 1);
+                const int j = 2 * tq + (e & 1);
+                float p = 0.f, q = 0.f;
+                if (f < F) {
+                    const bool vj = j < t.nvalid;
+                    const float y = vj ? eps + y_s[j * F + f] : 1.f;
+                    q = __frcp_rn(d[e]);
+                    p = y * q * q;
+                    if (want_loss && vj) {
+                        float r = y * q;
+                        lacc += (r - 1.f) - logf(r);
+                    }
+                }
+                PQ_s[j * WLD + f] = __float2bfloat16_rn(p);
+                PQ_s[(8 + j) * WLD + f] = __float2bfloat16_rn(q);
+            }
+        }
+        __syncthreads();
+        if (last) break;
+
+        // ---- [W^T p | W^T q] on tensor cores; h update in registers
+        if (hown) {
+            float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
+            float e0[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f};
+            const __nv_bfloat16 *wr0 = W_s + (16 * warp + g) * WLD + 2 * tq;
+            const __nv_bfloat16 *wr1 = W_s + (16 * warp + 8 + g) * WLD + 2 * tq;
+            const __nv_bfloat16 *arow = PQ_s + (r8 + 8 * (mi & 1)) * WLD + 8 * (mi >> 1);
+            int fs = 0;
+            for (; fs + 1 < FT; fs += 2) {
+                uint32_t a[4], c[4];
+                ldmatrix_x4(a, arow + 16 * fs);
+                ldmatrix_x4(c, arow + 16 * (fs + 1));
+                const int fa = 16 * fs, fb = 16 * (fs + 1);
+                mma_bf16_16816(d0, a, *reinterpret_cast<const uint32_t *>(wr0 + fa),
+                               *reinterpret_cast<const uint32_t *>(wr0 + fa + 8));
+                mma_bf16_16816(d1, a, *reinterpret_cast<const uint32_t *>(wr1 + fa),
+                               *reinterpret_cast<const uint32_t *>(wr1 + fa + 8));
+                mma_bf16_16816(e0, c, *reinterpret_cast<const uint32_t *>(wr0 + fb),
+                               *reinterpret_cast<const uint32_t *>(wr0 + fb + 8));
+                mma_bf16_16816(e1, c, *reinterpret_cast<const uint32_t *>(wr1 + fb),
+                               *reinterpret_cast<const uint32_t *>(wr1 + fb + 8));
+            }
+            if (fs < FT) {
+                uint32_t a[4];
+                ldmatrix_x4(a, arow + 16 * fs);
+                const int fa = 16 * fs;
+                mma_bf16_16816(d0, a, *reinterpret_cast<const uint32_t *>(wr0 + fa),
+                               *reinterpret_cast<const uint32_t *>(wr0 + fa + 8));
+                mma_bf16_16816(d1, a, *reinterpret_cast<const uint32_t *>(wr1 + fa),
+                               *reinterpret_cast<const uint32_t *>(wr1 + fa + 8));
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                d0[e] += e0[e];
+                d1[e] += e1[e];
+            }
+            // d[0..1] = (W^T p)[k, k+1] of frame g, d[2..3] = (W^T q)[k, k+1]
+            float num[4] = {d0[0], d0[1], d1[0], d1[1]};
+            float den[4] = {d0[2], d0[3], d1[2], d1[3]};
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (den[e] > 0.f) hr[e] = hr[e] * pow_gamma(__fdiv_rn(num[e], den[e]), gamma);
+            *reinterpret_cast<uint32_t *>(H_s + g * HLD + 16 * warp + 2 * tq) =
+                pack_bf16(hr[0], hr[1]);
+            *reinterpret_cast<uint32_t *>(H_s + g * HLD + 16 * warp + 8 + 2 * tq) =
+                pack_bf16(hr[2], hr[3]);
+        }
+        __syncthreads();
+    }
+
+    // ---- outputs
+    if (t.final_pass && t.Pg) {
+        __nv_bfloat16 *Pg = reinterpret_cast<__nv_bfloat16 *>(t.Pg);
+        __nv_bfloat16 *Qg = reinterpret_cast<__nv_bfloat16 *>(t.Qg);
+        __nv_bfloat16 *Hg = reinterpret_cast<__nv_bfloat16 *>(t.Hg);
+        const int cpr = Fp / 8;  // 16-byte chunks per row
+        for (int i = tid; i < kTile * cpr * 2; i += kThreads) {
+            const int which = i / (kTile * cpr);
+            const int rem = i - which * kTile * cpr;
+            const int j = rem / cpr, c = rem - j * cpr;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (j < t.nvalid) v = *reinterpret_cast<const uint4 *>(PQ_s + (which * 8 + j) * WLD + 8 * c);
+            __nv_bfloat16 *dst = (which ? Qg : Pg) + (t.j0 + j) * Fp + 8 * c;
+            *reinterpret_cast<uint4 *>(dst) = v;
+        }
+        for (int k = tid; k < Kp; k += kThreads) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = 2 * e;
+                __nv_bfloat16 a = (j < t.nvalid) ? H_s[j * HLD + k] : __float2bfloat16_rn(0.f);
+                __nv_bfloat16 b = (j + 1 < t.nvalid) ? H_s[(j + 1) * HLD + k] : __float2bfloat16_rn(0.f);
+                __nv_bfloat162 pr;
+                pr.x = a;
+                pr.y = b;
+                w[e] = *reinterpret_cast<uint32_t *>(&pr);
+            }
+            *reinterpret_cast<uint4 *>(Hg + (long long)k * t.betap + t.j0) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    }
+    if (t.H_out && hown && g < t.nvalid) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            int k = 16 * warp + 2 * tq + (e & 1) + 8 * (e >> 1);
+            if (k < K) t.H_out[(t.j0 + g) * t.ldh + k] = hr[e];
+        }
+    }
+    if (t.loss_slot) {
+        float l = warp_sum(lacc);
+        if (lane == 0) lw[warp] = l;
+        __syncthreads();
+        if (tid == 0) {
+            double dsum = 0.0;
+            for (int w = 0; w < kWarps; ++w) dsum += (double)lw[w];
+            *t.loss_slot = dsum;
+        }
+    }
+    __syncthreads();
+}
+
+}  // namespace onmf

@@ -1,0 +1,105 @@
+// Kernel-side data structures of libonmf (shared by the kernels and the
+// host code that launches them). Layouts in HBM:
+//
+//   V     F x n  float, column (frame) major, leading dimension ldv.
+//   Wcm   F x K  float, column-major: the dictionary W (state).
+//   Wrm   F x K  float, row-major copy of W (FP32 path, K-contiguous rows).
+//   Wimg  Kp x WLD bf16: W^T padded for the tensor-core path; row k holds
+//         column k of W (F values, zero padded to WLD = Fp16 + 8). The +8
+//         makes 8 consecutive rows fall in distinct shared-memory banks.
+//   A, B  F x K  double, column-major: the sufficient statistics (Eq. aux_fun).
+//   Pg,Qg betap x Fp16: per-frame rows of P = Y/X^2 and Q = 1/X of the
+//         current minibatch (float on the FP32 path, bf16 on the mixed path).
+//   Hg    FP32 path: betap x Kh float (frame rows); mixed path: Kh x betap
+//         bf16 (k rows, frames contiguous).
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+
+namespace onmf {
+
+constexpr int kThreads = 256;  // threads per CTA for every kernel here
+constexpr int kWarps = kThreads / 32;
+constexpr int kTile = 8;       // frames per h-solve tile
+
+enum Prec : int { PREC_FP32 = 0, PREC_MIXED = 1 };
+
+struct Shape {
+    int F, K;
+    int Fp16;  // F rounded up to 16
+    int Kp;    // K rounded up to 16
+    int Kh;    // K rounded up to 32 (statistics k-slabs, ld of Hg on FP32)
+    int WLD;   // row stride of Wimg (Fp16 + 8)
+};
+
+inline Shape make_shape(int F, int K) {
+    Shape s;
+    s.F = F;
+    s.K = K;
+    s.Fp16 = (F + 15) / 16 * 16;
+    s.Kp = (K + 15) / 16 * 16;
+    s.Kh = (K + 31) / 32 * 32;
+    s.WLD = s.Fp16 + 8;
+    return s;
+}
+
+// Arguments of the online step kernel (one launch = nmb minibatches).
+struct StepArgs {
+    Shape s;
+    float eps;
+    float gamma;
+    int n_in;
+    int normalize;
+    int rho_on_new;
+    // frames
+    const float *V;
+    long long ldv;
+    int nmb;      // minibatches in this launch
+    int beta;     // frames per full minibatch
+    int nb_last;  // frames in the last minibatch (<= beta)
+    double rho_full, rho_last;
+    float *H_out;  // optional K x frames (ldh)
+    long long ldh;
+    // state
+    float *Wcm;
+    float *Wrm;
+    __nv_bfloat16 *Wimg;
+    float *Wn;
+    double *A, *B;
+    double *loss_sum;
+    float *swpart;  // [K] column sums of the normalized W
+    // scratch
+    void *Pg, *Qg, *Hg;
+    int betap;  // rows of Pg/Qg (and columns of the bf16 Hg)
+    double *loss_part;
+    unsigned *bar;
+    int *err;
+};
+
+// Arguments of the projection / batch h-step kernels (no state update).
+struct TileArgs {
+    Shape s;
+    float eps;
+    float gamma;
+    int n_in;
+    const float *V;
+    long long ldv;
+    long long n;          // frames
+    const float *H_in;    // warm start (K x n, ld ldh_in) or NULL = fresh restart
+    long long ldh_in;
+    float *H_out;         // K x n (ldh) or NULL
+    long long ldh;
+    int loss_first;       // loss of the first X (before any h update)
+    int final_pass;       // compute X from the final h: loss, P/Q/Hg rows
+    const float *Wcm;
+    const float *Wrm;
+    const __nv_bfloat16 *Wimg;
+    const float *swpart;
+    void *Pg, *Qg, *Hg;
+    long long betap;
+    double *loss_part;    // [tiles] or NULL
+    int *err;
+};
+
+}  // namespace onmf

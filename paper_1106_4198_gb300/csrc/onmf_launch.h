@@ -1,0 +1,38 @@
+// Host-side launchers of the libonmf kernels (C++ linkage, internal).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "onmf_kernels.cuh"
+
+namespace onmf {
+
+int64_t kernel_launches();
+cudaError_t configure_kernels();
+size_t online_smem_bytes(const Shape &s, int prec);
+size_t tile_smem_bytes(const Shape &s, int prec);
+size_t batch_stats_smem_bytes(int prec);
+cudaError_t max_coresident_blocks(int prec, size_t smem, int *blocks_per_sm);
+
+cudaError_t launch_online(const StepArgs &a, int prec, int grid, size_t smem, cudaStream_t stream);
+cudaError_t launch_tiles(const TileArgs &a, int prec, int grid, size_t smem, cudaStream_t stream);
+cudaError_t launch_prepare(const Shape &s, const float *Wcm, float *Wrm, __nv_bfloat16 *Wimg,
+                           float *swpart, cudaStream_t stream);
+cudaError_t launch_sum(const double *x, long long n, double *out, int accumulate,
+                       cudaStream_t stream);
+cudaError_t launch_batch_stats(const Shape &s, int prec, const void *Pg, const void *Qg,
+                               const void *Hg, long long betap, long long N, int nchunks,
+                               float *part, int grid, cudaStream_t stream);
+cudaError_t launch_batch_wstep(const Shape &s, const float *part, int nchunks, float *W,
+                               cudaStream_t stream);
+cudaError_t launch_batch_normalize(const Shape &s, int normalize, float *W, float *scale, int *err,
+                                   cudaStream_t stream);
+cudaError_t launch_batch_scale_h(int K, long long N, float *H, const float *scale,
+                                 cudaStream_t stream);
+cudaError_t launch_batch_h0(const Shape &s, const float *V, long long ldv, long long N, float eps,
+                            const float *swpart, float *H, cudaStream_t stream);
+
+}  // namespace onmf

@@ -1,0 +1,82 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for
+sm_103a, loads, exports every function include/onmf.h declares, and rejects
+invalid configurations before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1106_4198_gb300 as onmf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "onmf.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b([A-Za-z_][A-Za-z0-9_]*)\s*\(", text)
+    return sorted({n for n in names if n.startswith(("onmf_", "nmf_"))})
+
+
+def test_header_and_binding_agree():
+    decl = set(declared_functions())
+    assert decl == set(onmf.EXPORTED), decl ^ set(onmf.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol():
+    L = onmf.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_config_layout_and_defaults():
+    assert ctypes.sizeof(onmf.onmf_config) == 64
+    c = onmf.onmf_config_default(513, 100)
+    assert (c.F, c.K, c.beta, c.n_inner) == (513, 100, 1000, 10)
+    assert c.eps == 1e-12 and c.r == 1.0 and c.n_ref == 0
+    assert c.h_exponent == 0.5 and c.normalize == 1 and c.rho_on_new == 0
+    assert c.precision == onmf.ONMF_FP32
+    assert onmf.onmf_abi_version() == 1
+
+
+def test_status_strings():
+    for st in range(9):
+        assert onmf.onmf_status_string(st).startswith("ONMF_")
+
+
+@pytest.mark.parametrize("field,value", [
+    ("F", 0), ("K", 0), ("K", 257), ("beta", 0), ("n_inner", -1),
+    ("eps", -1.0), ("r", 1.5), ("h_exponent", 0.0), ("precision", 7),
+    ("reserved", 1),
+])
+def test_invalid_config_rejected_on_host(field, value):
+    import numpy as np
+    c = onmf.onmf_config_default(16, 4)
+    setattr(c, field, value)
+    W0 = np.ones((4, 16), dtype=np.float32) / 16
+    h = ctypes.c_void_p()
+    st = onmf.lib().onmf_init(ctypes.byref(c), W0.ctypes.data, 0, None,
+                              ctypes.byref(h))
+    assert st == 1  # ONMF_EINVAL
+    assert not h.value
+
+
+def test_mixed_precision_k_limit():
+    import numpy as np
+    c = onmf.onmf_config_default(16, 200, precision=onmf.ONMF_MIXED)
+    W0 = np.ones((200, 16), dtype=np.float32) / 16
+    h = ctypes.c_void_p()
+    st = onmf.lib().onmf_init(ctypes.byref(c), W0.ctypes.data, 0, None,
+                              ctypes.byref(h))
+    assert st == 1
+
+
+def test_null_arguments_rejected():
+    L = onmf.lib()
+    assert L.onmf_push_frames(None, None, 0, 0, None, 0) == 1
+    assert L.onmf_flush(None) == 1
+    assert L.onmf_get_W(None, None, 0) == 1
+    assert L.nmf_batch_step(None, 0, None, None, 1, 1, 1, 0.0, 0.5, 1, 1, 0,
+                            None, None) == 1
