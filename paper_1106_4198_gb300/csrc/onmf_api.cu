@@ -8,7 +8,7 @@
 #include <cstring>
 #include <vector>
 
-#include "../../include/onmf.h"
+#include "onmf.h"
 #include "onmf_device.cuh"
 #include "onmf_kernels.cuh"
 #include "onmf_launch.h"
@@ -198,8 +198,8 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
         !(c.r >= 0.0 && c.r <= 1.0) || !(c.h_exponent > 0.0) || c.reserved != 0 ||
         (c.precision != ONMF_FP32 && c.precision != ONMF_MIXED))
         return ONMF_EINVAL;
-    if (c.precision == ONMF_MIXED && c.K > 128) {
-        snprintf(g_msg, sizeof g_msg, "mixed precision supports K <= 128");
+    if (c.precision == ONMF_MIXED && (c.K > 128 || c.F > 1024)) {
+        snprintf(g_msg, sizeof g_msg, "mixed precision supports K <= 128 and F <= 1024");
         return ONMF_EINVAL;
     }
     onmf_status st = ensure_configured();
@@ -274,12 +274,12 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
     cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
     s->smem = online_smem_bytes(sh, s->prec);
     s->tile_smem = tile_smem_bytes(sh, s->prec);
-    if (s->smem > 227 * 1024) {
-        snprintf(g_msg, sizeof g_msg, "shared memory need %zu exceeds 227 KB", s->smem);
+    if (s->smem > max_dynamic_smem()) {
+        snprintf(g_msg, sizeof g_msg, "shared memory need %zu exceeds the device limit", s->smem);
         return fail(ONMF_EINVAL);
     }
     int per_sm = 0;
-    if ((e = max_coresident_blocks(s->prec, s->smem, &per_sm)) != cudaSuccess || per_sm < 1) {
+    if ((e = max_coresident_blocks(s->prec, sh.Kp / 16, s->smem, &per_sm)) != cudaSuccess || per_sm < 1) {
         set_msg("occupancy", e);
         return fail(ONMF_ECUDA);
     }
@@ -599,7 +599,7 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
         n_iter < 0 || !(eps >= 0.0) || !(h_exponent > 0.0) ||
         (precision != ONMF_FP32 && precision != ONMF_MIXED))
         return ONMF_EINVAL;
-    if (precision == ONMF_MIXED && K > 128) return ONMF_EINVAL;
+    if (precision == ONMF_MIXED && (K > 128 || F > 1024)) return ONMF_EINVAL;
     onmf_status st = ensure_configured();
     if (st != ONMF_OK) return st;
     if (n_iter == 0) return ONMF_OK;

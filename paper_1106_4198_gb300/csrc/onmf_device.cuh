@@ -109,6 +109,25 @@ __device__ __forceinline__ void ldmatrix_x4_trans(uint32_t (&r)[4], const void *
                  : "r"(smem_u32(row_addr)));
 }
 
+// Store four 8x8 b16 matrices transposed: lane L supplies the row address of
+// row (L & 7) of matrix (L >> 3); register i holds this thread's pair
+// (row lane/4, columns 2*(lane%4), +1) of matrix i before transposition.
+__device__ __forceinline__ void stmatrix_x4_trans(void *row_addr, uint32_t r0, uint32_t r1,
+                                                  uint32_t r2, uint32_t r3) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.trans.shared.b16 [%0], {%1,%2,%3,%4};\n" ::"r"(
+                     smem_u32(row_addr)),
+                 "r"(r0), "r"(r1), "r"(r2), "r"(r3)
+                 : "memory");
+}
+
+// Approximate reciprocal (MUFU, about 1 ulp); used where the result is
+// rounded to BF16 afterwards.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // ------------------------------------------------------- async copies
 
 // 16-byte global->shared copy; src_bytes < 16 zero-fills the rest.

@@ -64,7 +64,7 @@ __host__ __device__ inline size_t hsolve_fp32_smem_bytes(const Shape &s) {
     return fl * sizeof(float);
 }
 
-__device__ void hsolve_tile_fp32(const Shape &s, float eps, float gamma, const float *Wcm,
+static __device__ void hsolve_tile_fp32(const Shape &s, float eps, float gamma, const float *Wcm,
                                  const float *Wrm, float sw, const TileJob &t,
                                  unsigned char *smem, int *err) {
     const int F = s.F, K = s.K, Kh = s.Kh;
@@ -271,8 +271,10 @@ __device__ void hsolve_tile_fp32(const Shape &s, float eps, float gamma, const f
 
 // ----------------------------------------------------------------- MIXED
 
+constexpr int kMtMax = 8;  // m16 row tiles of x = eps + W h per warp (F <= 1024)
+
 struct MixedLayout {
-    size_t w, pq, h, y, misc, total;  // byte offsets
+    size_t w, pq, h, yraw, yt, misc, total;  // byte offsets
     int HLD;
 };
 
@@ -289,8 +291,11 @@ __host__ __device__ inline MixedLayout mixed_layout(const Shape &s) {
     L.h = o;
     o += (size_t)kTile * L.HLD * 2;
     o = (o + 127) / 128 * 128;
-    L.y = o;
+    L.yraw = o;
     o += (size_t)kTile * s.F * 4;
+    o = (o + 127) / 128 * 128;
+    L.yt = o;
+    o += (size_t)s.Fp16 * kTile * 4;
     o = (o + 127) / 128 * 128;
     L.misc = o;
     o += 256;
@@ -298,10 +303,10 @@ __host__ __device__ inline MixedLayout mixed_layout(const Shape &s) {
     return L;
 }
 
-// Stage W^T (bf16 image) into shared memory with one bulk copy.
-__device__ __forceinline__ bool stage_wimg(const Shape &s, const __nv_bfloat16 *Wimg,
-                                           unsigned char *smem, uint64_t *bar, unsigned &parity,
-                                           int *err) {
+// Issue the bulk copy of W^T (bf16 image) into shared memory; the h-solve
+// waits for it (mbarrier `bar`) after issuing its own frame-tile copy.
+__device__ __forceinline__ void issue_wimg(const Shape &s, const __nv_bfloat16 *Wimg,
+                                           unsigned char *smem, uint64_t *bar) {
     const MixedLayout L = mixed_layout(s);
     const unsigned bytes = (unsigned)((size_t)s.Kp * s.WLD * 2);
     __syncthreads();
@@ -311,18 +316,30 @@ __device__ __forceinline__ bool stage_wimg(const Shape &s, const __nv_bfloat16 *
         mbar_arrive_expect_tx(bar, bytes);
         bulk_g2s(smem + L.w, Wimg, bytes, bar);
     }
-    bool ok = mbar_wait_bounded(bar, parity, err);
-    parity ^= 1u;
-    return ok;
 }
 
-// The tensor-core h-solve of one tile. W^T must already be in shared memory
-// (stage_wimg). Warps 0..Kp/16-1 own the h values of one 16-wide k slab each
-// (FP32 in registers); all warps share the x = eps + W h product.
-__device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma, float sw,
-                                  const TileJob &t, unsigned char *smem, uint64_t *vbar,
-                                  unsigned &vparity, int *err) {
-    const int F = s.F, K = s.K, Kp = s.Kp, WLD = s.WLD, Fp = s.Fp16;
+// Pending bulk copy of W^T that a tile must wait for before its first use.
+struct WStage {
+    uint64_t *bar;
+    unsigned *parity;
+    bool pending;
+};
+
+// The tensor-core h-solve of one tile (KS = Kp/16 k16 steps). W^T is in
+// shared memory as bf16 (row k = column k of W). Per iteration:
+//   step A  x = eps + W h: each warp owns m16 row tiles (interleaved
+//           accumulator chains over the KS k-steps), then p = y/x^2 and
+//           q = 1/x in FP32, rounded to bf16 and stored transposed with
+//           stmatrix as the 16 x Fp operand [P | Q]^T;
+//   step B  [W^T p | W^T q]: warp w < KS owns k in [16w, 16w+16) and all of
+//           F (4 interleaved chains per n-tile); the accumulator fragment
+//           holds (W^T p)_k and (W^T q)_k of the same (frame, k), so the h
+//           update happens in registers (FP32 master h).
+template <int KS>
+static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma, float sw,
+                                  const TileJob &t, unsigned char *smem, WStage &ws,
+                                  uint64_t *vbar, unsigned &vparity, int *err) {
+    const int F = s.F, K = s.K, WLD = s.WLD, Fp = s.Fp16;
     const MixedLayout L = mixed_layout(s);
     const int HLD = L.HLD;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -331,11 +348,11 @@ __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma, float 
     __nv_bfloat16 *W_s = reinterpret_cast<__nv_bfloat16 *>(smem + L.w);
     __nv_bfloat16 *PQ_s = reinterpret_cast<__nv_bfloat16 *>(smem + L.pq);
     __nv_bfloat16 *H_s = reinterpret_cast<__nv_bfloat16 *>(smem + L.h);
-    float *y_s = reinterpret_cast<float *>(smem + L.y);  // [8][F] raw v
+    float *y_raw = reinterpret_cast<float *>(smem + L.yraw);  // [8][F] raw v (bulk target)
+    float *yT = reinterpret_cast<float *>(smem + L.yt);       // [Fp][8] y = eps + v
     float *misc = reinterpret_cast<float *>(smem + L.misc);
     float *sy = misc, *lw = misc + 8;
-    const int KS = Kp / 16;  // k16 steps
-    const int FT = Fp / 16;  // f16 tiles
+    const int FT = Fp / 16;
 
     // ---- frame tile -> shared memory (bulk copy when contiguous and aligned)
     {
@@ -347,24 +364,31 @@ __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma, float 
             if (tid == 0) {
                 fence_proxy_async_shared();
                 mbar_arrive_expect_tx(vbar, (unsigned)bytes);
-                bulk_g2s(y_s, t.Vt, (unsigned)bytes, vbar);
+                bulk_g2s(y_raw, t.Vt, (unsigned)bytes, vbar);
             }
-            mbar_wait_bounded(vbar, vparity, err);
-            vparity ^= 1u;
         } else {
             for (int i = tid; i < t.nvalid * F; i += kThreads) {
                 int j = i / F, f = i - j * F;
-                y_s[i] = __ldg(t.Vt + (long long)j * t.ldv + f);
+                y_raw[i] = __ldg(t.Vt + (long long)j * t.ldv + f);
             }
-            __syncthreads();
         }
+        if (ws.pending) {
+            mbar_wait_bounded(ws.bar, *ws.parity, err);
+            *ws.parity ^= 1u;
+            ws.pending = false;
+        }
+        if (bulk) {
+            mbar_wait_bounded(vbar, vparity, err);
+            vparity ^= 1u;
+        }
+        __syncthreads();
     }
-    // frame sums (warp j sums frame j) and the input check
+    // frame sums and input check (warp j: frame j), f-major copy of y
     {
         float a = 0.f;
         if (warp < t.nvalid) {
             for (int f = lane; f < F; f += 32) {
-                float v = y_s[warp * F + f];
+                float v = y_raw[warp * F + f];
                 if (bad_value(v)) flag_error(err, ERR_INPUT);
                 a += eps + v;
             }
@@ -373,11 +397,15 @@ __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma, float 
         }
         a = warp_sum(a);
         if (lane == 0) sy[warp] = a;
+        for (int i = tid; i < Fp * kTile; i += kThreads) {
+            const int f = i >> 3, j = i & 7;
+            yT[i] = (j < t.nvalid && f < F) ? eps + y_raw[j * F + f] : 1.f;
+        }
     }
     __syncthreads();
 
     // ---- h in registers: warp w < KS owns k = 16w + {2tq, 2tq+1, 8+2tq, 9+2tq}, frame g
-    float hr[4];
+    float hr[4] = {0.f, 0.f, 0.f, 0.f};
     const bool hown = warp < KS;
     if (hown) {
 #pragma unroll
@@ -403,84 +431,95 @@ __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma, float 
         const bool last = (it == t.n_in);
         if (last && !t.final_pass) break;
         const bool want_loss = (last && t.final_pass) || (it == 0 && t.loss_first);
-        // ---- x = eps + W h on tensor cores; p, q -> PQ_s (bf16)
-        for (int mt = warp; mt < FT; mt += kWarps) {
-            const int f0 = 16 * mt;
-            float d[4] = {eps, eps, eps, eps};
-            for (int ks = 0; ks < KS; ++ks) {
-                uint32_t a[4];
-                const int krow = 16 * ks + r8 + 8 * (mi >> 1);
-                const int fcol = f0 + 8 * (mi & 1);
-                ldmatrix_x4_trans(a, W_s + krow * WLD + fcol);
-                uint32_t b0 = *reinterpret_cast<const uint32_t *>(H_s + g * HLD + 16 * ks + 2 * tq);
-                uint32_t b1 =
-                    *reinterpret_cast<const uint32_t *>(H_s + g * HLD + 16 * ks + 8 + 2 * tq);
-                mma_bf16_16816(d, a, b0, b1);
-            }
+        // ---- step A: x = eps + W h
+        {
+            float d[kMtMax][4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int f = f0 + g + 8 * (e >> 1);
-                const int j = 2 * tq + (e & 1);
-                float p = 0.f, q = 0.f;
-                if (f < F) {
-                    const bool vj = j < t.nvalid;
-                    const float y = vj ? eps + y_s[j * F + f] : 1.f;
-                    q = __frcp_rn(d[e]);
-                    p = y * q * q;
-                    if (want_loss && vj) {
-                        float r = y * q;
-                        lacc += (r - 1.f) - logf(r);
+            for (int i = 0; i < kMtMax; ++i)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) d[i][e] = eps;
+            const __nv_bfloat16 *wa = W_s + (r8 + 8 * (mi >> 1)) * WLD + 8 * (mi & 1) + 16 * warp;
+#pragma unroll
+            for (int ks = 0; ks < KS; ++ks) {
+                const uint32_t b0 =
+                    *reinterpret_cast<const uint32_t *>(H_s + g * HLD + 16 * ks + 2 * tq);
+                const uint32_t b1 =
+                    *reinterpret_cast<const uint32_t *>(H_s + g * HLD + 16 * ks + 8 + 2 * tq);
+#pragma unroll
+                for (int i = 0; i < kMtMax; ++i) {
+                    if (warp + kWarps * i < FT) {
+                        uint32_t a[4];
+                        ldmatrix_x4_trans(a, wa + 16 * ks * WLD + 16 * kWarps * i);
+                        mma_bf16_16816(d[i], a, b0, b1);
                     }
                 }
-                PQ_s[j * WLD + f] = __float2bfloat16_rn(p);
-                PQ_s[(8 + j) * WLD + f] = __float2bfloat16_rn(q);
+            }
+            // p = y/x^2, q = 1/x (FP32), bf16, stored transposed: PQ_s[j][f], PQ_s[8+j][f]
+#pragma unroll
+            for (int i = 0; i < kMtMax; ++i) {
+                const int mt = warp + kWarps * i;
+                if (mt < FT) {
+                    const int f0 = 16 * mt;
+                    const float2 ya = *reinterpret_cast<const float2 *>(yT + (f0 + g) * 8 + 2 * tq);
+                    const float2 yb =
+                        *reinterpret_cast<const float2 *>(yT + (f0 + g + 8) * 8 + 2 * tq);
+                    const float yv[4] = {ya.x, ya.y, yb.x, yb.y};
+                    float pv[4], qv[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int f = f0 + g + 8 * (e >> 1);
+                        const float q = rcp_approx(d[i][e]);
+                        const float p = yv[e] * q * q;
+                        const bool ok = f < F;
+                        pv[e] = ok ? p : 0.f;
+                        qv[e] = ok ? q : 0.f;
+                        if (want_loss && ok && (2 * tq + (e & 1)) < t.nvalid) {
+                            const float r = yv[e] * q;
+                            lacc += (r - 1.f) - logf(r);
+                        }
+                    }
+                    stmatrix_x4_trans(PQ_s + (r8 + 8 * (mi >> 1)) * WLD + f0 + 8 * (mi & 1),
+                                      pack_bf16(pv[0], pv[1]), pack_bf16(pv[2], pv[3]),
+                                      pack_bf16(qv[0], qv[1]), pack_bf16(qv[2], qv[3]));
+                }
             }
         }
         __syncthreads();
         if (last) break;
 
-        // ---- [W^T p | W^T q] on tensor cores; h update in registers
+        // ---- step B: [W^T p | W^T q] and the h update
         if (hown) {
-            float d0[4] = {0.f, 0.f, 0.f, 0.f}, d1[4] = {0.f, 0.f, 0.f, 0.f};
-            float e0[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f};
-            const __nv_bfloat16 *wr0 = W_s + (16 * warp + g) * WLD + 2 * tq;
-            const __nv_bfloat16 *wr1 = W_s + (16 * warp + 8 + g) * WLD + 2 * tq;
+            float c0[4][4], c1[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) c0[u][e] = c1[u][e] = 0.f;
             const __nv_bfloat16 *arow = PQ_s + (r8 + 8 * (mi & 1)) * WLD + 8 * (mi >> 1);
-            int fs = 0;
-            for (; fs + 1 < FT; fs += 2) {
-                uint32_t a[4], c[4];
-                ldmatrix_x4(a, arow + 16 * fs);
-                ldmatrix_x4(c, arow + 16 * (fs + 1));
-                const int fa = 16 * fs, fb = 16 * (fs + 1);
-                mma_bf16_16816(d0, a, *reinterpret_cast<const uint32_t *>(wr0 + fa),
-                               *reinterpret_cast<const uint32_t *>(wr0 + fa + 8));
-                mma_bf16_16816(d1, a, *reinterpret_cast<const uint32_t *>(wr1 + fa),
-                               *reinterpret_cast<const uint32_t *>(wr1 + fa + 8));
-                mma_bf16_16816(e0, c, *reinterpret_cast<const uint32_t *>(wr0 + fb),
-                               *reinterpret_cast<const uint32_t *>(wr0 + fb + 8));
-                mma_bf16_16816(e1, c, *reinterpret_cast<const uint32_t *>(wr1 + fb),
-                               *reinterpret_cast<const uint32_t *>(wr1 + fb + 8));
+            const __nv_bfloat16 *brow = W_s + (16 * warp + r8 + 8 * (mi >> 1)) * WLD + 8 * (mi & 1);
+            for (int fs = 0; fs < FT; fs += 4) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (fs + u < FT) {
+                        uint32_t a[4], b[4];
+                        ldmatrix_x4(a, arow + 16 * (fs + u));
+                        ldmatrix_x4(b, brow + 16 * (fs + u));
+                        mma_bf16_16816(c0[u], a, b[0], b[1]);
+                        mma_bf16_16816(c1[u], a, b[2], b[3]);
+                    }
+                }
             }
-            if (fs < FT) {
-                uint32_t a[4];
-                ldmatrix_x4(a, arow + 16 * fs);
-                const int fa = 16 * fs;
-                mma_bf16_16816(d0, a, *reinterpret_cast<const uint32_t *>(wr0 + fa),
-                               *reinterpret_cast<const uint32_t *>(wr0 + fa + 8));
-                mma_bf16_16816(d1, a, *reinterpret_cast<const uint32_t *>(wr1 + fa),
-                               *reinterpret_cast<const uint32_t *>(wr1 + fa + 8));
-            }
+            float n0[4], n1[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                d0[e] += e0[e];
-                d1[e] += e1[e];
+                n0[e] = (c0[0][e] + c0[1][e]) + (c0[2][e] + c0[3][e]);
+                n1[e] = (c1[0][e] + c1[1][e]) + (c1[2][e] + c1[3][e]);
             }
-            // d[0..1] = (W^T p)[k, k+1] of frame g, d[2..3] = (W^T q)[k, k+1]
-            float num[4] = {d0[0], d0[1], d1[0], d1[1]};
-            float den[4] = {d0[2], d0[3], d1[2], d1[3]};
+            // n[0..1] = (W^T p)[k, k+1] of frame g, n[2..3] = (W^T q)[k, k+1]
+            const float num[4] = {n0[0], n0[1], n1[0], n1[1]};
+            const float den[4] = {n0[2], n0[3], n1[2], n1[3]};
 #pragma unroll
             for (int e = 0; e < 4; ++e)
-                if (den[e] > 0.f) hr[e] = hr[e] * pow_gamma(__fdiv_rn(num[e], den[e]), gamma);
+                if (den[e] > 0.f) hr[e] = hr[e] * pow_gamma(__fdividef(num[e], den[e]), gamma);
             *reinterpret_cast<uint32_t *>(H_s + g * HLD + 16 * warp + 2 * tq) =
                 pack_bf16(hr[0], hr[1]);
             *reinterpret_cast<uint32_t *>(H_s + g * HLD + 16 * warp + 8 + 2 * tq) =
@@ -504,7 +543,7 @@ __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma, float 
             __nv_bfloat16 *dst = (which ? Qg : Pg) + (t.j0 + j) * Fp + 8 * c;
             *reinterpret_cast<uint4 *>(dst) = v;
         }
-        for (int k = tid; k < Kp; k += kThreads) {
+        for (int k = tid; k < KS * 16; k += kThreads) {
             uint32_t w[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {

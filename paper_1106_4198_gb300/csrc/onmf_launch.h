@@ -12,10 +12,11 @@ namespace onmf {
 
 int64_t kernel_launches();
 cudaError_t configure_kernels();
+size_t max_dynamic_smem();
 size_t online_smem_bytes(const Shape &s, int prec);
 size_t tile_smem_bytes(const Shape &s, int prec);
 size_t batch_stats_smem_bytes(int prec);
-cudaError_t max_coresident_blocks(int prec, size_t smem, int *blocks_per_sm);
+cudaError_t max_coresident_blocks(int prec, int ks, size_t smem, int *blocks_per_sm);
 
 cudaError_t launch_online(const StepArgs &a, int prec, int grid, size_t smem, cudaStream_t stream);
 cudaError_t launch_tiles(const TileArgs &a, int prec, int grid, size_t smem, cudaStream_t stream);

@@ -1,0 +1,458 @@
+// Templated step kernels of libonmf: the persistent online step (Algorithm 1
+// of arXiv:1106.4198, one launch = many minibatches), the tile kernel used by
+// projection and the batch H step, and the split-N statistics of the batch
+// W step. Included by the translation units that instantiate them.
+//
+// One online minibatch is three grid-wide phases separated by bounded grid
+// barriers (the launch is cooperative, so all CTAs are co-resident):
+//   1. h-solve of every 8-frame tile (frames are independent given W); each
+//      tile leaves its final P = Y/X^2, Q = 1/X and H rows in L2-resident
+//      scratch and its d_IS sum in a per-tile slot;
+//   2. statistics a = (P H^T) o W^2, b = Q H^T on (16 rows x 32 columns)
+//      output tiles, then A <- rho A + a, B <- rho B + b and W' = sqrt(A/B)
+//      for the tile's entries;
+//   3. one CTA per dictionary column: s_k = sum_f W'_fk (warp shuffles and
+//      a fixed-order combine), W = W'/s, A /= s, B *= s, the derived images
+//      of W, and the running loss.
+#pragma once
+
+#include "onmf_device.cuh"
+#include "onmf_hsolve.cuh"
+#include "onmf_kernels.cuh"
+
+namespace onmf {
+
+// ---------------------------------------------------------------- phase 2
+
+constexpr int kChunk = 1024;  // frames per shared-memory chunk (mixed stats)
+constexpr int kPS = 24;       // row stride (bf16) of the P/Q chunk rows
+constexpr int kHS = kChunk + 8;
+
+__host__ __device__ inline size_t stats_smem_bytes(int prec) {
+    if (prec == PREC_MIXED)
+        return (size_t)2 * kChunk * kPS * 2 + (size_t)32 * kHS * 2 + 2 * 16 * 32 * 4;
+    return (size_t)kWarps * 16 * 32 * 2 * 4 + 2 * 16 * 32 * 4;
+}
+
+// Accumulate sum_j P[j][f] H[j][k] and sum_j Q[j][f] H[j][k] over frames
+// [jb, je) for the output tile rows 16*mt.. and columns 32*ks.. into
+// acc[2][16][32] (shared memory). Warp w: n-tile w & 3, P (w < 4) or Q.
+static __device__ void stats_unit_mixed(const Shape &s, int mt, int ks, const __nv_bfloat16 *Pg,
+                                 const __nv_bfloat16 *Qg, const __nv_bfloat16 *Hg,
+                                 long long betap, long long jb, long long je, unsigned char *smem,
+                                 float *acc) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, tq = lane & 3, mi = lane >> 3, r8 = lane & 7;
+    __nv_bfloat16 *P_s = reinterpret_cast<__nv_bfloat16 *>(smem);
+    __nv_bfloat16 *Q_s = P_s + kChunk * kPS;
+    __nv_bfloat16 *H_s = Q_s + kChunk * kPS;
+    const int nt = warp & 3, which = warp >> 2;
+    const int Fp = s.Fp16;
+    const int f0 = 16 * mt, k0 = 32 * ks;
+    float c[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) c[u][e] = 0.f;
+    const __nv_bfloat16 *X_s = which ? Q_s : P_s;
+    for (long long cb = jb; cb < je; cb += kChunk) {
+        const int nf = (int)min((long long)kChunk, je - cb);
+        const int nfr = (nf + 15) / 16 * 16;  // rows touched by the k16 steps
+        for (int i = tid; i < nfr * 4; i += kThreads) {
+            const int w = i / (nfr * 2), rem = i - w * nfr * 2;
+            const int jj = rem >> 1, half = rem & 1;
+            const __nv_bfloat16 *base = w ? Qg : Pg;
+            const bool ok = jj < nf;
+            const __nv_bfloat16 *src = ok ? base + (cb + jj) * Fp + f0 + 8 * half : base;
+            __nv_bfloat16 *dst = (w ? Q_s : P_s) + jj * kPS + 8 * half;
+            cp_async16(dst, src, ok ? 16 : 0);
+        }
+        const int nch = nfr / 8;
+        for (int i = tid; i < 32 * nch; i += kThreads) {
+            const int kk = i / nch, ch = i - kk * nch;
+            const int jj = 8 * ch;
+            const bool ok = jj < nf;
+            const __nv_bfloat16 *src = ok ? Hg + (long long)(k0 + kk) * betap + cb + jj : Hg;
+            cp_async16(H_s + kk * kHS + jj, src, ok ? 16 : 0);
+        }
+        cp_async_commit();
+        cp_async_wait_all();
+        __syncthreads();
+        const int nks = nfr / 16;
+        const __nv_bfloat16 *hrow = H_s + (8 * nt + g) * kHS + 2 * tq;
+        const __nv_bfloat16 *xrow = X_s + (r8 + 8 * (mi >> 1)) * kPS + 8 * (mi & 1);
+        for (int k4 = 0; k4 < nks; k4 += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int ksi = k4 + u;
+                if (ksi < nks) {
+                    uint32_t a[4];
+                    ldmatrix_x4_trans(a, xrow + 16 * ksi * kPS);
+                    mma_bf16_16816(c[u], a, *reinterpret_cast<const uint32_t *>(hrow + 16 * ksi),
+                                   *reinterpret_cast<const uint32_t *>(hrow + 16 * ksi + 8));
+                }
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int ff = g + 8 * (e >> 1), kk = 8 * nt + 2 * tq + (e & 1);
+        acc[(which * 16 + ff) * 32 + kk] = (c[0][e] + c[1][e]) + (c[2][e] + c[3][e]);
+    }
+    __syncthreads();
+}
+
+static __device__ void stats_unit_fp32(const Shape &s, int mt, int ks, const float *Pg, const float *Qg,
+                                const float *Hg, long long jb, long long je, unsigned char *smem,
+                                float *acc) {
+    const int tid = threadIdx.x, lane = tid & 31, grp = tid >> 5;
+    float *red = reinterpret_cast<float *>(smem);  // [8][16][32][2]
+    const int fb = lane >> 3, kb = lane & 7;
+    const int Fp = s.Fp16, Kh = s.Kh;
+    const int f0 = 16 * mt + 4 * fb, k0 = 32 * ks + 4 * kb;
+    float cp[4][4], cq[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) cp[a][b] = cq[a][b] = 0.f;
+    const long long len = je - jb;
+    const long long per = (len + kWarps - 1) / kWarps;
+    const long long j1 = jb + grp * per, j2 = min(je, j1 + per);
+#pragma unroll 4
+    for (long long j = j1; j < j2; ++j) {
+        const float4 p = __ldcg(reinterpret_cast<const float4 *>(Pg + j * Fp + f0));
+        const float4 q = __ldcg(reinterpret_cast<const float4 *>(Qg + j * Fp + f0));
+        const float4 h = __ldcg(reinterpret_cast<const float4 *>(Hg + j * Kh + k0));
+        const float pv[4] = {p.x, p.y, p.z, p.w}, qv[4] = {q.x, q.y, q.z, q.w};
+        const float hv[4] = {h.x, h.y, h.z, h.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                cp[a][b] = fmaf(pv[a], hv[b], cp[a][b]);
+                cq[a][b] = fmaf(qv[a], hv[b], cq[a][b]);
+            }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            float *r = red + (((size_t)grp * 16 + 4 * fb + a) * 32 + 4 * kb + b) * 2;
+            r[0] = cp[a][b];
+            r[1] = cq[a][b];
+        }
+    __syncthreads();
+    for (int e = tid; e < 512; e += kThreads) {
+        const int ff = e >> 5, kk = e & 31;
+        float sp = 0.f, sq = 0.f;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            sp += red[(((size_t)w * 16 + ff) * 32 + kk) * 2];
+            sq += red[(((size_t)w * 16 + ff) * 32 + kk) * 2 + 1];
+        }
+        acc[ff * 32 + kk] = sp;
+        acc[(16 + ff) * 32 + kk] = sq;
+    }
+    __syncthreads();
+}
+
+template <int PREC>
+__device__ __forceinline__ void stats_unit(const Shape &s, int mt, int ks, const void *Pg,
+                                           const void *Qg, const void *Hg, long long betap,
+                                           long long jb, long long je, unsigned char *smem,
+                                           float *acc) {
+    if (PREC == PREC_MIXED)
+        stats_unit_mixed(s, mt, ks, reinterpret_cast<const __nv_bfloat16 *>(Pg),
+                         reinterpret_cast<const __nv_bfloat16 *>(Qg),
+                         reinterpret_cast<const __nv_bfloat16 *>(Hg), betap, jb, je, smem, acc);
+    else
+        stats_unit_fp32(s, mt, ks, reinterpret_cast<const float *>(Pg),
+                        reinterpret_cast<const float *>(Qg), reinterpret_cast<const float *>(Hg),
+                        jb, je, smem, acc);
+}
+
+// A <- rho A + a, B <- rho B + b, W' = sqrt(A/B) for the tile's entries
+// (Algorithm 1; the past-scaling reading of rho unless rho_on_new).
+static __device__ void online_epilogue(const StepArgs &a, int mt, int ks, double rho, const float *acc) {
+    const int F = a.s.F, K = a.s.K;
+    for (int e = threadIdx.x; e < 512; e += kThreads) {
+        const int kk = e >> 4, ff = e & 15;
+        const int f = 16 * mt + ff, k = 32 * ks + kk;
+        if (f >= F || k >= K) continue;
+        const long long i = f + (long long)k * F;
+        const float w = a.Wcm[i];
+        const double av = (double)(acc[ff * 32 + kk] * w * w);
+        const double bv = (double)acc[(16 + ff) * 32 + kk];
+        const double A0 = a.A[i], B0 = a.B[i];
+        double An, Bn;
+        if (a.rho_on_new) {
+            An = fma(rho, av, A0);
+            Bn = fma(rho, bv, B0);
+        } else {
+            An = fma(rho, A0, av);
+            Bn = fma(rho, B0, bv);
+        }
+        a.A[i] = An;
+        a.B[i] = Bn;
+        a.Wn[i] = (Bn > 0.0) ? sqrtf(__fdiv_rn((float)An, (float)Bn)) : w;
+    }
+}
+
+// Fixed-order sum of one float per thread over the CTA.
+__device__ __forceinline__ float block_sum_f(float v, float *red8) {
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red8[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float r = 0.f;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) r += red8[w];
+    __syncthreads();
+    return r;
+}
+
+// One CTA per column: s_k = sum_f W'_fk, then the L1 rescale of Algorithm 1
+// and the derived images of W. Each thread keeps its rows in registers
+// (up to 4 * kThreads rows per pass).
+template <int PREC>
+static __device__ void normalize_columns(const Shape &s, int normalize, const float *__restrict__ Wn,
+                                  float *__restrict__ Wcm, float *__restrict__ Wrm,
+                                  __nv_bfloat16 *__restrict__ Wimg, double *__restrict__ A,
+                                  double *__restrict__ B, float *__restrict__ swpart, int *err,
+                                  float *red8) {
+    const int F = s.F, K = s.K;
+    const int tid = threadIdx.x;
+    for (int k = blockIdx.x; k < K; k += gridDim.x) {
+        const float *col = Wn + (long long)k * F;
+        float part = 0.f;
+        for (int f = tid; f < F; f += kThreads) part += col[f];
+        const float sum = block_sum_f(part, red8);
+        const bool sc = normalize && sum > 0.f;
+        const float inv = sc ? __frcp_rn(sum) : 1.f;
+        const double invd = sc ? 1.0 / (double)sum : 1.0;
+        const double sd = sc ? (double)sum : 1.0;
+        bool bad = false;
+        for (int f0 = 0; f0 < F; f0 += 4 * kThreads) {
+            float w[4];
+            double av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int f = f0 + tid + u * kThreads;
+                if (f < F) {
+                    const long long i = f + (long long)k * F;
+                    w[u] = col[f];
+                    if (A) {
+                        av[u] = A[i];
+                        bv[u] = B[i];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int f = f0 + tid + u * kThreads;
+                if (f < F) {
+                    const long long i = f + (long long)k * F;
+                    const float wv = w[u] * inv;
+                    bad |= !isfinite(wv);
+                    Wcm[i] = wv;
+                    if (A) {
+                        A[i] = av[u] * invd;
+                        B[i] = bv[u] * sd;
+                    }
+                    if (PREC == PREC_FP32)
+                        Wrm[(long long)f * K + k] = wv;
+                    else
+                        Wimg[(long long)k * s.WLD + f] = __float2bfloat16_rn(wv);
+                }
+            }
+        }
+        if (bad) flag_error(err, ERR_NUMERIC);
+        if (tid == 0) swpart[k] = sc ? sum * inv : sum;
+    }
+}
+
+// Deterministic sum of n doubles by one CTA (fixed chunking and tree).
+static __device__ double block_sum_ordered(const double *x, long long n, double *red) {
+    const int tid = threadIdx.x;
+    const long long per = (n + kThreads - 1) / kThreads;
+    double a = 0.0;
+    const long long lo = tid * per, hi = min(n, lo + per);
+    for (long long i = lo; i < hi; ++i) a += x[i];
+    red[tid] = a;
+    __syncthreads();
+    for (int st = kThreads / 2; st > 0; st >>= 1) {
+        if (tid < st) red[tid] += red[tid + st];
+        __syncthreads();
+    }
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+template <int PREC, int KS>
+__device__ __forceinline__ void hsolve_tile(const Shape &s, float eps, float gamma,
+                                            const float *Wcm, const float *Wrm, float sw,
+                                            const TileJob &t, unsigned char *smem, WStage &ws,
+                                            uint64_t *vbar, unsigned &vpar, int *err) {
+    if constexpr (PREC == PREC_MIXED)
+        hsolve_tile_mixed<KS>(s, eps, gamma, sw, t, smem, ws, vbar, vpar, err);
+    else
+        hsolve_tile_fp32(s, eps, gamma, Wcm, Wrm, sw, t, smem, err);
+}
+
+// ----------------------------------------------------- persistent online step
+
+template <int PREC, int KS>
+__global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ float s_tmp;
+    __shared__ float s_red8[kWarps];
+    __shared__ double s_red[kThreads];
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned wpar = 0, vpar = 0, epoch = 0;
+    const unsigned G = gridDim.x;
+    const Shape &s = a.s;
+    const int FT = s.Fp16 / 16, KT = s.Kh / 32;
+    const int nunits = FT * KT;
+    float *acc = reinterpret_cast<float *>(smem + stats_smem_bytes(PREC) - 2 * 16 * 32 * 4);
+    for (int m = 0; m < a.nmb; ++m) {
+        const bool lastmb = (m == a.nmb - 1);
+        const int nb = lastmb ? a.nb_last : a.beta;
+        const double rho = lastmb ? a.rho_last : a.rho_full;
+        const float *Vm = a.V + (long long)m * a.beta * a.ldv;
+        float *Hm = a.H_out ? a.H_out + (long long)m * a.beta * a.ldh : nullptr;
+        const int ntiles = ceil_div(nb, kTile);
+        // ---- phase 1: h-solve of every tile
+        if ((int)blockIdx.x < ntiles) {
+            const float sw = sum_w(a.swpart, s.K, &s_tmp);
+            WStage ws{&mbar[0], &wpar, false};
+            if (PREC == PREC_MIXED) {
+                issue_wimg(s, a.Wimg, smem, &mbar[0]);
+                ws.pending = true;
+            }
+            for (int tile = blockIdx.x; tile < ntiles; tile += G) {
+                TileJob t;
+                t.Vt = Vm + (long long)tile * kTile * a.ldv;
+                t.ldv = a.ldv;
+                t.nvalid = min(kTile, nb - tile * kTile);
+                t.j0 = (long long)tile * kTile;
+                t.H_in = nullptr;
+                t.ldh_in = 0;
+                t.H_out = Hm;
+                t.ldh = a.ldh;
+                t.n_in = a.n_in;
+                t.loss_first = 0;
+                t.final_pass = 1;
+                t.loss_slot = a.loss_part + tile;
+                t.Pg = a.Pg;
+                t.Qg = a.Qg;
+                t.Hg = a.Hg;
+                t.betap = a.betap;
+                hsolve_tile<PREC, KS>(s, a.eps, a.gamma, a.Wcm, a.Wrm, sw, t, smem, ws, &mbar[1],
+                                      vpar, a.err);
+            }
+        }
+        if (!grid_sync(a.bar, G, epoch, a.err)) return;
+        // ---- phase 2: statistics and W' = sqrt(A/B)
+        for (int u = blockIdx.x; u < nunits; u += G) {
+            const int mt = u % FT, ks = u / FT;
+            stats_unit<PREC>(s, mt, ks, a.Pg, a.Qg, a.Hg, a.betap, 0, nb, smem, acc);
+            online_epilogue(a, mt, ks, rho, acc);
+            __syncthreads();
+        }
+        if (!grid_sync(a.bar, G, epoch, a.err)) return;
+        // ---- phase 3: column sums, rescale, images, loss
+        normalize_columns<PREC>(s, a.normalize, a.Wn, a.Wcm, a.Wrm, a.Wimg, a.A, a.B, a.swpart,
+                                a.err, s_red8);
+        if (blockIdx.x == G - 1) {
+            double l = block_sum_ordered(a.loss_part, ntiles, s_red);
+            if (threadIdx.x == 0) *a.loss_sum += l;
+        }
+        if (PREC == PREC_MIXED) asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        if (!lastmb && !grid_sync(a.bar, G, epoch, a.err)) return;
+    }
+}
+
+// ----------------------------------------------- projection / batch tiles
+
+template <int PREC, int KS>
+__global__ void __launch_bounds__(kThreads, 1) tile_kernel(TileArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ float s_tmp;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned wpar = 0, vpar = 0;
+    const long long ntiles = (a.n + kTile - 1) / kTile;
+    if ((long long)blockIdx.x >= ntiles) return;
+    const float sw = sum_w(a.swpart, a.s.K, &s_tmp);
+    WStage ws{&mbar[0], &wpar, false};
+    if (PREC == PREC_MIXED) {
+        issue_wimg(a.s, a.Wimg, smem, &mbar[0]);
+        ws.pending = true;
+    }
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        TileJob t;
+        t.Vt = a.V + tile * kTile * a.ldv;
+        t.ldv = a.ldv;
+        t.nvalid = (int)min((long long)kTile, a.n - tile * kTile);
+        t.j0 = tile * kTile;
+        t.H_in = a.H_in;
+        t.ldh_in = a.ldh_in;
+        t.H_out = a.H_out;
+        t.ldh = a.ldh;
+        t.n_in = a.n_in;
+        t.loss_first = a.loss_first;
+        t.final_pass = a.final_pass;
+        t.loss_slot = a.loss_part ? a.loss_part + tile : nullptr;
+        t.Pg = a.Pg;
+        t.Qg = a.Qg;
+        t.Hg = a.Hg;
+        t.betap = a.betap;
+        hsolve_tile<PREC, KS>(a.s, a.eps, a.gamma, a.Wcm, a.Wrm, sw, t, smem, ws, &mbar[1], vpar,
+                              a.err);
+    }
+}
+
+// Split-N statistics: partial sums over frame chunk `c` of P H^T and Q H^T
+// for every (16 x 32) output tile -> part[c][2][Fp16][Kh].
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1)
+    batch_stats_kernel(Shape s, const void *Pg, const void *Qg, const void *Hg, long long betap,
+                       long long N, int nchunks, float *part) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *acc = reinterpret_cast<float *>(smem + stats_smem_bytes(PREC) - 2 * 16 * 32 * 4);
+    const int FT = s.Fp16 / 16, KT = s.Kh / 32;
+    const long long per = ((N + nchunks - 1) / nchunks + 15) / 16 * 16;
+    const long long units = (long long)FT * KT * nchunks;
+    for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+        const int c = (int)(u / (FT * KT));
+        const int r = (int)(u - (long long)c * FT * KT);
+        const int mt = r % FT, ks = r / FT;
+        const long long jb = c * per, je = min(N, jb + per);
+        if (jb < je) {
+            stats_unit<PREC>(s, mt, ks, Pg, Qg, Hg, betap, jb, je, smem, acc);
+        } else {
+            for (int e = threadIdx.x; e < 1024; e += kThreads) acc[e] = 0.f;
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < 1024; e += kThreads) {
+            const int which = e >> 9, ff = (e >> 5) & 15, kk = e & 31;
+            part[(((long long)c * 2 + which) * s.Fp16 + 16 * mt + ff) * s.Kh + 32 * ks + kk] =
+                acc[e];
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace onmf
