@@ -1,0 +1,84 @@
+"""Parity of batch IS-NMF multiplicative updates (Section 2.1) on the GPU,
+through the C ABI (nmf_batch_init_H, nmf_batch_step), against the FP64 oracle.
+
+Tolerances (norm-wise relative): FP32 one cycle W, H <= 1e-5; objective
+trajectory <= 1e-3 at every cycle (50 cycles, config-1 shape); mixed
+precision stated per test."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1106_4198_gb300 as onmf
+from helpers import cuda, problem, relerr
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_batch(V, W0, n_iter, precision=onmf.ONMF_FP32, eps=1e-12, H0=None):
+    import torch
+    K, F = W0.shape
+    N = V.shape[0]
+    Vd = cuda(V)
+    W = cuda(W0.astype(np.float32))
+    if H0 is None:
+        H = torch.zeros((N, K), device="cuda")
+        onmf.nmf_batch_init_H(Vd, W, H, eps=eps)
+    else:
+        H = cuda(H0.astype(np.float32))
+    obj = onmf.nmf_batch_step(Vd, W, H, eps=eps, n_iter=n_iter, precision=precision)
+    torch.cuda.synchronize()
+    return W.cpu().numpy(), H.cpu().numpy(), obj
+
+
+def test_batch_start_point():
+    import torch
+    F, K, N = 129, 8, 500
+    V, W0 = problem(F, K, N)
+    H = torch.zeros((N, K), device="cuda")
+    onmf.nmf_batch_init_H(cuda(V), cuda(W0), H, eps=1e-12)
+    Ho = oracle.batch_h0(V, W0, eps=1e-12)
+    assert relerr(H.cpu().numpy(), Ho) <= 1e-6
+
+
+@pytest.mark.parametrize("F,K,N", [(129, 8, 2000), (513, 50, 3000), (33, 5, 41)])
+def test_batch_one_cycle_fp32(F, K, N):
+    V, W0 = problem(F, K, N)
+    H0 = oracle.batch_h0(V, W0)
+    Wg, Hg, objg = gpu_batch(V, W0, 1, H0=H0)
+    oracle.set_threads(16)
+    Wo, Ho, objo = oracle.batch(V, W0, H0, n_iter=1)
+    oracle.set_threads(1)
+    ew, eh = relerr(Wg, Wo), relerr(Hg, Ho)
+    eo = abs(objg[0] - objo[0]) / objo[0]
+    print("batch one cycle F=%d K=%d N=%d: W %.2e H %.2e obj %.2e" % (F, K, N, ew, eh, eo))
+    assert ew <= 1e-5 and eh <= 1e-5 and eo <= 1e-5
+
+
+def test_batch_c1_objective_trajectory():
+    """Config 1: F=129, K=8, N=2000, 50 cycles; every cycle's objective
+    within 1e-3 of the oracle, and (FP32) non-increasing."""
+    F, K, N, it = 129, 8, 2000, 50
+    V, W0 = problem(F, K, N)
+    H0 = oracle.batch_h0(V, W0)
+    Wg, Hg, objg = gpu_batch(V, W0, it, H0=H0)
+    oracle.set_threads(16)
+    Wo, Ho, objo = oracle.batch(V, W0, H0, n_iter=it)
+    oracle.set_threads(1)
+    rel = np.abs(objg - objo) / objo
+    print("batch C1: worst objective rel err %.2e, final W rel err %.2e"
+          % (rel.max(), relerr(Wg, Wo)))
+    assert rel.max() <= 1e-3
+    assert np.all(np.diff(objg) <= 1e-6 * objg[:-1])
+
+
+def test_batch_mixed_objective_stated():
+    """Mixed precision batch cycles (BF16 products): objective within 1e-3
+    of the FP64 oracle at every cycle (config-1 shape, 50 cycles)."""
+    F, K, N, it = 129, 8, 2000, 50
+    V, W0 = problem(F, K, N)
+    H0 = oracle.batch_h0(V, W0)
+    _, _, objg = gpu_batch(V, W0, it, precision=onmf.ONMF_MIXED, H0=H0)
+    _, _, objo = oracle.batch(V, W0, H0, n_iter=it)
+    rel = np.abs(objg - objo) / objo
+    print("batch mixed C1: worst objective rel err %.2e" % rel.max())
+    assert rel.max() <= 1e-3
