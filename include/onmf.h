@@ -164,6 +164,38 @@ onmf_status nmf_batch_init_H(const float *V, int64_t ldv, const float *W,
                              float *H, int32_t F, int32_t K, int64_t N,
                              double eps, void *stream);
 
+/* Size of the fixed device scratch array used by onmf_project_static. */
+#define ONMF_STATIC_SCRATCH_BYTES (4u << 20)
+
+/* Projection (the h-solve of onmf_project, same kernels and results) for
+ * callers that cannot allocate device memory: code running in a real-time
+ * audio callback, where cudaMalloc may stall on a device-wide
+ * synchronization, or inside a host that gives the library a fixed memory
+ * arena. The paper has no counterpart; this is a deployment variant.
+ *   W: F x K dictionary (device, ld F). V: F x n frames (device, ldv >= F).
+ *   H_out: K x n (device, ldh >= K) or NULL. obj_sum: NULL or a device double
+ *   that receives sum_n d_IS(eps + v_n, eps + W h_n). precision: onmf_precision.
+ *   stream: cudaStream_t (NULL = legacy default stream).
+ * Allocates nothing: its scratch (the derived images of W, K column sums and
+ * one double per 8 frames) lives in one static device array of
+ * ONMF_STATIC_SCRATCH_BYTES (4 MiB) that every GPU loading the library keeps
+ * until the process exits. A call whose scratch would not fit returns
+ * ONMF_EINVAL: the need is about 4*F*K bytes (FP32) or 2*K*F bytes (mixed)
+ * for the image of W, plus 4*K, plus n bytes for the loss slots, and it
+ * must stay under 4 MiB - 256 B (F = 513, K = 100 leaves room for about
+ * 3.9 million frames per call in FP32). All calls share the array: calls that run at the same
+ * time on the GPU (different streams or threads) race and must be serialized
+ * by the caller. The first call on each device looks up the array's device
+ * address (and sets kernel attributes); make that first call before any
+ * stream capture. Asynchronous; V is not checked for negative or non-finite
+ * values here (the caller validates its input). */
+onmf_status onmf_project_static(const float *W, int32_t F, int32_t K,
+                                const float *V, int64_t ldv, int64_t n,
+                                float *H_out, int64_t ldh, double eps,
+                                double h_exponent, int32_t n_inner,
+                                int32_t precision, double *obj_sum,
+                                void *stream);
+
 /* Release the state and everything the library allocated for it. */
 void onmf_destroy(onmf_state *s);
 

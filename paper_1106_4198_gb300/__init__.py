@@ -23,7 +23,7 @@ __all__ = [
     "onmf_synchronize", "onmf_get_W", "onmf_get_stats", "onmf_set_state",
     "onmf_project", "nmf_batch_step", "nmf_batch_init_H", "onmf_destroy",
     "onmf_status_string", "onmf_kernel_launches", "onmf_abi_version",
-    "OnlineISNMF", "EXPORTED",
+    "onmf_project_static", "OnlineISNMF", "EXPORTED",
 ]
 
 ONMF_FP32 = 0
@@ -35,7 +35,7 @@ EXPORTED = [
     "onmf_synchronize", "onmf_get_W", "onmf_get_stats", "onmf_set_state",
     "onmf_project", "nmf_batch_step", "nmf_batch_init_H", "onmf_destroy",
     "onmf_status_string", "onmf_last_error_message", "onmf_kernel_launches",
-    "onmf_abi_version",
+    "onmf_abi_version", "onmf_project_static",
 ]
 
 
@@ -95,6 +95,8 @@ def lib():
                                  _i32, _i32, _i32, _vp, _vp]
     L.nmf_batch_init_H.argtypes = [_vp, _i64, _vp, _vp, _i32, _i32, _i64, _d,
                                    _vp]
+    L.onmf_project_static.argtypes = [_vp, _i32, _i32, _vp, _i64, _i64, _vp,
+                                      _i64, _d, _d, _i32, _i32, _vp, _vp]
     L.onmf_destroy.argtypes = [_vp]
     L.onmf_destroy.restype = None
     L.onmf_status_string.argtypes = [ctypes.c_int]
@@ -105,7 +107,7 @@ def lib():
     for name in ("onmf_init", "onmf_push_frames", "onmf_flush",
                  "onmf_synchronize", "onmf_get_W", "onmf_get_stats",
                  "onmf_set_state", "onmf_project", "nmf_batch_step",
-                 "nmf_batch_init_H"):
+                 "nmf_batch_init_H", "onmf_project_static"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -271,6 +273,21 @@ def nmf_batch_step(V, W, H, eps=1e-12, h_exponent=0.5, n_iter=1, normalize=1,
                                 obj, _stream_handle(stream)),
            "nmf_batch_step")
     return np.array(obj[:n_iter]) if want_obj else None
+
+
+def onmf_project_static(W, V, H_out=None, obj_sum=None, eps=1e-12,
+                        h_exponent=0.5, n_inner=10, precision=ONMF_FP32,
+                        stream=None):
+    """Allocation-free projection: device tensors W (K, F), V (n, F), H_out
+    (n, K) or None, obj_sum a 1-element float64 device tensor or None."""
+    K, F = W.shape
+    pv, ldv = _ptr_ld(V, F)
+    ph, ldh = _ptr_ld(H_out, K) if H_out is not None else (None, K)
+    po = obj_sum.data_ptr() if obj_sum is not None else None
+    _check(lib().onmf_project_static(W.data_ptr(), F, K, pv, ldv, V.shape[0], ph,
+                                     ldh, eps, h_exponent, n_inner, precision,
+                                     po, _stream_handle(stream)),
+           "onmf_project_static")
 
 
 def onmf_destroy(state):
