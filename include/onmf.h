@@ -180,8 +180,8 @@ onmf_status nmf_batch_init_H(const float *V, int64_t ldv, const float *W,
  * one double per 8 frames) lives in one static device array of
  * ONMF_STATIC_SCRATCH_BYTES (4 MiB) that every GPU loading the library keeps
  * until the process exits. A call whose scratch would not fit returns
- * ONMF_EINVAL: the need is about 4*F*K bytes (FP32) or 2*K*F bytes (mixed)
- * for the image of W, plus 4*K, plus n bytes for the loss slots, and it
+ * ONMF_EINVAL: the need is about 4*F*K bytes (FP32) or 4*K*F bytes (mixed:
+ * two bf16 images of W) for W, plus 4*K, plus n bytes for the loss slots, and it
  * must stay under 4 MiB - 256 B (F = 513, K = 100 leaves room for about
  * 3.9 million frames per call in FP32). All calls share the array: calls that run at the same
  * time on the GPU (different streams or threads) race and must be serialized

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -62,6 +63,27 @@ struct Segment {
 
 int g_configured = 0;
 
+// Mixed precision runs the mma.sync h-solve unless ONMF_HSOLVE=tc selects the
+// tcgen05 one (where the shape allows it: F >= 128 with at most 32 rows past
+// the last 128-row tile, K <= 128). At 16-frame tiles a tcgen05 MMA costs a
+// fixed ~55 cycles (N <= 64), which leaves the two within ~10% of each other
+// on the online minibatch; the faster one is picked per shape by measurement.
+// The tcgen05 kernels allocate all 512 TMEM columns per CTA; asking for more
+// than half of an SM's shared memory keeps them at one CTA per SM, so an
+// allocation never waits on a co-resident CTA (which, inside a cooperative
+// launch, could be waiting at a grid barrier).
+size_t tc_min_smem(int prec, size_t smem) {
+    const size_t one_per_sm = 116 * 1024;
+    return (prec == PREC_TC && smem < one_per_sm) ? one_per_sm : smem;
+}
+
+int pick_prec(int precision, const Shape &sh) {
+    if (precision != ONMF_MIXED) return PREC_FP32;
+    const char *env = getenv("ONMF_HSOLVE");
+    if (env && strcmp(env, "tc") == 0 && tc_shape_supported(sh)) return PREC_TC;
+    return PREC_MIXED;
+}
+
 onmf_status ensure_configured() {
     if (!g_configured) {
         CK(configure_kernels());
@@ -79,7 +101,7 @@ struct onmf_state {
     int prec;
     // state
     float *Wcm = nullptr, *Wrm = nullptr, *Wn = nullptr, *swpart = nullptr;
-    __nv_bfloat16 *Wimg = nullptr;
+    __nv_bfloat16 *Wimg = nullptr, *Wrow = nullptr;
     double *A = nullptr, *B = nullptr, *loss_sum = nullptr;
     // scratch
     void *Pg = nullptr, *Qg = nullptr, *Hg = nullptr;
@@ -129,7 +151,8 @@ static onmf_status sync_and_check(onmf_state *s) {
 
 static onmf_status prepare_images(onmf_state *s) {
     CK(launch_prepare(s->s, s->Wcm, s->prec == PREC_FP32 ? s->Wrm : nullptr,
-                      s->prec == PREC_MIXED ? s->Wimg : nullptr, s->swpart, s->stream));
+                      s->prec != PREC_FP32 ? s->Wimg : nullptr, s->swpart, s->stream,
+                      s->prec == PREC_TC ? s->Wrow : nullptr));
     return ONMF_OK;
 }
 
@@ -175,7 +198,7 @@ int32_t onmf_abi_version(void) { return ONMF_ABI_VERSION; }
 void onmf_destroy(onmf_state *s) {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
-    void *dev[] = {s->Wcm, s->Wrm, s->Wn, s->swpart, s->Wimg, s->A, s->B, s->loss_sum, s->Pg,
+    void *dev[] = {s->Wcm, s->Wrm, s->Wn, s->swpart, s->Wimg, s->Wrow, s->A, s->B, s->loss_sum, s->Pg,
                    s->Qg, s->Hg, s->loss_part, s->tmp_sum, s->bar, s->err_d, s->staging,
                    s->Hstage, s->vring[0], s->vring[1], s->hring[0], s->hring[1]};
     for (void *p : dev)
@@ -208,11 +231,11 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
     s->cfg = c;
     s->s = make_shape(c.F, c.K);
     s->stream = reinterpret_cast<cudaStream_t>(stream);
-    s->prec = c.precision == ONMF_MIXED ? PREC_MIXED : PREC_FP32;
+    s->prec = pick_prec(c.precision, s->s);
     const Shape &sh = s->s;
     const size_t FK = (size_t)c.F * c.K;
     s->betap = (c.beta + 15) / 16 * 16;
-    const size_t elem = s->prec == PREC_MIXED ? 2 : 4;
+    const size_t elem = s->prec == PREC_FP32 ? 4 : 2;
     const int ntiles = (c.beta + kTile - 1) / kTile;
     auto fail = [&](onmf_status e) {
         onmf_destroy(s);
@@ -239,6 +262,7 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
     } else {
         AL(s->Wimg, (size_t)sh.Kp * sh.WLD * 2);
         AL(s->Hg, (size_t)sh.Kh * s->betap * 2);
+        if (s->prec == PREC_TC) AL(s->Wrow, (size_t)sh.F * sh.Kp * 2);
     }
     AL(s->Pg, (size_t)s->betap * sh.Fp16 * elem);
     AL(s->Qg, (size_t)s->betap * sh.Fp16 * elem);
@@ -255,6 +279,7 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
     cudaStream_t q = s->stream;
     cudaError_t e = cudaSuccess;
     if (s->Wimg && e == cudaSuccess) e = cudaMemsetAsync(s->Wimg, 0, (size_t)sh.Kp * sh.WLD * 2, q);
+    if (s->Wrow && e == cudaSuccess) e = cudaMemsetAsync(s->Wrow, 0, (size_t)sh.F * sh.Kp * 2, q);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->Hg, 0, (size_t)s->betap * sh.Kh * elem, q);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->Pg, 0, (size_t)s->betap * sh.Fp16 * elem, q);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->Qg, 0, (size_t)s->betap * sh.Fp16 * elem, q);
@@ -272,8 +297,8 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    s->smem = online_smem_bytes(sh, s->prec);
-    s->tile_smem = tile_smem_bytes(sh, s->prec);
+    s->smem = tc_min_smem(s->prec, online_smem_bytes(sh, s->prec));
+    s->tile_smem = tc_min_smem(s->prec, tile_smem_bytes(sh, s->prec));
     if (s->smem > max_dynamic_smem()) {
         snprintf(g_msg, sizeof g_msg, "shared memory need %zu exceeds the device limit", s->smem);
         return fail(ONMF_EINVAL);
@@ -284,7 +309,8 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
         return fail(ONMF_ECUDA);
     }
     const int units = (sh.Fp16 / 16) * (sh.Kh / 32);
-    int want = std::max(std::max(ntiles, units), (c.K + kWarps - 1) / kWarps);
+    const int tiles = s->prec == PREC_TC ? (c.beta + kTcTile - 1) / kTcTile : ntiles;
+    int want = std::max(std::max(tiles, units), (c.K + kWarps - 1) / kWarps);
     s->grid = std::min(want, per_sm * s->num_sms);
     s->tile_grid = s->num_sms;
     // sanity: all of W0 finite and >= 0 (checked on the host copy)
@@ -325,6 +351,7 @@ static onmf_status run_minibatches(onmf_state *s, const float *V, long long ldv,
     a.Wcm = s->Wcm;
     a.Wrm = s->Wrm;
     a.Wimg = s->Wimg;
+    a.Wrow = s->Wrow;
     a.Wn = s->Wn;
     a.A = s->A;
     a.B = s->B;
@@ -521,7 +548,8 @@ onmf_status onmf_project(onmf_state *s, const float *V, int64_t ldv, int64_t n, 
     const float *Vd = V;
     float *Vtmp = nullptr, *Htmp = nullptr;
     double *lp = nullptr;
-    const long long ntiles = (n + kTile - 1) / kTile;
+    const int tile = s->prec == PREC_TC ? kTcTile : kTile;
+    const long long ntiles = (n + tile - 1) / tile;
     cudaStream_t q = s->stream;
     if (!vdev) {
         CK(cudaMallocAsync((void **)&Vtmp, (size_t)n * c.F * 4, q));
@@ -552,6 +580,7 @@ onmf_status onmf_project(onmf_state *s, const float *V, int64_t ldv, int64_t n, 
     a.Wcm = s->Wcm;
     a.Wrm = s->Wrm;
     a.Wimg = s->Wimg;
+    a.Wrow = s->Wrow;
     a.swpart = s->swpart;
     a.loss_part = lp;
     a.err = s->err_d;
@@ -604,11 +633,12 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
     if (st != ONMF_OK) return st;
     if (n_iter == 0) return ONMF_OK;
     cudaStream_t q = reinterpret_cast<cudaStream_t>(stream);
-    const int prec = precision == ONMF_MIXED ? PREC_MIXED : PREC_FP32;
     const Shape sh = make_shape(F, K);
+    const int prec = pick_prec(precision, sh);
     const long long betap = (N + 15) / 16 * 16;
-    const size_t elem = prec == PREC_MIXED ? 2 : 4;
-    const long long ntiles = (N + kTile - 1) / kTile;
+    const size_t elem = prec == PREC_FP32 ? 4 : 2;
+    const int tile = prec == PREC_TC ? kTcTile : kTile;
+    const long long ntiles = (N + tile - 1) / tile;
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -616,7 +646,7 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
     int nchunks = std::max(1, std::min<int>((2 * nsm + units - 1) / units, (int)((N + 255) / 256)));
     // scratch
     float *Wrm = nullptr, *swp = nullptr, *part = nullptr, *scale = nullptr;
-    __nv_bfloat16 *Wimg = nullptr;
+    __nv_bfloat16 *Wimg = nullptr, *Wrow = nullptr;
     void *Pg = nullptr, *Qg = nullptr, *Hg = nullptr;
     double *lp = nullptr, *obj_d = nullptr;
     int *err = nullptr;
@@ -632,7 +662,8 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
               al(&Hg, (size_t)betap * sh.Kh * elem) && al((void **)&lp, (size_t)ntiles * 8) &&
               al((void **)&obj_d, (size_t)std::max(1, n_iter) * 8) && al((void **)&err, 16);
     if (ok && prec == PREC_FP32) ok = al((void **)&Wrm, (size_t)F * K * 4);
-    if (ok && prec == PREC_MIXED) ok = al((void **)&Wimg, (size_t)sh.Kp * sh.WLD * 2);
+    if (ok && prec != PREC_FP32) ok = al((void **)&Wimg, (size_t)sh.Kp * sh.WLD * 2);
+    if (ok && prec == PREC_TC) ok = al((void **)&Wrow, (size_t)F * sh.Kp * 2);
     auto cleanup = [&]() {
         for (void *p : owned) cudaFreeAsync(p, q);
     };
@@ -643,9 +674,10 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
     }
     cudaError_t e = cudaSuccess;
     if (Wimg) e = cudaMemsetAsync(Wimg, 0, (size_t)sh.Kp * sh.WLD * 2, q);
+    if (Wrow && e == cudaSuccess) e = cudaMemsetAsync(Wrow, 0, (size_t)F * sh.Kp * 2, q);
     if (e == cudaSuccess) e = cudaMemsetAsync(Hg, 0, (size_t)betap * sh.Kh * elem, q);
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 16, q);
-    const size_t tsm = tile_smem_bytes(sh, prec);
+    const size_t tsm = tc_min_smem(prec, tile_smem_bytes(sh, prec));
     const int tgrid = (int)std::min<long long>(ntiles, 2LL * nsm);
     TileArgs a;
     memset(&a, 0, sizeof a);
@@ -658,12 +690,13 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
     a.Wcm = W;
     a.Wrm = Wrm;
     a.Wimg = Wimg;
+    a.Wrow = Wrow;
     a.swpart = swp;
     a.err = err;
     a.betap = betap;
     for (int it = 0; it < n_iter && e == cudaSuccess; ++it) {
         // H step (its first X gives the objective of the previous iterate)
-        e = launch_prepare(sh, W, Wrm, Wimg, swp, q);
+        e = launch_prepare(sh, W, Wrm, Wimg, swp, q, Wrow);
         TileArgs h = a;
         h.n_in = 1;
         h.H_in = H;
@@ -694,7 +727,7 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
     }
     if (e == cudaSuccess && obj_out) {
         // objective of the final iterate
-        e = launch_prepare(sh, W, Wrm, Wimg, swp, q);
+        e = launch_prepare(sh, W, Wrm, Wimg, swp, q, Wrow);
         TileArgs o = a;
         o.n_in = 0;
         o.H_in = H;

@@ -271,7 +271,8 @@ static __device__ void hsolve_tile_fp32(const Shape &s, float eps, float gamma, 
 
 // ----------------------------------------------------------------- MIXED
 
-constexpr int kMtMax = 8;  // m16 row tiles of x = eps + W h per warp (F <= 1024)
+constexpr int kMtMax = 5;    // m16 row tiles of x = eps + W h per warp per pass
+constexpr int kFtCache = 0;  // f16 steps of W^T kept in registers (0: read from shared memory)
 
 struct MixedLayout {
     size_t w, pq, h, yraw, yt, misc, total;  // byte offsets
@@ -426,38 +427,51 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
     }
     __syncthreads();
 
+    // step B can keep W^T's fragments in registers for the whole tile
+    // (kFtCache f16 steps); at 256 threads that costs more in register
+    // pressure than it saves in shared-memory traffic, so it is off
+    const bool wcached = kFtCache > 0 && FT <= kFtCache;
+    uint32_t wb[kFtCache > 0 ? kFtCache : 1][4];
+    if (hown && wcached) {
+        const __nv_bfloat16 *brow = W_s + (16 * warp + r8 + 8 * (mi >> 1)) * WLD + 8 * (mi & 1);
+#pragma unroll
+        for (int fs = 0; fs < kFtCache; ++fs)
+            if (fs < FT) ldmatrix_x4(wb[fs], brow + 16 * fs);
+    }
+
     float lacc = 0.f;
     for (int it = 0;; ++it) {
         const bool last = (it == t.n_in);
         if (last && !t.final_pass) break;
         const bool want_loss = (last && t.final_pass) || (it == 0 && t.loss_first);
-        // ---- step A: x = eps + W h
-        {
+        // ---- step A: x = eps + W h (groups of kMtMax m16 tiles per warp;
+        //      every ldmatrix of a k-step is issued before its MMAs)
+        for (int mg = warp; mg < FT; mg += kWarps * kMtMax) {
             float d[kMtMax][4];
 #pragma unroll
             for (int i = 0; i < kMtMax; ++i)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) d[i][e] = eps;
-            const __nv_bfloat16 *wa = W_s + (r8 + 8 * (mi >> 1)) * WLD + 8 * (mi & 1) + 16 * warp;
+            const __nv_bfloat16 *wa = W_s + (r8 + 8 * (mi >> 1)) * WLD + 8 * (mi & 1) + 16 * mg;
 #pragma unroll
             for (int ks = 0; ks < KS; ++ks) {
                 const uint32_t b0 =
                     *reinterpret_cast<const uint32_t *>(H_s + g * HLD + 16 * ks + 2 * tq);
                 const uint32_t b1 =
                     *reinterpret_cast<const uint32_t *>(H_s + g * HLD + 16 * ks + 8 + 2 * tq);
+                uint32_t a[kMtMax][4];
 #pragma unroll
-                for (int i = 0; i < kMtMax; ++i) {
-                    if (warp + kWarps * i < FT) {
-                        uint32_t a[4];
-                        ldmatrix_x4_trans(a, wa + 16 * ks * WLD + 16 * kWarps * i);
-                        mma_bf16_16816(d[i], a, b0, b1);
-                    }
-                }
+                for (int i = 0; i < kMtMax; ++i)
+                    if (mg + kWarps * i < FT)
+                        ldmatrix_x4_trans(a[i], wa + 16 * ks * WLD + 16 * kWarps * i);
+#pragma unroll
+                for (int i = 0; i < kMtMax; ++i)
+                    if (mg + kWarps * i < FT) mma_bf16_16816(d[i], a[i], b0, b1);
             }
             // p = y/x^2, q = 1/x (FP32), bf16, stored transposed: PQ_s[j][f], PQ_s[8+j][f]
 #pragma unroll
             for (int i = 0; i < kMtMax; ++i) {
-                const int mt = warp + kWarps * i;
+                const int mt = mg + kWarps * i;
                 if (mt < FT) {
                     const int f0 = 16 * mt;
                     const float2 ya = *reinterpret_cast<const float2 *>(yT + (f0 + g) * 8 + 2 * tq);
@@ -495,17 +509,37 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
 #pragma unroll
                 for (int e = 0; e < 4; ++e) c0[u][e] = c1[u][e] = 0.f;
             const __nv_bfloat16 *arow = PQ_s + (r8 + 8 * (mi & 1)) * WLD + 8 * (mi >> 1);
-            const __nv_bfloat16 *brow = W_s + (16 * warp + r8 + 8 * (mi >> 1)) * WLD + 8 * (mi & 1);
-            for (int fs = 0; fs < FT; fs += 4) {
+            if (wcached) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (fs + u < FT) {
-                        uint32_t a[4], b[4];
-                        ldmatrix_x4(a, arow + 16 * (fs + u));
-                        ldmatrix_x4(b, brow + 16 * (fs + u));
-                        mma_bf16_16816(c0[u], a, b[0], b[1]);
-                        mma_bf16_16816(c1[u], a, b[2], b[3]);
-                    }
+                for (int fs = 0; fs < kFtCache; fs += 4) {
+                    uint32_t a[4][4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (fs + u < kFtCache && fs + u < FT) ldmatrix_x4(a[u], arow + 16 * (fs + u));
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (fs + u < kFtCache && fs + u < FT) {
+                            mma_bf16_16816(c0[u], a[u], wb[fs + u][0], wb[fs + u][1]);
+                            mma_bf16_16816(c1[u], a[u], wb[fs + u][2], wb[fs + u][3]);
+                        }
+                }
+            } else {
+                const __nv_bfloat16 *brow =
+                    W_s + (16 * warp + r8 + 8 * (mi >> 1)) * WLD + 8 * (mi & 1);
+                for (int fs = 0; fs < FT; fs += 4) {
+                    uint32_t a[4][4], b[4][4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (fs + u < FT) {
+                            ldmatrix_x4(a[u], arow + 16 * (fs + u));
+                            ldmatrix_x4(b[u], brow + 16 * (fs + u));
+                        }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (fs + u < FT) {
+                            mma_bf16_16816(c0[u], a[u], b[u][0], b[u][1]);
+                            mma_bf16_16816(c1[u], a[u], b[u][2], b[u][3]);
+                        }
                 }
             }
             float n0[4], n1[4];

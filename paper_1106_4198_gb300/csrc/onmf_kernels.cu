@@ -14,7 +14,8 @@ namespace onmf {
 // Derived images of a dictionary W (column-major F x K): the row-major copy,
 // the bf16 W^T image and the column sums. One warp per column.
 __global__ void __launch_bounds__(kThreads) prepare_kernel(Shape s, const float *Wcm, float *Wrm,
-                                                           __nv_bfloat16 *Wimg, float *swpart) {
+                                                           __nv_bfloat16 *Wimg,
+                                                           __nv_bfloat16 *Wrow, float *swpart) {
     const int lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kWarps + (threadIdx.x >> 5);
     const int nw = gridDim.x * kWarps;
@@ -25,6 +26,7 @@ __global__ void __launch_bounds__(kThreads) prepare_kernel(Shape s, const float 
             sum += w;
             if (Wrm) Wrm[(long long)f * s.K + k] = w;
             if (Wimg) Wimg[(long long)k * s.WLD + f] = __float2bfloat16_rn(w);
+            if (Wrow) Wrow[(long long)f * s.Kp + k] = __float2bfloat16_rn(w);
         }
         sum = warp_sum(sum);
         if (lane == 0) swpart[k] = sum;
@@ -120,35 +122,40 @@ static int64_t g_launches = 0;
 int64_t kernel_launches() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 static void count_launch(int n = 1) { __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED); }
 
+static size_t hsolve_smem(const Shape &s, int prec) {
+    if (prec == PREC_TC) return tc_layout(s).total;
+    return prec == PREC_MIXED ? mixed_layout(s).total : hsolve_fp32_smem_bytes(s);
+}
+
+bool tc_shape_supported(const Shape &s) { return tc_supported(s); }
+
 size_t online_smem_bytes(const Shape &s, int prec) {
-    size_t p1 = prec == PREC_MIXED ? mixed_layout(s).total : hsolve_fp32_smem_bytes(s);
+    size_t p1 = hsolve_smem(s, prec);
     size_t p2 = stats_smem_bytes(prec);
     return p1 > p2 ? p1 : p2;
 }
 
-size_t tile_smem_bytes(const Shape &s, int prec) {
-    return prec == PREC_MIXED ? mixed_layout(s).total : hsolve_fp32_smem_bytes(s);
-}
+size_t tile_smem_bytes(const Shape &s, int prec) { return hsolve_smem(s, prec); }
 
 size_t batch_stats_smem_bytes(int prec) { return stats_smem_bytes(prec); }
 
 // Mixed-precision kernels are instantiated per k-slab count in
 // onmf_mixed_lo.cu (1..4) and onmf_mixed_hi.cu (5..8).
-const void *mixed_online_lo(int ks);
-const void *mixed_online_hi(int ks);
-const void *mixed_tile_lo(int ks);
-const void *mixed_tile_hi(int ks);
+const void *mixed_online_lo(int prec, int ks);
+const void *mixed_online_hi(int prec, int ks);
+const void *mixed_tile_lo(int prec, int ks);
+const void *mixed_tile_hi(int prec, int ks);
 
 static const void *online_fn(int prec, int ks) {
-    if (prec != PREC_MIXED) return (const void *)online_kernel<PREC_FP32, 0>;
-    return ks <= 4 ? mixed_online_lo(ks) : mixed_online_hi(ks);
+    if (prec == PREC_FP32) return (const void *)online_kernel<PREC_FP32, 0>;
+    return ks <= 4 ? mixed_online_lo(prec, ks) : mixed_online_hi(prec, ks);
 }
 static const void *tile_fn(int prec, int ks) {
-    if (prec != PREC_MIXED) return (const void *)tile_kernel<PREC_FP32, 0>;
-    return ks <= 4 ? mixed_tile_lo(ks) : mixed_tile_hi(ks);
+    if (prec == PREC_FP32) return (const void *)tile_kernel<PREC_FP32, 0>;
+    return ks <= 4 ? mixed_tile_lo(prec, ks) : mixed_tile_hi(prec, ks);
 }
 static const void *bstats_fn(int prec) {
-    return prec == PREC_MIXED ? (const void *)batch_stats_kernel<PREC_MIXED>
+    return prec != PREC_FP32 ? (const void *)batch_stats_kernel<PREC_MIXED>
                               : (const void *)batch_stats_kernel<PREC_FP32>;
 }
 
@@ -162,10 +169,11 @@ cudaError_t configure_kernels() {
         cudaSuccess)
         return e;
     std::vector<const void *> fns = {online_fn(0, 0), tile_fn(0, 0), bstats_fn(0), bstats_fn(1)};
-    for (int ks = 1; ks <= 8; ++ks) {
-        fns.push_back(online_fn(1, ks));
-        fns.push_back(tile_fn(1, ks));
-    }
+    for (int p = PREC_MIXED; p <= PREC_TC; ++p)
+        for (int ks = 1; ks <= 8; ++ks) {
+            fns.push_back(online_fn(p, ks));
+            fns.push_back(tile_fn(p, ks));
+        }
     for (const void *fn : fns) {
         cudaFuncAttributes at;
         if ((e = cudaFuncGetAttributes(&at, fn)) != cudaSuccess) return e;
@@ -184,10 +192,11 @@ size_t max_dynamic_smem() {
     cudaFuncAttributes at;
     size_t worst = 0;
     std::vector<const void *> fns = {online_fn(0, 0), tile_fn(0, 0)};
-    for (int ks = 1; ks <= 8; ++ks) {
-        fns.push_back(online_fn(1, ks));
-        fns.push_back(tile_fn(1, ks));
-    }
+    for (int p = PREC_MIXED; p <= PREC_TC; ++p)
+        for (int ks = 1; ks <= 8; ++ks) {
+            fns.push_back(online_fn(p, ks));
+            fns.push_back(tile_fn(p, ks));
+        }
     for (const void *fn : fns)
         if (cudaFuncGetAttributes(&at, fn) == cudaSuccess && at.sharedSizeBytes > worst)
             worst = at.sharedSizeBytes;
@@ -205,8 +214,8 @@ cudaError_t launch_online(const StepArgs &a, int prec, int grid, size_t smem,
     if (e != cudaSuccess) return e;
     StepArgs copy = a;
     void *args[] = {&copy};
-    e = cudaLaunchCooperativeKernel(online_fn(prec, a.s.Kp / 16), dim3(grid), dim3(kThreads), args,
-                                    smem, stream);
+    e = cudaLaunchCooperativeKernel(online_fn(prec, a.s.Kp / 16), dim3(grid), dim3(kThreads),
+                                    args, smem, stream);
     if (e == cudaSuccess) count_launch();
     return e;
 }
@@ -221,9 +230,9 @@ cudaError_t launch_tiles(const TileArgs &a, int prec, int grid, size_t smem, cud
 }
 
 cudaError_t launch_prepare(const Shape &s, const float *Wcm, float *Wrm, __nv_bfloat16 *Wimg,
-                           float *swpart, cudaStream_t stream) {
+                           float *swpart, cudaStream_t stream, __nv_bfloat16 *Wrow) {
     const int grid = (s.K + kWarps - 1) / kWarps;
-    prepare_kernel<<<grid, kThreads, 0, stream>>>(s, Wcm, Wrm, Wimg, swpart);
+    prepare_kernel<<<grid, kThreads, 0, stream>>>(s, Wcm, Wrm, Wimg, Wrow, swpart);
     count_launch();
     return cudaGetLastError();
 }

@@ -21,9 +21,11 @@ namespace onmf {
 
 constexpr int kThreads = 256;  // threads per CTA for every kernel here
 constexpr int kWarps = kThreads / 32;
-constexpr int kTile = 8;       // frames per h-solve tile
+constexpr int kTile = 8;       // frames per h-solve tile (mma.sync and FP32 paths)
+constexpr int kTcTile = 16;    // frames per h-solve tile (tcgen05 path)
 
-enum Prec : int { PREC_FP32 = 0, PREC_MIXED = 1 };
+// PREC_TC: the mixed-precision arithmetic with the tcgen05 (TMEM) h-solve.
+enum Prec : int { PREC_FP32 = 0, PREC_MIXED = 1, PREC_TC = 2 };
 
 struct Shape {
     int F, K;
@@ -65,6 +67,7 @@ struct StepArgs {
     float *Wcm;
     float *Wrm;
     __nv_bfloat16 *Wimg;
+    __nv_bfloat16 *Wrow;  // tensor-core path: bf16 W, row f = row f of W (ld Kp)
     float *Wn;
     double *A, *B;
     double *loss_sum;
@@ -95,6 +98,7 @@ struct TileArgs {
     const float *Wcm;
     const float *Wrm;
     const __nv_bfloat16 *Wimg;
+    const __nv_bfloat16 *Wrow;
     const float *swpart;
     void *Pg, *Qg, *Hg;
     long long betap;

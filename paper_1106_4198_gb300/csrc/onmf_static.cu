@@ -5,6 +5,7 @@
 // their own. This entry point keeps its scratch (the derived images of W, the
 // column sums and the per-tile loss slots) in one fixed device array below;
 // the caller passes inputs and outputs.
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -60,16 +61,26 @@ extern "C" onmf_status onmf_project_static(const float *W, int32_t F, int32_t K,
         (precision != ONMF_FP32 && precision != ONMF_MIXED) || K > 256 || F > 8192)
         return ONMF_EINVAL;
     if (precision == ONMF_MIXED && (K > 128 || F > 1024)) return ONMF_EINVAL;
-    const int prec = precision == ONMF_MIXED ? PREC_MIXED : PREC_FP32;
     const Shape sh = make_shape(F, K);
-    const long long ntiles = (n + kTile - 1) / kTile;
-    // scratch layout: [W image][column sums][per-tile loss]
-    const size_t img = prec == PREC_MIXED ? (size_t)sh.Kp * sh.WLD * 2 : (size_t)F * K * 4;
-    const size_t off_sw = align256(img);
+    // the same h-solve as onmf_project: tcgen05 where the shape allows it
+    int prec = PREC_FP32;
+    if (precision == ONMF_MIXED) {
+        const char *env = getenv("ONMF_HSOLVE");
+        const bool tc = env && strcmp(env, "tc") == 0;
+        prec = (tc && tc_shape_supported(sh)) ? PREC_TC : PREC_MIXED;
+    }
+    const int tile = prec == PREC_TC ? kTcTile : kTile;
+    const long long ntiles = (n + tile - 1) / tile;
+    // scratch layout: [W image][row-major bf16 W (tcgen05)][column sums][per-tile loss]
+    const size_t img = prec == PREC_FP32 ? (size_t)F * K * 4 : (size_t)sh.Kp * sh.WLD * 2;
+    const size_t rows = prec == PREC_TC ? (size_t)F * sh.Kp * 2 : 0;
+    const size_t off_rows = align256(img);
+    const size_t off_sw = off_rows + align256(rows);
     const size_t off_loss = off_sw + align256((size_t)K * 4);
     const size_t need = off_loss + (size_t)(ntiles > 0 ? ntiles : 1) * 8;
     if (need > ONMF_STATIC_SCRATCH_BYTES - 256) return ONMF_EINVAL;
-    const size_t smem = tile_smem_bytes(sh, prec);
+    size_t smem = tile_smem_bytes(sh, prec);
+    if (prec == PREC_TC && smem < 116 * 1024) smem = 116 * 1024;  // one CTA per SM (TMEM)
     if (smem > max_dynamic_smem()) return ONMF_EINVAL;
     void *base = nullptr;
     onmf_status st = scratch_address(&base);
@@ -77,13 +88,16 @@ extern "C" onmf_status onmf_project_static(const float *W, int32_t F, int32_t K,
     unsigned char *b = static_cast<unsigned char *>(base);
     cudaStream_t q = reinterpret_cast<cudaStream_t>(stream);
     float *Wrm = prec == PREC_FP32 ? reinterpret_cast<float *>(b) : nullptr;
-    __nv_bfloat16 *Wimg = prec == PREC_MIXED ? reinterpret_cast<__nv_bfloat16 *>(b) : nullptr;
+    __nv_bfloat16 *Wimg = prec != PREC_FP32 ? reinterpret_cast<__nv_bfloat16 *>(b) : nullptr;
+    __nv_bfloat16 *Wrow =
+        prec == PREC_TC ? reinterpret_cast<__nv_bfloat16 *>(b + off_rows) : nullptr;
     float *swpart = reinterpret_cast<float *>(b + off_sw);
     double *loss = reinterpret_cast<double *>(b + off_loss);
     // the padding of the bf16 image must read as zero whatever an earlier
     // call of another shape left there
     if (Wimg && cudaMemsetAsync(Wimg, 0, img, q) != cudaSuccess) return ONMF_ECUDA;
-    if (launch_prepare(sh, W, Wrm, Wimg, swpart, q) != cudaSuccess) return ONMF_ECUDA;
+    if (Wrow && cudaMemsetAsync(Wrow, 0, rows, q) != cudaSuccess) return ONMF_ECUDA;
+    if (launch_prepare(sh, W, Wrm, Wimg, swpart, q, Wrow) != cudaSuccess) return ONMF_ECUDA;
     if (n == 0) {
         if (obj_sum && cudaMemsetAsync(obj_sum, 0, sizeof(double), q) != cudaSuccess)
             return ONMF_ECUDA;
@@ -104,6 +118,7 @@ extern "C" onmf_status onmf_project_static(const float *W, int32_t F, int32_t K,
     a.Wcm = W;
     a.Wrm = Wrm;
     a.Wimg = Wimg;
+    a.Wrow = Wrow;
     a.swpart = swpart;
     a.loss_part = obj_sum ? loss : nullptr;
     // the kernel's input-check flag goes to the last 256 bytes of the scratch;

@@ -19,6 +19,7 @@
 #include "onmf_device.cuh"
 #include "onmf_hsolve.cuh"
 #include "onmf_kernels.cuh"
+#include "onmf_tc.cuh"
 
 namespace onmf {
 
@@ -29,7 +30,7 @@ constexpr int kPS = 24;       // row stride (bf16) of the P/Q chunk rows
 constexpr int kHS = kChunk + 8;
 
 __host__ __device__ inline size_t stats_smem_bytes(int prec) {
-    if (prec == PREC_MIXED)
+    if (prec != PREC_FP32)
         return (size_t)2 * kChunk * kPS * 2 + (size_t)32 * kHS * 2 + 2 * 16 * 32 * 4;
     return (size_t)kWarps * 16 * 32 * 2 * 4 + 2 * 16 * 32 * 4;
 }
@@ -162,7 +163,7 @@ __device__ __forceinline__ void stats_unit(const Shape &s, int mt, int ks, const
                                            const void *Qg, const void *Hg, long long betap,
                                            long long jb, long long je, unsigned char *smem,
                                            float *acc) {
-    if (PREC == PREC_MIXED)
+    if (PREC != PREC_FP32)
         stats_unit_mixed(s, mt, ks, reinterpret_cast<const __nv_bfloat16 *>(Pg),
                          reinterpret_cast<const __nv_bfloat16 *>(Qg),
                          reinterpret_cast<const __nv_bfloat16 *>(Hg), betap, jb, je, smem, acc);
@@ -217,7 +218,8 @@ __device__ __forceinline__ float block_sum_f(float v, float *red8) {
 template <int PREC>
 static __device__ void normalize_columns(const Shape &s, int normalize, const float *__restrict__ Wn,
                                   float *__restrict__ Wcm, float *__restrict__ Wrm,
-                                  __nv_bfloat16 *__restrict__ Wimg, double *__restrict__ A,
+                                  __nv_bfloat16 *__restrict__ Wimg,
+                                  __nv_bfloat16 *__restrict__ Wrow, double *__restrict__ A,
                                   double *__restrict__ B, float *__restrict__ swpart, int *err,
                                   float *red8) {
     const int F = s.F, K = s.K;
@@ -259,10 +261,12 @@ static __device__ void normalize_columns(const Shape &s, int normalize, const fl
                         A[i] = av[u] * invd;
                         B[i] = bv[u] * sd;
                     }
-                    if (PREC == PREC_FP32)
+                    if (PREC == PREC_FP32) {
                         Wrm[(long long)f * K + k] = wv;
-                    else
+                    } else {
                         Wimg[(long long)k * s.WLD + f] = __float2bfloat16_rn(wv);
+                        if (PREC == PREC_TC) Wrow[(long long)f * s.Kp + k] = __float2bfloat16_rn(wv);
+                    }
                 }
             }
         }
@@ -305,17 +309,22 @@ __device__ __forceinline__ void hsolve_tile(const Shape &s, float eps, float gam
 template <int PREC, int KS>
 __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[4];
     __shared__ float s_tmp;
     __shared__ float s_red8[kWarps];
     __shared__ double s_red[kThreads];
+    __shared__ uint32_t s_tslot;
     if (threadIdx.x == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int i = 0; i < 4; ++i) mbar_init(&mbar[i], 1);
         fence_mbar_init();
     }
+    if (PREC == PREC_TC && threadIdx.x < 32) tmem_alloc(&s_tslot, kTmemCols);
+    tc_fence_before();
     __syncthreads();
-    unsigned wpar = 0, vpar = 0, epoch = 0;
+    tc_fence_after();
+    const uint32_t tbase = PREC == PREC_TC ? s_tslot : 0u;
+    unsigned wpar = 0, vpar = 0, epoch = 0, parA = 0, parB = 0;
+    constexpr int TILE = PREC == PREC_TC ? kTcTile : kTile;
     const unsigned G = gridDim.x;
     const Shape &s = a.s;
     const int FT = s.Fp16 / 16, KT = s.Kh / 32;
@@ -327,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
         const double rho = lastmb ? a.rho_last : a.rho_full;
         const float *Vm = a.V + (long long)m * a.beta * a.ldv;
         float *Hm = a.H_out ? a.H_out + (long long)m * a.beta * a.ldh : nullptr;
-        const int ntiles = ceil_div(nb, kTile);
+        const int ntiles = ceil_div(nb, TILE);
         // ---- phase 1: h-solve of every tile
         if ((int)blockIdx.x < ntiles) {
             const float sw = sum_w(a.swpart, s.K, &s_tmp);
@@ -336,12 +345,13 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                 issue_wimg(s, a.Wimg, smem, &mbar[0]);
                 ws.pending = true;
             }
+            if (PREC == PREC_TC) stage_w_tc(s, tc_layout(s), a.Wimg, a.Wrow, a.Wcm, tbase, smem);
             for (int tile = blockIdx.x; tile < ntiles; tile += G) {
                 TileJob t;
-                t.Vt = Vm + (long long)tile * kTile * a.ldv;
+                t.Vt = Vm + (long long)tile * TILE * a.ldv;
                 t.ldv = a.ldv;
-                t.nvalid = min(kTile, nb - tile * kTile);
-                t.j0 = (long long)tile * kTile;
+                t.nvalid = min(TILE, nb - tile * TILE);
+                t.j0 = (long long)tile * TILE;
                 t.H_in = nullptr;
                 t.ldh_in = 0;
                 t.H_out = Hm;
@@ -354,11 +364,15 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                 t.Qg = a.Qg;
                 t.Hg = a.Hg;
                 t.betap = a.betap;
-                hsolve_tile<PREC, KS>(s, a.eps, a.gamma, a.Wcm, a.Wrm, sw, t, smem, ws, &mbar[1],
-                                      vpar, a.err);
+                if constexpr (PREC == PREC_TC)
+                    hsolve_tile_tc<KS>(s, a.eps, a.gamma, sw, t, smem, tbase, &mbar[2], &mbar[3],
+                                       parA, parB, &mbar[1], vpar, a.err);
+                else
+                    hsolve_tile<PREC, KS>(s, a.eps, a.gamma, a.Wcm, a.Wrm, sw, t, smem, ws,
+                                          &mbar[1], vpar, a.err);
             }
         }
-        if (!grid_sync(a.bar, G, epoch, a.err)) return;
+        if (!grid_sync(a.bar, G, epoch, a.err)) break;
         // ---- phase 2: statistics and W' = sqrt(A/B)
         for (int u = blockIdx.x; u < nunits; u += G) {
             const int mt = u % FT, ks = u / FT;
@@ -366,16 +380,21 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
             online_epilogue(a, mt, ks, rho, acc);
             __syncthreads();
         }
-        if (!grid_sync(a.bar, G, epoch, a.err)) return;
+        if (!grid_sync(a.bar, G, epoch, a.err)) break;
         // ---- phase 3: column sums, rescale, images, loss
-        normalize_columns<PREC>(s, a.normalize, a.Wn, a.Wcm, a.Wrm, a.Wimg, a.A, a.B, a.swpart,
-                                a.err, s_red8);
+        normalize_columns<PREC>(s, a.normalize, a.Wn, a.Wcm, a.Wrm, a.Wimg, a.Wrow, a.A, a.B,
+                                a.swpart, a.err, s_red8);
         if (blockIdx.x == G - 1) {
             double l = block_sum_ordered(a.loss_part, ntiles, s_red);
             if (threadIdx.x == 0) *a.loss_sum += l;
         }
-        if (PREC == PREC_MIXED) asm volatile("fence.proxy.async.global;\n" ::: "memory");
-        if (!lastmb && !grid_sync(a.bar, G, epoch, a.err)) return;
+        if (PREC != PREC_FP32) asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        if (!lastmb && !grid_sync(a.bar, G, epoch, a.err)) break;
+    }
+    if (PREC == PREC_TC) {
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x < 32) tmem_dealloc(tbase, kTmemCols);
     }
 }
 
@@ -384,29 +403,35 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
 template <int PREC, int KS>
 __global__ void __launch_bounds__(kThreads, 1) tile_kernel(TileArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar[4];
     __shared__ float s_tmp;
+    __shared__ uint32_t s_tslot;
+    constexpr int TILE = PREC == PREC_TC ? kTcTile : kTile;
+    const long long ntiles = (a.n + TILE - 1) / TILE;
+    if ((long long)blockIdx.x >= ntiles) return;
     if (threadIdx.x == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
+        for (int i = 0; i < 4; ++i) mbar_init(&mbar[i], 1);
         fence_mbar_init();
     }
+    if (PREC == PREC_TC && threadIdx.x < 32) tmem_alloc(&s_tslot, kTmemCols);
+    tc_fence_before();
     __syncthreads();
-    unsigned wpar = 0, vpar = 0;
-    const long long ntiles = (a.n + kTile - 1) / kTile;
-    if ((long long)blockIdx.x >= ntiles) return;
+    tc_fence_after();
+    const uint32_t tbase = PREC == PREC_TC ? s_tslot : 0u;
+    unsigned wpar = 0, vpar = 0, parA = 0, parB = 0;
     const float sw = sum_w(a.swpart, a.s.K, &s_tmp);
     WStage ws{&mbar[0], &wpar, false};
     if (PREC == PREC_MIXED) {
         issue_wimg(a.s, a.Wimg, smem, &mbar[0]);
         ws.pending = true;
     }
+    if (PREC == PREC_TC) stage_w_tc(a.s, tc_layout(a.s), a.Wimg, a.Wrow, a.Wcm, tbase, smem);
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         TileJob t;
-        t.Vt = a.V + tile * kTile * a.ldv;
+        t.Vt = a.V + tile * TILE * a.ldv;
         t.ldv = a.ldv;
-        t.nvalid = (int)min((long long)kTile, a.n - tile * kTile);
-        t.j0 = tile * kTile;
+        t.nvalid = (int)min((long long)TILE, a.n - tile * TILE);
+        t.j0 = tile * TILE;
         t.H_in = a.H_in;
         t.ldh_in = a.ldh_in;
         t.H_out = a.H_out;
@@ -419,8 +444,17 @@ __global__ void __launch_bounds__(kThreads, 1) tile_kernel(TileArgs a) {
         t.Qg = a.Qg;
         t.Hg = a.Hg;
         t.betap = a.betap;
-        hsolve_tile<PREC, KS>(a.s, a.eps, a.gamma, a.Wcm, a.Wrm, sw, t, smem, ws, &mbar[1], vpar,
-                              a.err);
+        if constexpr (PREC == PREC_TC)
+            hsolve_tile_tc<KS>(a.s, a.eps, a.gamma, sw, t, smem, tbase, &mbar[2], &mbar[3], parA,
+                               parB, &mbar[1], vpar, a.err);
+        else
+            hsolve_tile<PREC, KS>(a.s, a.eps, a.gamma, a.Wcm, a.Wrm, sw, t, smem, ws, &mbar[1],
+                                  vpar, a.err);
+    }
+    if (PREC == PREC_TC) {
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x < 32) tmem_dealloc(tbase, kTmemCols);
     }
 }
 

@@ -71,9 +71,14 @@ def test_batch_c1_objective_trajectory():
     assert np.all(np.diff(objg) <= 1e-6 * objg[:-1])
 
 
-def test_batch_mixed_objective_stated():
-    """Mixed precision batch cycles (BF16 products): objective within 1e-3
-    of the FP64 oracle at every cycle (config-1 shape, 50 cycles)."""
+@pytest.mark.parametrize("hsolve", ["mma", "tc"])
+def test_batch_mixed_objective_stated(hsolve, monkeypatch):
+    """Mixed precision batch cycles (BF16 products, both h-solves): objective
+    within 1e-3 of the FP64 oracle at every cycle (config-1 shape, 50 cycles)."""
+    if hsolve == "tc":
+        monkeypatch.setenv("ONMF_HSOLVE", "tc")
+    else:
+        monkeypatch.delenv("ONMF_HSOLVE", raising=False)
     F, K, N, it = 129, 8, 2000, 50
     V, W0 = problem(F, K, N)
     H0 = oracle.batch_h0(V, W0)

@@ -130,7 +130,7 @@ def test_host_input_matches_device_input():
     assert np.array_equal(a["W"], b["W"]) and np.array_equal(a["H"], b["H"])
 
 
-def test_scale_equivariance_bitwise_gpu():
+def test_scale_equivariance_bitwise_gpu(hsolve):
     """eps = 0: V -> 4V leaves W, A, B bit-identical and scales H by 4
     (power-of-two scaling is exact and every ratio is invariant)."""
     F, K, beta = 129, 8, 50
@@ -235,8 +235,20 @@ def test_projection_block_diagonal_closed_form():
     assert worst <= 1e-5
 
 
-@pytest.mark.parametrize("F,K,beta,n_in", [(129, 8, 50, 5), (513, 100, 1000, 10)])
-def test_mixed_single_minibatch_error_stated(F, K, beta, n_in):
+@pytest.fixture(params=["mma", "tc"])
+def hsolve(request, monkeypatch):
+    """Mixed precision has two h-solves: mma.sync (default) and tcgen05
+    (ONMF_HSOLVE=tc); every mixed test runs on both."""
+    if request.param == "tc":
+        monkeypatch.setenv("ONMF_HSOLVE", "tc")
+    else:
+        monkeypatch.delenv("ONMF_HSOLVE", raising=False)
+    return request.param
+
+
+@pytest.mark.parametrize("F,K,beta,n_in", [(129, 8, 50, 5), (513, 100, 1000, 10),
+                                           (513, 128, 512, 10), (256, 40, 37, 4)])
+def test_mixed_single_minibatch_error_stated(F, K, beta, n_in, hsolve):
     """Mixed precision (BF16 tensor-core products, FP32 ratios, FP64 A/B):
     one minibatch against the FP64 oracle. Stated bounds: W, A, B, H within
     1e-2 and the minibatch loss within 1e-3."""
@@ -246,7 +258,7 @@ def test_mixed_single_minibatch_error_stated(F, K, beta, n_in):
     errs = dict(W=relerr(g["W"], o["W"]), A=relerr(g["A"], o["A"]),
                 B=relerr(g["B"], o["B"]), H=relerr(g["H"], o["H"]),
                 loss=abs(g["loss_sum"] - o["loss_sum"]) / abs(o["loss_sum"]))
-    print("mixed errors:", {k: "%.2e" % v for k, v in errs.items()})
+    print("mixed (%s) errors:" % hsolve, {k: "%.2e" % v for k, v in errs.items()})
     assert errs["loss"] <= 1e-3
     for k in ("W", "A", "B", "H"):
         assert errs[k] <= 1e-2, (k, errs)
