@@ -199,6 +199,83 @@ onmf_status onmf_project_static(const float *W, int32_t F, int32_t K,
 /* Release the state and everything the library allocated for it. */
 void onmf_destroy(onmf_state *s);
 
+/* ------------------------------------------------------------------ serving
+ * Many concurrent streams, each its own run of Algorithm 1 (own W, A, B),
+ * fed chunk by chunk. Every chunk is one minibatch of that stream (beta' =
+ * chunk length, rho = r^(beta'/n_ref)): h-solve with the stream's W, then
+ * the statistics and the dictionary step. A worker thread batches the
+ * queued chunks of all admitted streams that have no chunk on the GPU into
+ * one kernel launch (continuous batching: chunks that arrive while a batch
+ * runs join the next one, and up to `slots` batches are in flight on
+ * separate CUDA streams). A chunk is computed by one CTA with a fixed order
+ * of operations, so its result does not depend on what it is batched with.
+ * Streams are admitted by a device-memory budget: a stream whose state does
+ * not fit waits (its chunks queue) until closed streams free memory. */
+
+typedef struct onmf_server onmf_server;
+
+typedef struct {
+    int32_t F;              /* frequency bins shared by all streams          */
+    int32_t max_chunk;      /* largest chunk in frames (<= 4096)             */
+    int32_t max_batch;      /* chunks per launch                             */
+    int32_t slots;          /* batches in flight (1..4)                      */
+    int64_t budget_bytes;   /* device memory for stream states               */
+    int32_t precision;      /* onmf_precision for all streams                */
+    int32_t reserved;       /* must be 0                                     */
+} onmf_server_config;
+
+typedef struct {
+    int64_t stream_id;
+    int64_t tag;            /* the caller's tag from onmf_server_submit      */
+    int64_t frames;
+    double loss;            /* sum of d_IS(eps+v, eps+W h) over the chunk    */
+    double t_submit;        /* seconds, CLOCK_MONOTONIC, at submit           */
+    double t_done;          /* seconds, when the worker saw the result ready */
+    int32_t status;         /* onmf_status of this chunk                     */
+    int32_t reserved;
+} onmf_completion;
+
+typedef struct {
+    int64_t launches, chunks, frames, batches_overlapped;
+    int64_t streams_admitted, streams_pending, bytes_in_use;
+} onmf_server_stats;
+
+/* Create a server (allocates the per-slot device buffers; the budget covers
+ * only stream states). Errors: EINVAL, ENOMEM, ECUDA. */
+onmf_status onmf_server_create(const onmf_server_config *cfg, onmf_server **out);
+
+/* Open a stream with its own parameters (cfg->F must equal the server's F;
+ * K <= 128; cfg->beta is ignored: chunks are the minibatches) and initial
+ * dictionary W0 (F x K, host). Returns its id; the stream is admitted now if
+ * its state fits the budget, else it waits in FIFO order. */
+onmf_status onmf_server_open_stream(onmf_server *srv, const onmf_config *cfg,
+                                    const float *W0, int64_t *stream_id);
+
+/* Queue a chunk of n frames (F x n host memory, leading dimension ldv) for
+ * a stream; the frames are copied before the call returns. H_out: NULL or
+ * host memory K x n (ld K) that receives the chunk's h when it completes.
+ * Errors: EINVAL (n < 1, n > max_chunk, unknown or closing stream). */
+onmf_status onmf_server_submit(onmf_server *srv, int64_t stream_id,
+                               const float *V, int64_t ldv, int64_t n,
+                               float *H_out, int64_t tag);
+
+/* Take up to max completions (oldest first), waiting up to wait_ms for the
+ * first one. *count receives how many were written (0 on timeout). */
+onmf_status onmf_server_poll(onmf_server *srv, onmf_completion *out,
+                             int32_t max, int32_t *count, int32_t wait_ms);
+
+/* Copy a stream's current W (F x K, host) once its queued chunks are done. */
+onmf_status onmf_server_get_W(onmf_server *srv, int64_t stream_id, float *W_out);
+
+/* Close a stream after its queued chunks complete; frees its device memory
+ * and admits waiting streams. */
+onmf_status onmf_server_close_stream(onmf_server *srv, int64_t stream_id);
+
+onmf_status onmf_server_get_stats(onmf_server *srv, onmf_server_stats *out);
+
+/* Stop the worker (after the work already queued) and free everything. */
+void onmf_server_destroy(onmf_server *srv);
+
 /* Static string naming a status. */
 const char *onmf_status_string(onmf_status st);
 

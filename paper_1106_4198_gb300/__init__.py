@@ -36,6 +36,9 @@ EXPORTED = [
     "onmf_project", "nmf_batch_step", "nmf_batch_init_H", "onmf_destroy",
     "onmf_status_string", "onmf_last_error_message", "onmf_kernel_launches",
     "onmf_abi_version", "onmf_project_static",
+    "onmf_server_create", "onmf_server_open_stream", "onmf_server_submit",
+    "onmf_server_poll", "onmf_server_get_W", "onmf_server_close_stream",
+    "onmf_server_get_stats", "onmf_server_destroy",
 ]
 
 
@@ -48,6 +51,30 @@ class onmf_config(ctypes.Structure):
         ("normalize", ctypes.c_int32), ("rho_on_new", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
+
+
+class onmf_server_config(ctypes.Structure):
+    _fields_ = [
+        ("F", ctypes.c_int32), ("max_chunk", ctypes.c_int32),
+        ("max_batch", ctypes.c_int32), ("slots", ctypes.c_int32),
+        ("budget_bytes", ctypes.c_int64), ("precision", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
+class onmf_completion(ctypes.Structure):
+    _fields_ = [
+        ("stream_id", ctypes.c_int64), ("tag", ctypes.c_int64),
+        ("frames", ctypes.c_int64), ("loss", ctypes.c_double),
+        ("t_submit", ctypes.c_double), ("t_done", ctypes.c_double),
+        ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class onmf_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "launches", "chunks", "frames", "batches_overlapped",
+        "streams_admitted", "streams_pending", "bytes_in_use")]
 
 
 class OnmfError(RuntimeError):
@@ -99,6 +126,18 @@ def lib():
                                       _i64, _d, _d, _i32, _i32, _vp, _vp]
     L.onmf_destroy.argtypes = [_vp]
     L.onmf_destroy.restype = None
+    L.onmf_server_create.argtypes = [ctypes.POINTER(onmf_server_config),
+                                     ctypes.POINTER(_vp)]
+    L.onmf_server_open_stream.argtypes = [_vp, ctypes.POINTER(onmf_config), _vp,
+                                          ctypes.POINTER(_i64)]
+    L.onmf_server_submit.argtypes = [_vp, _i64, _vp, _i64, _i64, _vp, _i64]
+    L.onmf_server_poll.argtypes = [_vp, ctypes.POINTER(onmf_completion), _i32,
+                                   ctypes.POINTER(_i32), _i32]
+    L.onmf_server_get_W.argtypes = [_vp, _i64, _vp]
+    L.onmf_server_close_stream.argtypes = [_vp, _i64]
+    L.onmf_server_get_stats.argtypes = [_vp, ctypes.POINTER(onmf_server_stats)]
+    L.onmf_server_destroy.argtypes = [_vp]
+    L.onmf_server_destroy.restype = None
     L.onmf_status_string.argtypes = [ctypes.c_int]
     L.onmf_status_string.restype = ctypes.c_char_p
     L.onmf_last_error_message.restype = ctypes.c_char_p
@@ -107,7 +146,10 @@ def lib():
     for name in ("onmf_init", "onmf_push_frames", "onmf_flush",
                  "onmf_synchronize", "onmf_get_W", "onmf_get_stats",
                  "onmf_set_state", "onmf_project", "nmf_batch_step",
-                 "nmf_batch_init_H", "onmf_project_static"):
+                 "nmf_batch_init_H", "onmf_project_static", "onmf_server_create",
+                 "onmf_server_open_stream", "onmf_server_submit", "onmf_server_poll",
+                 "onmf_server_get_W", "onmf_server_close_stream",
+                 "onmf_server_get_stats"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -338,3 +380,62 @@ class OnlineISNMF:
             self.close()
         except Exception:
             pass
+
+
+# ----------------------------------------------------------------- serving
+
+
+def onmf_server_create(F, max_chunk=512, max_batch=256, slots=2,
+                       budget_bytes=1 << 30, precision=ONMF_MIXED):
+    c = onmf_server_config(F, max_chunk, max_batch, slots, budget_bytes,
+                           precision, 0)
+    h = _vp()
+    _check(lib().onmf_server_create(ctypes.byref(c), ctypes.byref(h)),
+           "onmf_server_create")
+    return h
+
+
+def onmf_server_open_stream(srv, cfg, W0):
+    W0 = np.ascontiguousarray(W0, dtype=np.float32)
+    sid = _i64(0)
+    _check(lib().onmf_server_open_stream(srv, ctypes.byref(cfg), W0.ctypes.data,
+                                         ctypes.byref(sid)),
+           "onmf_server_open_stream")
+    return sid.value
+
+
+def onmf_server_submit(srv, sid, V, tag=0, H_out=None):
+    """Queue frames V (n, F) float32 host array; H_out (n, K) host array or None."""
+    V = np.ascontiguousarray(V, dtype=np.float32)
+    ph = H_out.ctypes.data if H_out is not None else None
+    _check(lib().onmf_server_submit(srv, sid, V.ctypes.data, V.shape[1], V.shape[0],
+                                    ph, int(tag)), "onmf_server_submit")
+
+
+def onmf_server_poll(srv, max_n=1024, wait_ms=0):
+    buf = (onmf_completion * max_n)()
+    n = _i32(0)
+    _check(lib().onmf_server_poll(srv, buf, max_n, ctypes.byref(n), wait_ms),
+           "onmf_server_poll")
+    return [buf[i] for i in range(n.value)]
+
+
+def onmf_server_get_W(srv, sid, K, F):
+    W = np.empty((K, F), dtype=np.float32)
+    _check(lib().onmf_server_get_W(srv, sid, W.ctypes.data), "onmf_server_get_W")
+    return W
+
+
+def onmf_server_close_stream(srv, sid):
+    _check(lib().onmf_server_close_stream(srv, sid), "onmf_server_close_stream")
+
+
+def onmf_server_get_stats(srv):
+    st = onmf_server_stats()
+    _check(lib().onmf_server_get_stats(srv, ctypes.byref(st)), "onmf_server_get_stats")
+    return {n: getattr(st, n) for n, _ in onmf_server_stats._fields_}
+
+
+def onmf_server_destroy(srv):
+    if srv:
+        lib().onmf_server_destroy(srv)

@@ -7,6 +7,7 @@
 #include "onmf_device.cuh"
 #include "onmf_kernels.cuh"
 #include "onmf_launch.h"
+#include "onmf_serve.cuh"
 #include "onmf_step.cuh"
 
 namespace onmf {
@@ -145,6 +146,14 @@ const void *mixed_online_lo(int prec, int ks);
 const void *mixed_online_hi(int prec, int ks);
 const void *mixed_tile_lo(int prec, int ks);
 const void *mixed_tile_hi(int prec, int ks);
+const void *mixed_serve_lo(int ks);
+const void *mixed_serve_hi(int ks);
+
+// Serving kernels: FP32 (one variant) or mixed, one per k16-slab count.
+const void *serve_fn(int prec, int ks) {
+    if (prec == PREC_FP32) return (const void *)serve_kernel<PREC_FP32, 0>;
+    return ks <= 4 ? mixed_serve_lo(ks) : mixed_serve_hi(ks);
+}
 
 static const void *online_fn(int prec, int ks) {
     if (prec == PREC_FP32) return (const void *)online_kernel<PREC_FP32, 0>;
@@ -168,12 +177,14 @@ cudaError_t configure_kernels() {
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
         cudaSuccess)
         return e;
-    std::vector<const void *> fns = {online_fn(0, 0), tile_fn(0, 0), bstats_fn(0), bstats_fn(1)};
+    std::vector<const void *> fns = {online_fn(0, 0), tile_fn(0, 0), bstats_fn(0), bstats_fn(1),
+                                     serve_fn(PREC_FP32, 0)};
     for (int p = PREC_MIXED; p <= PREC_TC; ++p)
         for (int ks = 1; ks <= 8; ++ks) {
             fns.push_back(online_fn(p, ks));
             fns.push_back(tile_fn(p, ks));
         }
+    for (int ks = 1; ks <= 8; ++ks) fns.push_back(serve_fn(PREC_MIXED, ks));
     for (const void *fn : fns) {
         cudaFuncAttributes at;
         if ((e = cudaFuncGetAttributes(&at, fn)) != cudaSuccess) return e;

@@ -35,7 +35,7 @@ struct Shape {
     int WLD;   // row stride of Wimg (Fp16 + 8)
 };
 
-inline Shape make_shape(int F, int K) {
+__host__ __device__ inline Shape make_shape(int F, int K) {
     Shape s;
     s.F = F;
     s.K = K;

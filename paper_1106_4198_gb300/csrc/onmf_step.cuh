@@ -175,29 +175,36 @@ __device__ __forceinline__ void stats_unit(const Shape &s, int mt, int ks, const
 
 // A <- rho A + a, B <- rho B + b, W' = sqrt(A/B) for the tile's entries
 // (Algorithm 1; the past-scaling reading of rho unless rho_on_new).
-static __device__ void online_epilogue(const StepArgs &a, int mt, int ks, double rho, const float *acc) {
-    const int F = a.s.F, K = a.s.K;
+static __device__ void epilogue_unit(const Shape &s, const float *Wcm, double *A, double *B,
+                                     float *Wn, double rho, int rho_on_new, int mt, int ks,
+                                     const float *acc) {
+    const int F = s.F, K = s.K;
     for (int e = threadIdx.x; e < 512; e += kThreads) {
         const int kk = e >> 4, ff = e & 15;
         const int f = 16 * mt + ff, k = 32 * ks + kk;
         if (f >= F || k >= K) continue;
         const long long i = f + (long long)k * F;
-        const float w = a.Wcm[i];
+        const float w = Wcm[i];
         const double av = (double)(acc[ff * 32 + kk] * w * w);
         const double bv = (double)acc[(16 + ff) * 32 + kk];
-        const double A0 = a.A[i], B0 = a.B[i];
+        const double A0 = A[i], B0 = B[i];
         double An, Bn;
-        if (a.rho_on_new) {
+        if (rho_on_new) {
             An = fma(rho, av, A0);
             Bn = fma(rho, bv, B0);
         } else {
             An = fma(rho, A0, av);
             Bn = fma(rho, B0, bv);
         }
-        a.A[i] = An;
-        a.B[i] = Bn;
-        a.Wn[i] = (Bn > 0.0) ? sqrtf(__fdiv_rn((float)An, (float)Bn)) : w;
+        A[i] = An;
+        B[i] = Bn;
+        Wn[i] = (Bn > 0.0) ? sqrtf(__fdiv_rn((float)An, (float)Bn)) : w;
     }
+}
+
+static __device__ __forceinline__ void online_epilogue(const StepArgs &a, int mt, int ks,
+                                                       double rho, const float *acc) {
+    epilogue_unit(a.s, a.Wcm, a.A, a.B, a.Wn, rho, a.rho_on_new, mt, ks, acc);
 }
 
 // Fixed-order sum of one float per thread over the CTA.
@@ -221,10 +228,10 @@ static __device__ void normalize_columns(const Shape &s, int normalize, const fl
                                   __nv_bfloat16 *__restrict__ Wimg,
                                   __nv_bfloat16 *__restrict__ Wrow, double *__restrict__ A,
                                   double *__restrict__ B, float *__restrict__ swpart, int *err,
-                                  float *red8) {
+                                  float *red8, int first, int stride) {
     const int F = s.F, K = s.K;
     const int tid = threadIdx.x;
-    for (int k = blockIdx.x; k < K; k += gridDim.x) {
+    for (int k = first; k < K; k += stride) {
         const float *col = Wn + (long long)k * F;
         float part = 0.f;
         for (int f = tid; f < F; f += kThreads) part += col[f];
@@ -383,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
         if (!grid_sync(a.bar, G, epoch, a.err)) break;
         // ---- phase 3: column sums, rescale, images, loss
         normalize_columns<PREC>(s, a.normalize, a.Wn, a.Wcm, a.Wrm, a.Wimg, a.Wrow, a.A, a.B,
-                                a.swpart, a.err, s_red8);
+                                a.swpart, a.err, s_red8, blockIdx.x, gridDim.x);
         if (blockIdx.x == G - 1) {
             double l = block_sum_ordered(a.loss_part, ntiles, s_red);
             if (threadIdx.x == 0) *a.loss_sum += l;

@@ -1,0 +1,183 @@
+"""Serving: many streams, each its own run of Algorithm 1, fed chunk by chunk
+through onmf_server_* (C ABI). Every chunk is one minibatch of its stream.
+
+Checked here:
+  - one stream served chunk by chunk equals the single-state path
+    (onmf_push_frames + onmf_flush per chunk), bit for bit;
+  - a stream's results alone equal its results in a mix of streams with
+    other dictionary sizes and chunk lengths, bit for bit;
+  - parity with the FP64 oracle run chunk by chunk (FP32 <= 1e-5; mixed
+    within the stated 1e-2 on W, 1e-3 on the losses);
+  - admission by the memory budget: streams that do not fit wait and run
+    once others close.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1106_4198_gb300 as onmf
+from helpers import cuda, problem, relerr
+
+pytestmark = pytest.mark.gpu
+
+
+def chunks_of(n_total, rng, lo=8, hi=64):
+    sizes = []
+    while sum(sizes) < n_total:
+        sizes.append(int(min(rng.integers(lo, hi + 1), n_total - sum(sizes))))
+    return sizes
+
+
+def serve(streams, precision, budget=1 << 30, max_batch=64, close_early=None):
+    """streams: list of (V (N,F), W0 (K,F), sizes, cfg kwargs). Submits every
+    chunk of every stream interleaved; returns per-stream (W, chunk losses)."""
+    F = streams[0][0].shape[1]
+    srv = onmf.onmf_server_create(F, max_chunk=512, max_batch=max_batch, slots=2,
+                                  budget_bytes=budget, precision=precision)
+    try:
+        ids = []
+        for V, W0, sizes, kw in streams:
+            K = W0.shape[0]
+            cfg = onmf.onmf_config_default(F, K, precision=precision, **kw)
+            ids.append(onmf.onmf_server_open_stream(srv, cfg, W0))
+        offs = [0] * len(streams)
+        k = [0] * len(streams)
+        pending = sum(len(s[2]) for s in streams)
+        order = []
+        while len(order) < pending:
+            for i, (V, W0, sizes, kw) in enumerate(streams):
+                if k[i] < len(sizes):
+                    order.append((i, k[i]))
+                    k[i] += 1
+        for i, c in order:
+            V, W0, sizes, kw = streams[i]
+            a = sum(sizes[:c])
+            onmf.onmf_server_submit(srv, ids[i], V[a:a + sizes[c]], tag=c)
+        losses = [dict() for _ in streams]
+        got = 0
+        pos = {sid: i for i, sid in enumerate(ids)}
+        while got < pending:
+            for cp in onmf.onmf_server_poll(srv, 256, wait_ms=2000):
+                assert cp.status == 0
+                losses[pos[cp.stream_id]][cp.tag] = cp.loss
+                got += 1
+        out = []
+        for i, (V, W0, sizes, kw) in enumerate(streams):
+            W = onmf.onmf_server_get_W(srv, ids[i], W0.shape[0], F)
+            out.append((W, [losses[i][c] for c in range(len(sizes))]))
+        stats = onmf.onmf_server_get_stats(srv)
+    finally:
+        onmf.onmf_server_destroy(srv)
+    return out, stats
+
+
+def single_state(V, W0, sizes, precision, **kw):
+    K, F = W0.shape
+    m = onmf.OnlineISNMF(F, K, W0, beta=512, precision=precision, **kw)
+    Vd = cuda(V)
+    losses = []
+    prev = 0.0
+    a = 0
+    for n in sizes:
+        m.push(Vd[a:a + n])
+        m.flush()
+        _, _, _, ls = m.stats()
+        losses.append(ls - prev)
+        prev = ls
+        a += n
+    W = m.W()
+    m.close()
+    return W, losses
+
+
+@pytest.mark.parametrize("precision", [onmf.ONMF_FP32, onmf.ONMF_MIXED])
+def test_served_stream_equals_single_state_path(precision):
+    F, K = 129, 16
+    V, W0 = problem(F, K, 400)
+    sizes = chunks_of(400, np.random.default_rng(1))
+    (W, losses), = serve([(V, W0, sizes, dict(n_inner=5))], precision)[0]
+    Ws, ls = single_state(V, W0, sizes, precision, n_inner=5)
+    assert np.array_equal(W, Ws)
+    # per-chunk losses: served values are exact, single-state ones are
+    # differences of the running sum (rounding of the subtraction)
+    assert np.allclose(losses, ls, rtol=1e-9)
+
+
+@pytest.mark.parametrize("precision", [onmf.ONMF_FP32, onmf.ONMF_MIXED])
+def test_result_alone_equals_result_in_the_mix(precision):
+    rng = np.random.default_rng(2)
+    F = 129
+    target_V, target_W0 = problem(F, 32, 600, seed=7)
+    target_sizes = chunks_of(600, rng, 8, 128)
+    target = (target_V, target_W0, target_sizes, dict(n_inner=6))
+    alone, _ = serve([target], precision)
+    others = []
+    for i in range(23):
+        K = int(rng.choice([16, 32, 64, 128]))
+        N = int(rng.integers(100, 700))
+        V, W0 = problem(F, K, N, seed=100 + i)
+        others.append((V, W0, chunks_of(N, rng, 8, 256), dict(n_inner=6)))
+    mixed, stats = serve(others[:11] + [target] + others[11:], precision, max_batch=32)
+    W_alone, l_alone = alone[0]
+    W_mix, l_mix = mixed[11]
+    assert np.array_equal(W_alone, W_mix)
+    assert l_alone == l_mix
+    print("mix stats:", stats)
+    assert stats["chunks"] == sum(len(s[2]) for s in others) + len(target_sizes)
+
+
+@pytest.mark.parametrize("precision,tol_w,tol_l", [(onmf.ONMF_FP32, 1e-5, 1e-5),
+                                                   (onmf.ONMF_MIXED, 1e-2, 1e-3)])
+def test_served_streams_match_oracle(precision, tol_w, tol_l):
+    rng = np.random.default_rng(3)
+    F = 129
+    streams = []
+    for i, K in enumerate([16, 32, 64, 128]):
+        V, W0 = problem(F, K, 300, seed=40 + i)
+        streams.append((V, W0, chunks_of(300, rng, 8, 100), dict(n_inner=5, r=0.7, n_ref=300)))
+    out, _ = serve(streams, precision)
+    for (V, W0, sizes, kw), (W, losses) in zip(streams, out):
+        Wo, Ao, Bo = W0.astype(np.float64), None, None
+        lo = []
+        a = 0
+        for n in sizes:
+            o = oracle.online_pass(V[a:a + n], Wo, Ao, Bo, beta=n, n_in=5, r=0.7, n_ref=300)
+            Wo, Ao, Bo = o["W"], o["A"], o["B"]
+            lo.append(o["loss_sum"])
+            a += n
+        ew = relerr(W, Wo)
+        el = np.max(np.abs(np.array(losses) - lo) / np.array(lo))
+        print("K=%d: W rel err %.2e, worst chunk loss rel err %.2e" % (W0.shape[0], ew, el))
+        assert ew <= tol_w and el <= tol_l
+
+
+def test_admission_by_budget():
+    F, K = 129, 64
+    srv = onmf.onmf_server_create(F, max_chunk=128, max_batch=16, slots=2,
+                                  budget_bytes=500_000, precision=onmf.ONMF_MIXED)
+    try:
+        ids = []
+        data = []
+        for i in range(4):
+            V, W0 = problem(F, K, 64, seed=60 + i)
+            cfg = onmf.onmf_config_default(F, K, precision=onmf.ONMF_MIXED, n_inner=3)
+            ids.append(onmf.onmf_server_open_stream(srv, cfg, W0))
+            data.append(V)
+        st = onmf.onmf_server_get_stats(srv)
+        assert st["streams_admitted"] < 4 and st["streams_pending"] > 0
+        for sid, V in zip(ids, data):
+            onmf.onmf_server_submit(srv, sid, V, tag=sid)
+        done = set()
+        # the admitted streams finish; closing them lets the waiting ones in
+        for _ in range(200):
+            for cp in onmf.onmf_server_poll(srv, 16, wait_ms=50):
+                assert cp.status == 0
+                done.add(cp.stream_id)
+                onmf.onmf_server_close_stream(srv, cp.stream_id)
+            if len(done) == 4:
+                break
+        assert done == set(ids)
+        st = onmf.onmf_server_get_stats(srv)
+        assert st["streams_admitted"] == 4 and st["streams_pending"] == 0
+    finally:
+        onmf.onmf_server_destroy(srv)
