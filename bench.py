@@ -27,6 +27,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+import numpy as np  # noqa: E402
+
 F, K, BETA, N_IN = 513, 100, 1000, 10
 FLOP_PER_FRAME = (6 * N_IN + 6) * F * K  # algorithmic flops of one frame
 METRIC = "online IS-NMF frames/s (F=513,K=100)"
@@ -44,6 +46,10 @@ def parse():
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-cpu", action="store_true")
     p.add_argument("--cpu-sample-minibatches", type=int, default=6)
+    p.add_argument("--serve-seconds", type=float, default=30.0,
+                   help="wall window of the serving replay (0 skips serving)")
+    p.add_argument("--serve-streams", type=int, default=256)
+    p.add_argument("--serve-budget", type=int, default=1 << 30)
     return p.parse_args()
 
 
@@ -282,6 +288,114 @@ def run_ours(args):
     return out, dist
 
 
+# ----------------------------------------------------------------- serving
+
+HOP_S = 0.032         # 32 ms hop
+SPEEDUP = 4.0         # arrivals at 4x real time
+SERVE_KS = (16, 32, 64, 128)
+
+
+def serving_schedule(n_streams, window_s, rng):
+    """Per-stream chunk arrivals: K ~ U{16,32,64,128}; stream length
+    log-uniform over 10 s .. 2 h of 32 ms frames; chunk length log-uniform
+    integer in [8, 512]; chunks of a stream arrive as a Poisson process whose
+    frame rate is 4x real time; stream starts uniform over the first 60 s of
+    the replay (scaled into the window). Returns (streams, events) with
+    events = [(t, stream, n)] sorted by time."""
+    streams = []
+    events = []
+    rate = SPEEDUP / HOP_S  # frames per second per stream
+    start_span = min(60.0, window_s / 2)
+    for i in range(n_streams):
+        K = int(rng.choice(SERVE_KS))
+        length = int(np.exp(rng.uniform(np.log(10 / HOP_S), np.log(7200 / HOP_S))))
+        t = rng.uniform(0, start_span)
+        left = length
+        while left > 0 and t < window_s:
+            n = int(min(left, np.floor(np.exp(rng.uniform(np.log(8), np.log(513))))))
+            t += rng.exponential(n / rate)
+            if t >= window_s:
+                break
+            events.append((t, i, n))
+            left -= n
+        streams.append(K)
+    events.sort()
+    return streams, events
+
+
+def run_serving(args, precision):
+    import paper_1106_4198_gb300 as onmf
+    import synth
+    rng = np.random.default_rng(4321)
+    Ks, events = serving_schedule(args.serve_streams, args.serve_seconds, rng)
+    pool = synth.spectrogram(F, 64, 65536, seed=synth.DATA_SEED + 17)  # gamma-model frames
+    srv = onmf.onmf_server_create(F, max_chunk=512, max_batch=256, slots=2,
+                                  budget_bytes=args.serve_budget, precision=precision)
+    lat, frames_done = [], 0
+    try:
+        ids = []
+        for i, K in enumerate(Ks):
+            cfg = onmf.onmf_config_default(F, K, precision=precision, n_inner=N_IN)
+            ids.append(onmf.onmf_server_open_stream(srv, cfg, synth.init_dictionary(F, K)))
+        # warm-up: one chunk per stream
+        for sid in ids:
+            onmf.onmf_server_submit(srv, sid, pool[:32], tag=-1)
+        got = 0
+        while got < len(ids):
+            got += len(onmf.onmf_server_poll(srv, 1024, wait_ms=1000))
+        # timed replay at the scheduled arrival times
+        t0 = time.perf_counter()
+        k = 0
+        pending = 0
+        while k < len(events) or pending:
+            now = time.perf_counter() - t0
+            while k < len(events) and events[k][0] <= now:
+                _, i, n = events[k]
+                off = int(rng.integers(0, pool.shape[0] - n))
+                onmf.onmf_server_submit(srv, ids[i], pool[off:off + n], tag=k)
+                pending += 1
+                k += 1
+            wait = 0 if k < len(events) else 50
+            for cp in onmf.onmf_server_poll(srv, 1024, wait_ms=wait):
+                lat.append(cp.t_done - cp.t_submit)
+                frames_done += cp.frames
+                pending -= 1
+            if k < len(events):
+                nxt = events[k][0] - (time.perf_counter() - t0)
+                if nxt > 0.0005:
+                    time.sleep(min(nxt, 0.002))
+        replay_s = time.perf_counter() - t0
+        # saturation: the same chunks submitted at once
+        t1 = time.perf_counter()
+        sat_frames = 0
+        for k, (_, i, n) in enumerate(events):
+            off = int(rng.integers(0, pool.shape[0] - n))
+            onmf.onmf_server_submit(srv, ids[i], pool[off:off + n], tag=k)
+            sat_frames += n
+        got = 0
+        while got < len(events):
+            got += len(onmf.onmf_server_poll(srv, 4096, wait_ms=1000))
+        sat_s = time.perf_counter() - t1
+        st = onmf.onmf_server_get_stats(srv)
+    finally:
+        onmf.onmf_server_destroy(srv)
+    lat_ms = np.array(lat) * 1e3
+    offered = sum(n for _, _, n in events) / args.serve_seconds
+    return {
+        "workload": "%d streams, K in {16,32,64,128}, F=513, chunks 8-512 frames, "
+                    "Poisson arrivals at 4x real time, %.0f s replay" % (len(Ks), args.serve_seconds),
+        "chunks": len(events), "frames": int(frames_done),
+        "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat) else None,
+        "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat) else None,
+        "max_ms": float(lat_ms.max()) if len(lat) else None,
+        "offered_frames_per_s": offered,
+        "achieved_frames_per_s": frames_done / replay_s,
+        "saturation_frames_per_s": sat_frames / sat_s,
+        "launches": st["launches"], "batches_overlapped": st["batches_overlapped"],
+        "budget_bytes": args.serve_budget, "precision": "mixed" if precision else "fp32",
+    }
+
+
 # ----------------------------------------------------------- oracle (CPU)
 
 
@@ -355,6 +469,9 @@ def main():
                 "sample": "%d minibatches (%d frames) of the workload, %.1f s"
                           % (args.cpu_sample_minibatches,
                              args.cpu_sample_minibatches * BETA, dt)}
+        if args.serve_seconds > 0 and world == 1:
+            import paper_1106_4198_gb300 as onmf
+            out["serving"] = run_serving(args, onmf.ONMF_MIXED)
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
