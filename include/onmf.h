@@ -101,7 +101,11 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0,
  *       written when their minibatch runs (a later push or onmf_flush), so
  *       H_out must stay valid until then.
  * Asynchronous on the state's stream; V (if on the device) must stay valid
- * until the stream reaches this call. n = 0 is a no-op.
+ * until the stream reaches this call. Host V goes through a two-slot device
+ * ring filled on a private copy stream, so the copy of one slot overlaps the
+ * steps on the other: pageable host V may be reused as soon as the call
+ * returns, page-locked host V must stay unchanged until the state's stream
+ * reaches this call (onmf_synchronize). n = 0 is a no-op.
  * Errors: EINVAL, ESTATE (sticky error), ECUDA; kernel-detected input errors
  * surface later as ENUMERIC. */
 onmf_status onmf_push_frames(onmf_state *s, const float *V, int64_t ldv,
@@ -285,6 +289,21 @@ const char *onmf_last_error_message(void);
 /* Number of kernel launches this process has issued through the library
  * (all states), for launch accounting in benchmarks. */
 int64_t onmf_kernel_launches(void);
+
+/* Fault-path self-test (no counterpart in the paper). Runs one of the
+ * library's bounded device waits on a condition that never holds, on a
+ * two-CTA launch on `stream` (a cudaStream_t, NULL = legacy default):
+ *   which 0: the grid barrier of the persistent step kernel, told to expect
+ *            one CTA more than the grid has;
+ *   which 1: an mbarrier phase that nothing arrives on;
+ *   which 2: as 1, while the CTA holds tensor memory, freed before it returns.
+ * Each wait gives up after its limit (2 s), flags a timeout and leaves the
+ * kernel; the CUDA context stays usable. Blocks until the stream drains.
+ * elapsed_ns (may be NULL) receives the device time from kernel start to the
+ * first CTA's exit.
+ * Returns ETIMEOUT when the wait ran out as designed, OK if it did not,
+ * EINVAL (which out of range), ENOMEM, ECUDA. */
+onmf_status onmf_selftest_wait(int32_t which, void *stream, int64_t *elapsed_ns);
 
 /* ABI version (ONMF_ABI_VERSION). */
 int32_t onmf_abi_version(void);

@@ -28,6 +28,7 @@ __all__ = [
 
 ONMF_FP32 = 0
 ONMF_MIXED = 1
+ONMF_ETIMEOUT = 6
 
 # Every symbol include/onmf.h declares.
 EXPORTED = [
@@ -38,7 +39,7 @@ EXPORTED = [
     "onmf_abi_version", "onmf_project_static",
     "onmf_server_create", "onmf_server_open_stream", "onmf_server_submit",
     "onmf_server_poll", "onmf_server_get_W", "onmf_server_close_stream",
-    "onmf_server_get_stats", "onmf_server_destroy",
+    "onmf_server_get_stats", "onmf_server_destroy", "onmf_selftest_wait",
 ]
 
 
@@ -143,13 +144,14 @@ def lib():
     L.onmf_last_error_message.restype = ctypes.c_char_p
     L.onmf_kernel_launches.restype = _i64
     L.onmf_abi_version.restype = _i32
+    L.onmf_selftest_wait.argtypes = [_i32, _vp, ctypes.POINTER(_i64)]
     for name in ("onmf_init", "onmf_push_frames", "onmf_flush",
                  "onmf_synchronize", "onmf_get_W", "onmf_get_stats",
                  "onmf_set_state", "onmf_project", "nmf_batch_step",
                  "nmf_batch_init_H", "onmf_project_static", "onmf_server_create",
                  "onmf_server_open_stream", "onmf_server_submit", "onmf_server_poll",
                  "onmf_server_get_W", "onmf_server_close_stream",
-                 "onmf_server_get_stats"):
+                 "onmf_server_get_stats", "onmf_selftest_wait"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -210,6 +212,15 @@ def onmf_kernel_launches():
 
 def onmf_abi_version():
     return int(lib().onmf_abi_version())
+
+
+def onmf_selftest_wait(which, stream=None):
+    """Run bounded wait `which` (0 grid barrier, 1 mbarrier, 2 mbarrier with
+    tensor memory held) on a condition that never holds. Returns
+    (status, elapsed device ns); the expected status is ONMF_ETIMEOUT."""
+    el = _i64(0)
+    st = lib().onmf_selftest_wait(int(which), _stream_handle(stream), ctypes.byref(el))
+    return int(st), int(el.value)
 
 
 def onmf_config_default(F, K, **kw):

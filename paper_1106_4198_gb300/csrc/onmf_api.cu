@@ -114,10 +114,12 @@ struct onmf_state {
     float *staging = nullptr, *Hstage = nullptr;
     int staged = 0;
     std::vector<Segment> segs;
-    // host-input ring
+    // host-input ring: copies on copy_stream overlap the step kernels
     float *vring[2] = {nullptr, nullptr};
     float *hring[2] = {nullptr, nullptr};
-    cudaEvent_t ring_ev[2] = {nullptr, nullptr};
+    cudaEvent_t ring_ev[2] = {nullptr, nullptr};    // slot consumed by the step kernels
+    cudaEvent_t ring_full[2] = {nullptr, nullptr};  // slot filled by the copy
+    cudaStream_t copy_stream = nullptr;
     long long ring_frames = 0;
     double *obj_h = nullptr;  // pinned
     long long t = 0;
@@ -195,9 +197,40 @@ int64_t onmf_kernel_launches(void) { return kernel_launches(); }
 
 int32_t onmf_abi_version(void) { return ONMF_ABI_VERSION; }
 
+onmf_status onmf_selftest_wait(int32_t which, void *stream, int64_t *elapsed_ns) {
+    if (which < 0 || which > 2) return ONMF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned *counter = nullptr;
+    int *err = nullptr;
+    unsigned long long *el = nullptr;
+    onmf_status rc = ONMF_OK;
+    int bits = 0;
+    unsigned long long el_h = 0;
+    cudaError_t e = cudaMalloc((void **)&counter, 256);
+    if (e == cudaSuccess) {
+        err = (int *)((char *)counter + 64);
+        el = (unsigned long long *)((char *)counter + 128);
+        e = cudaMemsetAsync(counter, 0, 256, st);
+    }
+    if (e == cudaSuccess) e = launch_wait_selftest(which, counter, err, el, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, err, sizeof bits, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&el_h, el, sizeof el_h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        set_msg("wait self-test", e);
+        rc = e == cudaErrorMemoryAllocation ? ONMF_ENOMEM : ONMF_ECUDA;
+    } else {
+        rc = status_from_err(bits);
+        if (elapsed_ns) *elapsed_ns = (int64_t)el_h;
+    }
+    if (counter) cudaFree(counter);
+    return rc;
+}
+
 void onmf_destroy(onmf_state *s) {
     if (!s) return;
     cudaStreamSynchronize(s->stream);
+    if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
     void *dev[] = {s->Wcm, s->Wrm, s->Wn, s->swpart, s->Wimg, s->Wrow, s->A, s->B, s->loss_sum, s->Pg,
                    s->Qg, s->Hg, s->loss_part, s->tmp_sum, s->bar, s->err_d, s->staging,
                    s->Hstage, s->vring[0], s->vring[1], s->hring[0], s->hring[1]};
@@ -205,8 +238,11 @@ void onmf_destroy(onmf_state *s) {
         if (p) cudaFree(p);
     if (s->err_h) cudaFreeHost(s->err_h);
     if (s->obj_h) cudaFreeHost(s->obj_h);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
         if (s->ring_ev[i]) cudaEventDestroy(s->ring_ev[i]);
+        if (s->ring_full[i]) cudaEventDestroy(s->ring_full[i]);
+    }
+    if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
     delete s;
 }
 
@@ -453,22 +489,32 @@ onmf_status onmf_push_frames(onmf_state *s, const float *V, int64_t ldv, int64_t
     if (n < 0 || (n > 0 && !V) || ldv < s->cfg.F || (H_out && ldh < s->cfg.K)) return ONMF_EINVAL;
     if (n == 0) return ONMF_OK;
     if (is_device_ptr(V)) return push_device(s, V, ldv, n, H_out, ldh);
-    // host frames: copy through a double-buffered device ring, chunk by chunk
+    // host frames: copy through a double-buffered device ring, chunk by chunk,
+    // on a copy stream so the copy of chunk i+1 overlaps the steps of chunk i
     const onmf_config &c = s->cfg;
     if (!s->vring[0]) {
         s->ring_frames = (long long)std::max(1, (1 << 18) / c.beta) * c.beta;
+        CK(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
         for (int b = 0; b < 2; ++b) {
             CK(cudaMalloc((void **)&s->vring[b], (size_t)s->ring_frames * c.F * 4));
             CK(cudaEventCreateWithFlags(&s->ring_ev[b], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&s->ring_full[b], cudaEventDisableTiming));
+            CK(cudaEventRecord(s->ring_ev[b], s->stream));
         }
     }
     long long i = 0;
     int b = 0;
     while (i < n) {
         long long m = std::min(s->ring_frames, n - i);
-        CK(cudaEventSynchronize(s->ring_ev[b]));  // slot free (previous use consumed)
-        CK(cudaMemcpy2DAsync(s->vring[b], (size_t)c.F * 4, V + i * ldv, (size_t)ldv * 4,
-                             (size_t)c.F * 4, m, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamWaitEvent(s->copy_stream, s->ring_ev[b], 0));  // slot consumed
+        if (ldv == c.F)
+            CK(cudaMemcpyAsync(s->vring[b], V + i * ldv, (size_t)m * c.F * 4,
+                               cudaMemcpyHostToDevice, s->copy_stream));
+        else
+            CK(cudaMemcpy2DAsync(s->vring[b], (size_t)c.F * 4, V + i * ldv, (size_t)ldv * 4,
+                                 (size_t)c.F * 4, m, cudaMemcpyHostToDevice, s->copy_stream));
+        CK(cudaEventRecord(s->ring_full[b], s->copy_stream));
+        CK(cudaStreamWaitEvent(s->stream, s->ring_full[b], 0));  // slot filled
         st = push_device(s, s->vring[b], c.F, m, H_out ? H_out + i * ldh : nullptr, ldh);
         if (st != ONMF_OK) return st;
         CK(cudaEventRecord(s->ring_ev[b], s->stream));

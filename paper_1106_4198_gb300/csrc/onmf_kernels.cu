@@ -312,4 +312,49 @@ cudaError_t launch_batch_h0(const Shape &s, const float *V, long long ldv, long 
     return cudaGetLastError();
 }
 
+// Fault-path self-test: runs one of the library's bounded waits on a
+// condition that can never hold, so the wait must run out, flag ERR_TIMEOUT
+// and leave the kernel with the context intact.
+//   which 0: grid barrier expecting one CTA more than the grid has;
+//   which 1: mbarrier phase that nothing arrives on;
+//   which 2: as 1, while the CTA holds tensor memory, which it frees before
+//            returning (the exit path of the tcgen05 h-solve kernels).
+__global__ void __launch_bounds__(kThreads) wait_selftest_kernel(int which, unsigned *counter,
+                                                                 int *err,
+                                                                 unsigned long long *elapsed) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    const uint64_t t0 = global_ns();
+    if (which == 0) {
+        unsigned epoch = 0;
+        grid_sync(counter, gridDim.x + 1, epoch, err);
+    } else {
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            fence_mbar_init();
+        }
+        if (which == 2 && threadIdx.x < 32) tmem_alloc(&tslot, 32);
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0, err);
+        tc_fence_before();
+        __syncthreads();
+        if (which == 2 && threadIdx.x < 32) tmem_dealloc(tslot, 32);
+    }
+    if (threadIdx.x == 0 && blockIdx.x == 0) *elapsed = global_ns() - t0;
+}
+
+cudaError_t launch_wait_selftest(int which, unsigned *counter, int *err,
+                                 unsigned long long *elapsed, cudaStream_t stream) {
+    void *args[] = {&which, &counter, &err, &elapsed};
+    cudaError_t e = which == 0 ? cudaLaunchCooperativeKernel((const void *)wait_selftest_kernel,
+                                                             dim3(2), dim3(kThreads), args, 0,
+                                                             stream)
+                               : cudaLaunchKernel((const void *)wait_selftest_kernel, dim3(2),
+                                                  dim3(kThreads), args, 0, stream);
+    if (e == cudaSuccess) count_launch();
+    return e;
+}
+
 }  // namespace onmf

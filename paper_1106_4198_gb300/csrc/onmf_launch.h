@@ -37,5 +37,7 @@ cudaError_t launch_batch_scale_h(int K, long long N, float *H, const float *scal
                                  cudaStream_t stream);
 cudaError_t launch_batch_h0(const Shape &s, const float *V, long long ldv, long long N, float eps,
                             const float *swpart, float *H, cudaStream_t stream);
+cudaError_t launch_wait_selftest(int which, unsigned *counter, int *err,
+                                 unsigned long long *elapsed, cudaStream_t stream);
 
 }  // namespace onmf

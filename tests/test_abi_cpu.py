@@ -80,3 +80,6 @@ def test_null_arguments_rejected():
     assert L.onmf_get_W(None, None, 0) == 1
     assert L.nmf_batch_step(None, 0, None, None, 1, 1, 1, 0.0, 0.5, 1, 1, 0,
                             None, None) == 1
+    # an unknown wait kind is refused before any device work
+    assert L.onmf_selftest_wait(7, None, None) == 1
+    assert L.onmf_selftest_wait(-1, None, None) == 1

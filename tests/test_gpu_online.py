@@ -130,6 +130,30 @@ def test_host_input_matches_device_input():
     assert np.array_equal(a["W"], b["W"]) and np.array_equal(a["H"], b["H"])
 
 
+def test_host_input_ring_crosses_slots():
+    """Host frames run through a two-slot device ring filled on a copy stream.
+    beta = 2**18 makes one slot hold exactly one minibatch, so 2.5 minibatches
+    reuse both slots and leave a ragged tail in staging. Pageable, page-locked
+    and strided host buffers (with host H_out) all equal the device path."""
+    import torch
+    F, K, beta = 33, 4, 1 << 18
+    N = 5 * beta // 2
+    V, W0 = problem(F, K, N, seed=11)
+    ref = run_gpu(V, W0, beta=beta, n_inner=3, precision=MIXED)
+    pinned = torch.from_numpy(V).pin_memory()
+    wide = np.zeros((N, F + 3), dtype=np.float32)
+    wide[:, :F] = V
+    for Vh in (np.ascontiguousarray(V), pinned, wide[:, :F]):
+        m = onmf.OnlineISNMF(F, K, W0, beta=beta, n_inner=3, precision=MIXED)
+        H = np.zeros((N, K), dtype=np.float32)
+        m.push(Vh, H)
+        m.flush()
+        m.sync()
+        assert np.array_equal(m.W(), ref["W"])
+        assert np.array_equal(H, ref["H"])
+        m.close()
+
+
 def test_scale_equivariance_bitwise_gpu(hsolve):
     """eps = 0: V -> 4V leaves W, A, B bit-identical and scales H by 4
     (power-of-two scaling is exact and every ratio is invariant)."""
