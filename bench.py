@@ -30,6 +30,7 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 F, K, BETA, N_IN = 513, 100, 1000, 10
+HSOLVE = os.environ.get("ONMF_HSOLVE", "mma")  # h-solve variant the library selects
 FLOP_PER_FRAME = (6 * N_IN + 6) * F * K  # algorithmic flops of one frame
 METRIC = "online IS-NMF frames/s (F=513,K=100)"
 WORKLOAD = "online IS-NMF long stream F=513 K=100 beta=1000 n_inner=10, 1e6 frames/step"
@@ -45,7 +46,9 @@ def parse():
     p.add_argument("--skip-fp32", action="store_true")
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-cpu", action="store_true")
-    p.add_argument("--cpu-sample-minibatches", type=int, default=6)
+    p.add_argument("--cpu-sample-minibatches", type=int, default=120)
+    p.add_argument("--skip-c2", action="store_true",
+                   help="skip the objective-vs-time comparison (online vs batch)")
     p.add_argument("--serve-seconds", type=float, default=30.0,
                    help="wall window of the serving replay (0 skips serving)")
     p.add_argument("--serve-streams", type=int, default=256)
@@ -160,6 +163,13 @@ class ClockSampler:
 # ----------------------------------------------------------------- peaks
 
 
+# DRAM bytes (read + write) per frame of the step kernel, from one ncu
+# capture of each h-solve variant (64,000 frames, scaled per frame: the
+# traffic is proportional to the frames processed). A variant that changed
+# since its capture is absent here and reports traffic = null.
+NCU_TRAFFIC_PER_FRAME = {"mma": 2136.4}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -259,8 +269,12 @@ def run_ours(args):
         achieved = FLOP_PER_FRAME * fps / (launch_ms / 1e3) / 1e12
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                "kernel": "online_kernel<mixed>",
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": (NCU_TRAFFIC_PER_FRAME[HSOLVE] * fps
+                            if HSOLVE in NCU_TRAFFIC_PER_FRAME else None),
+                "traffic_note": "DRAM bytes per launch of %d frames, scaled from an ncu "
+                                "capture of 64,000 frames" % fps,
+                "kernel": "online step kernel, mixed precision, %s h-solve" % HSOLVE,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"
                 if peaks else "fallback"}
         out = {
@@ -399,6 +413,102 @@ def run_serving(args, precision):
 # ----------------------------------------------------------- oracle (CPU)
 
 
+# ------------------------------------- objective vs time: online vs batch
+
+C2_F, C2_K, C2_N, C2_ITERS = 513, 50, 112_500, 200
+
+
+def run_c2(precision):
+    """Objective against device time for one online pass (beta = 1000 and
+    100, n_inner = 10, fresh restarts) and 200 batch multiplicative-update
+    cycles on the same 112,500 x 513 gamma-model spectrogram, K = 50.
+
+    Both methods are scored alike: at each checkpoint the current W is held
+    fixed and every frame's h is solved from the fresh-restart start point
+    (onmf_project, 10 iterations); the score is the mean d_IS per frame.
+    Batch also reports its own objective (with its current H). Times are
+    CUDA-event device times of the updates only (scoring excluded)."""
+    import torch
+
+    import paper_1106_4198_gb300 as onmf
+    import synth
+
+    F_, K_, N_ = C2_F, C2_K, C2_N
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    seed = synth.DATA_SEED + 2
+    Wstar = torch.as_tensor(synth.dictionary(F_, K_, seed), dtype=torch.float32, device=dev)
+    V = synth.device_frames(F_, K_, N_, seed=seed, chunk=0, Wstar=Wstar)
+    W0 = synth.init_dictionary(F_, K_)
+    Hs = torch.empty((N_, K_), device=dev)
+
+    def score(W):
+        s = onmf.OnlineISNMF(F_, K_, W, stream=stream, beta=1000, n_inner=N_IN,
+                             precision=precision)
+        obj = s.project(V, Hs, n_inner=N_IN, want_obj=True)
+        s.close()
+        return obj / N_
+
+    curves = {}
+    for beta in (1000, 100):
+        m = onmf.OnlineISNMF(F_, K_, W0, stream=stream, beta=beta, n_inner=N_IN,
+                             precision=precision)
+        pts = [(0.0, score(W0))]
+        t = 0.0
+        seg = N_ // 10
+        for a in range(0, N_, seg):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m.push(V[a:a + seg])
+            if a + seg >= N_:
+                m.flush()
+            e1.record(stream)
+            e1.synchronize()
+            t += e0.elapsed_time(e1)
+            pts.append((t, score(m.W())))
+        m.close()
+        curves["online_beta%d" % beta] = pts
+
+    W = torch.as_tensor(np.asarray(W0, dtype=np.float32), device=dev).contiguous()
+    H = torch.zeros((N_, K_), device=dev)
+    onmf.nmf_batch_init_H(V, W, H, stream=stream)
+    pts = [(0.0, score(W0))]
+    own = []
+    t = 0.0
+    for c in range(C2_ITERS // 10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        obj = onmf.nmf_batch_step(V, W, H, n_iter=10, precision=precision, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        t += e0.elapsed_time(e1)
+        own.extend(obj.tolist())
+        pts.append((t, score(W.cpu().numpy())))
+    curves["batch"] = pts
+
+    def first_time_below(pts, target):
+        for tt, v in pts:
+            if v <= target:
+                return tt
+        return None
+
+    b_final = curves["batch"][-1][1]
+    out = {"workload": "F=513 K=50 N=112,500 gamma-model spectrogram; online one pass "
+                       "(beta 1000 and 100, n_inner 10) vs 200 batch MU cycles",
+           "precision": "mixed" if precision == onmf.ONMF_MIXED else "fp32",
+           "score": "mean d_IS per frame, h re-solved with W fixed (10 iterations)",
+           "curves_ms_score": {k: [[round(a, 4), b] for a, b in v] for k, v in curves.items()},
+           "batch_own_objective_first_last": [own[0], own[-1]]}
+    for k in ("online_beta1000", "online_beta100"):
+        t_end, s_end = curves[k][-1]
+        out[k] = {"pass_ms": t_end, "final_score": s_end,
+                  "batch_ms_to_same_score": first_time_below(curves["batch"], s_end),
+                  "batch_score_at_same_time": min(
+                      [v for tt, v in curves["batch"] if tt <= t_end] or [curves["batch"][0][1]])}
+    out["batch"] = {"ms_200_cycles": curves["batch"][-1][0], "final_score": b_final}
+    return out
+
+
 def cpu_oracle_rate(n_mb, threads):
     """Frames/s of the FP64 oracle on a bounded sample of the workload."""
     import numpy as np
@@ -469,6 +579,9 @@ def main():
                 "sample": "%d minibatches (%d frames) of the workload, %.1f s"
                           % (args.cpu_sample_minibatches,
                              args.cpu_sample_minibatches * BETA, dt)}
+        if not args.skip_c2 and world == 1:
+            import paper_1106_4198_gb300 as onmf
+            out["objective_vs_time"] = run_c2(onmf.ONMF_MIXED)
         if args.serve_seconds > 0 and world == 1:
             import paper_1106_4198_gb300 as onmf
             out["serving"] = run_serving(args, onmf.ONMF_MIXED)
