@@ -54,7 +54,8 @@ typedef enum {
 typedef enum {
     ONMF_FP32 = 0,  /* FP32 everywhere on the GPU (A, B accumulate in FP64)   */
     ONMF_MIXED = 1  /* BF16 tensor-core products with FP32 accumulation, FP32
-                       ratios y/x^2 and 1/x, FP64 A and B; K <= 128, F <= 1024 */
+                       ratios y/x^2 and 1/x, FP64 A and B; K <= 256, F <= 1024
+                       (K > 128: the cluster h-solve; serving: K <= 128) */
 } onmf_precision;
 
 /* Parameters of Algorithm 1 (Section 2.3). */

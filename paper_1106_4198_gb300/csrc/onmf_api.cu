@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "onmf.h"
+#include "onmf_cluster.cuh"
 #include "onmf_device.cuh"
 #include "onmf_kernels.cuh"
 #include "onmf_launch.h"
@@ -45,6 +46,7 @@ bool is_device_ptr(const void *p) {
 }
 
 onmf_status status_from_err(int bits) {
+    if (bits & ERR_CONFIG) return ONMF_ECUDA;
     if (bits & ERR_TIMEOUT) return ONMF_ETIMEOUT;
     if (bits & (ERR_INPUT | ERR_NUMERIC)) return ONMF_ENUMERIC;
     return ONMF_OK;
@@ -78,10 +80,7 @@ size_t tc_min_smem(int prec, size_t smem) {
 }
 
 int pick_prec(int precision, const Shape &sh) {
-    if (precision != ONMF_MIXED) return PREC_FP32;
-    const char *env = getenv("ONMF_HSOLVE");
-    if (env && strcmp(env, "tc") == 0 && tc_shape_supported(sh)) return PREC_TC;
-    return PREC_MIXED;
+    return select_prec(precision == ONMF_MIXED, sh);
 }
 
 onmf_status ensure_configured() {
@@ -99,6 +98,7 @@ struct onmf_state {
     Shape s;
     cudaStream_t stream;
     int prec;
+    int C = 0;  // CTAs per cluster (cluster h-solve)
     // state
     float *Wcm = nullptr, *Wrm = nullptr, *Wn = nullptr, *swpart = nullptr;
     __nv_bfloat16 *Wimg = nullptr, *Wrow = nullptr;
@@ -152,9 +152,8 @@ static onmf_status sync_and_check(onmf_state *s) {
 }
 
 static onmf_status prepare_images(onmf_state *s) {
-    CK(launch_prepare(s->s, s->Wcm, s->prec == PREC_FP32 ? s->Wrm : nullptr,
-                      s->prec != PREC_FP32 ? s->Wimg : nullptr, s->swpart, s->stream,
-                      s->prec == PREC_TC ? s->Wrow : nullptr));
+    CK(launch_prepare(s->s, s->Wcm, s->prec == PREC_FP32 ? s->Wrm : nullptr, s->Wimg, s->swpart,
+                      s->stream, s->Wrow));
     return ONMF_OK;
 }
 
@@ -257,8 +256,8 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
         !(c.r >= 0.0 && c.r <= 1.0) || !(c.h_exponent > 0.0) || c.reserved != 0 ||
         (c.precision != ONMF_FP32 && c.precision != ONMF_MIXED))
         return ONMF_EINVAL;
-    if (c.precision == ONMF_MIXED && (c.K > 128 || c.F > 1024)) {
-        snprintf(g_msg, sizeof g_msg, "mixed precision supports K <= 128 and F <= 1024");
+    if (c.precision == ONMF_MIXED && c.F > 1024) {
+        snprintf(g_msg, sizeof g_msg, "mixed precision supports F <= 1024");
         return ONMF_EINVAL;
     }
     onmf_status st = ensure_configured();
@@ -273,6 +272,8 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
     s->betap = (c.beta + 15) / 16 * 16;
     const size_t elem = s->prec == PREC_FP32 ? 4 : 2;
     const int ntiles = (c.beta + kTile - 1) / kTile;
+    // loss slots: one per 8-frame tile, or one per (32-frame tile, cluster CTA)
+    const int nslots = std::max(ntiles, (c.beta + kClTile - 1) / kClTile * kClMaxC);
     auto fail = [&](onmf_status e) {
         onmf_destroy(s);
         return e;
@@ -296,13 +297,13 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
         AL(s->Wrm, FK * 4);
         AL(s->Hg, (size_t)s->betap * sh.Kh * 4);
     } else {
-        AL(s->Wimg, (size_t)sh.Kp * sh.WLD * 2);
+        if (s->prec != PREC_CL) AL(s->Wimg, (size_t)sh.Kp * sh.WLD * 2);
         AL(s->Hg, (size_t)sh.Kh * s->betap * 2);
-        if (s->prec == PREC_TC) AL(s->Wrow, (size_t)sh.F * sh.Kp * 2);
+        if (s->prec == PREC_TC || s->prec == PREC_CL) AL(s->Wrow, (size_t)sh.F * sh.Kp * 2);
     }
     AL(s->Pg, (size_t)s->betap * sh.Fp16 * elem);
     AL(s->Qg, (size_t)s->betap * sh.Fp16 * elem);
-    AL(s->loss_part, (size_t)ntiles * 8);
+    AL(s->loss_part, (size_t)nslots * 8);
     AL(s->bar, 16);
     AL(s->err_d, 16);
     AL(s->staging, (size_t)c.beta * c.F * 4);
@@ -333,21 +334,43 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
-    s->smem = tc_min_smem(s->prec, online_smem_bytes(sh, s->prec));
+    if (s->prec == PREC_CL) {
+        s->C = cluster_choose(sh, c.beta, s->num_sms, max_dynamic_smem(), true);
+        if (s->C == 0) {
+            snprintf(g_msg, sizeof g_msg, "no cluster layout fits F=%d K=%d", c.F, c.K);
+            return fail(ONMF_EINVAL);
+        }
+        s->smem = cluster_smem_bytes(sh, s->C, true);
+    } else {
+        s->smem = tc_min_smem(s->prec, online_smem_bytes(sh, s->prec));
+    }
     s->tile_smem = tc_min_smem(s->prec, tile_smem_bytes(sh, s->prec));
     if (s->smem > max_dynamic_smem()) {
         snprintf(g_msg, sizeof g_msg, "shared memory need %zu exceeds the device limit", s->smem);
         return fail(ONMF_EINVAL);
     }
-    int per_sm = 0;
-    if ((e = max_coresident_blocks(s->prec, sh.Kp / 16, s->smem, &per_sm)) != cudaSuccess || per_sm < 1) {
-        set_msg("occupancy", e);
-        return fail(ONMF_ECUDA);
-    }
     const int units = (sh.Fp16 / 16) * (sh.Kh / 32);
-    const int tiles = s->prec == PREC_TC ? (c.beta + kTcTile - 1) / kTcTile : ntiles;
-    int want = std::max(std::max(tiles, units), (c.K + kWarps - 1) / kWarps);
-    s->grid = std::min(want, per_sm * s->num_sms);
+    if (s->prec == PREC_CL) {
+        // whole clusters, all co-resident: enough for the tiles and the units
+        const int act = cluster_max_active(sh, s->C, true);
+        if (act < 1) {
+            snprintf(g_msg, sizeof g_msg, "no co-resident cluster of %d CTAs", s->C);
+            return fail(ONMF_ECUDA);
+        }
+        const int tiles = (c.beta + kClTile - 1) / kClTile;
+        const int want = std::max(tiles, (std::max(units, c.K) + s->C - 1) / s->C);
+        s->grid = std::min(want, act) * s->C;
+    } else {
+        int per_sm = 0;
+        if ((e = max_coresident_blocks(s->prec, sh.Kp / 16, s->smem, &per_sm)) != cudaSuccess ||
+            per_sm < 1) {
+            set_msg("occupancy", e);
+            return fail(ONMF_ECUDA);
+        }
+        const int tiles = s->prec == PREC_TC ? (c.beta + kTcTile - 1) / kTcTile : ntiles;
+        int want = std::max(std::max(tiles, units), (c.K + kWarps - 1) / kWarps);
+        s->grid = std::min(want, per_sm * s->num_sms);
+    }
     s->tile_grid = s->num_sms;
     // sanity: all of W0 finite and >= 0 (checked on the host copy)
     std::vector<float> w(FK);
@@ -400,7 +423,10 @@ static onmf_status run_minibatches(onmf_state *s, const float *V, long long ldv,
     a.loss_part = s->loss_part;
     a.bar = s->bar;
     a.err = s->err_d;
-    CK(launch_online(a, s->prec, s->grid, s->smem, s->stream));
+    if (s->prec == PREC_CL)
+        CK(launch_online_cluster(a, s->C, s->grid, s->smem, s->stream));
+    else
+        CK(launch_online(a, s->prec, s->grid, s->smem, s->stream));
     s->t += (long long)(nmb - 1) * c.beta + nb_last;
     return mirror_err(s);
 }
@@ -595,7 +621,13 @@ onmf_status onmf_project(onmf_state *s, const float *V, int64_t ldv, int64_t n, 
     float *Vtmp = nullptr, *Htmp = nullptr;
     double *lp = nullptr;
     const int tile = s->prec == PREC_TC ? kTcTile : kTile;
-    const long long ntiles = (n + tile - 1) / tile;
+    long long ntiles = (n + tile - 1) / tile;  // loss slots
+    ClusterTiles ct;
+    if (s->prec == PREC_CL) {
+        ct = cluster_tiles(s->s, n);
+        if (ct.C == 0) return ONMF_EINVAL;
+        ntiles = ct.slots;
+    }
     cudaStream_t q = s->stream;
     if (!vdev) {
         CK(cudaMallocAsync((void **)&Vtmp, (size_t)n * c.F * 4, q));
@@ -630,8 +662,12 @@ onmf_status onmf_project(onmf_state *s, const float *V, int64_t ldv, int64_t n, 
     a.swpart = s->swpart;
     a.loss_part = lp;
     a.err = s->err_d;
-    const int grid = (int)std::min<long long>(ntiles, (long long)s->tile_grid * 2);
-    CK(launch_tiles(a, s->prec, grid, s->tile_smem, q));
+    if (s->prec == PREC_CL) {
+        CK(launch_tiles_cluster(a, ct.C, ct.grid, ct.smem, q));
+    } else {
+        const int grid = (int)std::min<long long>(ntiles, (long long)s->tile_grid * 2);
+        CK(launch_tiles(a, s->prec, grid, s->tile_smem, q));
+    }
     if (Htmp)
         CK(cudaMemcpy2DAsync(H_out, ldh * 4, Htmp, (size_t)c.K * 4, (size_t)c.K * 4, n,
                              cudaMemcpyDeviceToHost, q));
@@ -674,7 +710,7 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
         n_iter < 0 || !(eps >= 0.0) || !(h_exponent > 0.0) ||
         (precision != ONMF_FP32 && precision != ONMF_MIXED))
         return ONMF_EINVAL;
-    if (precision == ONMF_MIXED && (K > 128 || F > 1024)) return ONMF_EINVAL;
+    if (precision == ONMF_MIXED && F > 1024) return ONMF_EINVAL;
     onmf_status st = ensure_configured();
     if (st != ONMF_OK) return st;
     if (n_iter == 0) return ONMF_OK;
@@ -684,7 +720,13 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
     const long long betap = (N + 15) / 16 * 16;
     const size_t elem = prec == PREC_FP32 ? 4 : 2;
     const int tile = prec == PREC_TC ? kTcTile : kTile;
-    const long long ntiles = (N + tile - 1) / tile;
+    long long ntiles = (N + tile - 1) / tile;  // loss slots
+    ClusterTiles ct;
+    if (prec == PREC_CL) {
+        ct = cluster_tiles(sh, N);
+        if (ct.C == 0) return ONMF_EINVAL;
+        ntiles = ct.slots;
+    }
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -708,8 +750,8 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
               al(&Hg, (size_t)betap * sh.Kh * elem) && al((void **)&lp, (size_t)ntiles * 8) &&
               al((void **)&obj_d, (size_t)std::max(1, n_iter) * 8) && al((void **)&err, 16);
     if (ok && prec == PREC_FP32) ok = al((void **)&Wrm, (size_t)F * K * 4);
-    if (ok && prec != PREC_FP32) ok = al((void **)&Wimg, (size_t)sh.Kp * sh.WLD * 2);
-    if (ok && prec == PREC_TC) ok = al((void **)&Wrow, (size_t)F * sh.Kp * 2);
+    if (ok && prec != PREC_FP32 && prec != PREC_CL) ok = al((void **)&Wimg, (size_t)sh.Kp * sh.WLD * 2);
+    if (ok && (prec == PREC_TC || prec == PREC_CL)) ok = al((void **)&Wrow, (size_t)F * sh.Kp * 2);
     auto cleanup = [&]() {
         for (void *p : owned) cudaFreeAsync(p, q);
     };
@@ -725,6 +767,10 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
     if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 16, q);
     const size_t tsm = tc_min_smem(prec, tile_smem_bytes(sh, prec));
     const int tgrid = (int)std::min<long long>(ntiles, 2LL * nsm);
+    auto run_tiles = [&](const TileArgs &x) {
+        return prec == PREC_CL ? launch_tiles_cluster(x, ct.C, ct.grid, ct.smem, q)
+                               : launch_tiles(x, prec, tgrid, tsm, q);
+    };
     TileArgs a;
     memset(&a, 0, sizeof a);
     a.s = sh;
@@ -752,7 +798,7 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
         h.loss_first = (it > 0 && obj_out) ? 1 : 0;
         h.final_pass = 0;
         h.loss_part = h.loss_first ? lp : nullptr;
-        if (e == cudaSuccess) e = launch_tiles(h, prec, tgrid, tsm, q);
+        if (e == cudaSuccess) e = run_tiles(h);
         if (e == cudaSuccess && h.loss_first) e = launch_sum(lp, ntiles, obj_d + it - 1, 0, q);
         // P, Q, H rows from the updated H, then the W step
         TileArgs r = a;
@@ -763,7 +809,7 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
         r.Pg = Pg;
         r.Qg = Qg;
         r.Hg = Hg;
-        if (e == cudaSuccess) e = launch_tiles(r, prec, tgrid, tsm, q);
+        if (e == cudaSuccess) e = run_tiles(r);
         if (e == cudaSuccess)
             e = launch_batch_stats(sh, prec, Pg, Qg, Hg, betap, N, nchunks, part,
                                    std::min(units * nchunks, 2 * nsm), q);
@@ -780,7 +826,7 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
         o.ldh_in = K;
         o.final_pass = 1;
         o.loss_part = lp;
-        if (e == cudaSuccess) e = launch_tiles(o, prec, tgrid, tsm, q);
+        if (e == cudaSuccess) e = run_tiles(o);
         if (e == cudaSuccess) e = launch_sum(lp, ntiles, obj_d + n_iter - 1, 0, q);
     }
     int errh = 0;

@@ -14,6 +14,7 @@ enum : int {
     ERR_INPUT = 1,    // a frame value was negative, NaN or Inf
     ERR_NUMERIC = 2,  // the dictionary step produced a non-finite W
     ERR_TIMEOUT = 4,  // a bounded wait (grid barrier, bulk copy) ran out
+    ERR_CONFIG = 8,   // the launch did not have the shape the kernel needs
 };
 
 // Every device-side wait gives up after this many nanoseconds of
@@ -69,9 +70,10 @@ __device__ __forceinline__ bool grid_sync(unsigned *counter, unsigned nblocks,
             }
         }
         __threadfence();
+        if (read_error(err) != 0) s_ok = 0;  // one read, so every thread agrees
     }
     __syncthreads();
-    return s_ok != 0 && read_error(err) == 0;
+    return s_ok != 0;
 }
 
 // ---------------------------------------------------------------- BF16
@@ -135,6 +137,13 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src,
                                            int src_bytes = 16) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem_dst)),
                  "l"(gmem_src), "r"(src_bytes)
+                 : "memory");
+}
+
+// 4-byte global->shared copy (no alignment beyond 4 bytes needed).
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(smem_dst)),
+                 "l"(gmem_src)
                  : "memory");
 }
 
@@ -203,6 +212,58 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity
         }
     }
     return true;
+}
+
+// ------------------------------------------ thread-block clusters (DSMEM)
+
+__device__ __forceinline__ unsigned cluster_ctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned cluster_nctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// Cluster-wide barrier of all threads of all CTAs in the cluster; release
+// and acquire order the shared::cluster stores issued before it.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n"
+                 "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// Address in CTA `rank`'s shared memory of the local shared address `a`.
+__device__ __forceinline__ uint32_t map_rank(uint32_t a, unsigned rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void st_cluster_f32x2(uint32_t a, float x, float y) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x), "f"(y) : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_u32(uint32_t a, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_v4(uint32_t a, uint4 v) {
+    asm volatile("st.shared::cluster.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_f32x4(uint32_t a, float x, float y, float z, float w) {
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x), "f"(y),
+                 "f"(z), "f"(w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_f32(uint32_t a, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
 }
 
 __device__ __forceinline__ float warp_sum(float v) {

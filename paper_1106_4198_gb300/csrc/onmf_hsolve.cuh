@@ -35,10 +35,37 @@ struct TileJob {
     long long betap;
 };
 
-__device__ __forceinline__ float pow_gamma(float r, float gamma) {
-    if (gamma == 0.5f) return sqrtf(r);
-    if (gamma == 1.0f) return r;
-    return powf(r, gamma);
+// Compile-time tags, so that a hot loop is instantiated once per value of a
+// run-time switch that is uniform over the CTA (the exponent mode, whether
+// the loss is wanted) instead of carrying the rarely taken path (powf, logf)
+// as predicated code in every iteration.
+template <int V> struct IntTag {
+    static constexpr int value = V;
+};
+
+// Exponent mode of the h update: 0 for gamma = 1/2, 1 for gamma = 1, 2 else.
+__host__ __device__ inline int gamma_mode(float gamma) {
+    return gamma == 0.5f ? 0 : (gamma == 1.0f ? 1 : 2);
+}
+
+// h * r^gamma for the exponent mode GM.
+template <int GM>
+__device__ __forceinline__ float scale_pow(float h, float r, float gamma) {
+    if (GM == 0) return h * sqrtf(r);
+    if (GM == 1) return h * r;
+    return h * powf(r, gamma);
+}
+
+// Run f(IntTag<mode>{}) for the exponent mode of gamma.
+template <class Fn>
+__device__ __forceinline__ void with_gamma_mode(float gamma, Fn &&f) {
+    const int gm = gamma_mode(gamma);
+    if (gm == 0)
+        f(IntTag<0>{});
+    else if (gm == 1)
+        f(IntTag<1>{});
+    else
+        f(IntTag<2>{});
 }
 
 __device__ __forceinline__ bool bad_value(float v) { return !(v >= 0.f) || isinf(v); }
@@ -114,7 +141,8 @@ static __device__ void hsolve_tile_fp32(const Shape &s, float eps, float gamma, 
         const bool last = (it == t.n_in);
         if (last && !t.final_pass) break;
         const bool want_loss = (last && t.final_pass) || (it == 0 && t.loss_first);
-        auto finish_row = [&](int f, const float (&acc)[kTile]) {
+        auto finish_row_t = [&](auto loss_tag, int f, const float (&acc)[kTile]) {
+            constexpr bool LOSS = decltype(loss_tag)::value != 0;
             float4 ya = *reinterpret_cast<const float4 *>(y_s + f * kTile);
             float4 yb = *reinterpret_cast<const float4 *>(y_s + f * kTile + 4);
             float ys[kTile] = {ya.x, ya.y, ya.z, ya.w, yb.x, yb.y, yb.z, yb.w};
@@ -125,7 +153,7 @@ static __device__ void hsolve_tile_fp32(const Shape &s, float eps, float gamma, 
                 float q = __frcp_rn(x);
                 qv[j] = q;
                 pv[j] = ys[j] * q * q;
-                if (want_loss && j < t.nvalid) {
+                if (LOSS && j < t.nvalid) {
                     float r = ys[j] * q;
                     lacc += (r - 1.f) - logf(r);
                 }
@@ -134,6 +162,13 @@ static __device__ void hsolve_tile_fp32(const Shape &s, float eps, float gamma, 
             *reinterpret_cast<float4 *>(p_s + f * kTile + 4) = make_float4(pv[4], pv[5], pv[6], pv[7]);
             *reinterpret_cast<float4 *>(q_s + f * kTile) = make_float4(qv[0], qv[1], qv[2], qv[3]);
             *reinterpret_cast<float4 *>(q_s + f * kTile + 4) = make_float4(qv[4], qv[5], qv[6], qv[7]);
+        };
+        // the loss is a separate instantiation (no logf where it is not needed)
+        auto finish_row = [&](int f, const float (&acc)[kTile]) {
+            if (want_loss)
+                finish_row_t(IntTag<1>{}, f, acc);
+            else
+                finish_row_t(IntTag<0>{}, f, acc);
         };
         // x = eps + W h: rows [0, mainF) one per thread, the rest split over k by warps
         for (int f = tid; f < mainF; f += kThreads) {
@@ -212,20 +247,23 @@ static __device__ void hsolve_tile_fp32(const Shape &s, float eps, float gamma, 
                 }
             }
             __syncthreads();
-            for (int e = tid; e < 128 * kTile; e += kThreads) {
-                int kk = e / kTile, j = e % kTile, k = k0 + kk;
-                if (k < K) {
-                    float num = 0.f, den = 0.f;
+            with_gamma_mode(gamma, [&](auto gm) {
+                constexpr int GM = decltype(gm)::value;
+                for (int e = tid; e < 128 * kTile; e += kThreads) {
+                    int kk = e / kTile, j = e % kTile, k = k0 + kk;
+                    if (k < K) {
+                        float num = 0.f, den = 0.f;
 #pragma unroll
-                    for (int w = 0; w < kWarps; ++w) {
-                        num += red[((size_t)w * 128 + kk) * 16 + j];
-                        den += red[((size_t)w * 128 + kk) * 16 + 8 + j];
+                        for (int w = 0; w < kWarps; ++w) {
+                            num += red[((size_t)w * 128 + kk) * 16 + j];
+                            den += red[((size_t)w * 128 + kk) * 16 + 8 + j];
+                        }
+                        float h = h_s[k * kTile + j];
+                        if (den > 0.f) h = scale_pow<GM>(h, __fdiv_rn(num, den), gamma);
+                        h_s[k * kTile + j] = h;
                     }
-                    float h = h_s[k * kTile + j];
-                    if (den > 0.f) h = h * pow_gamma(__fdiv_rn(num, den), gamma);
-                    h_s[k * kTile + j] = h;
                 }
-            }
+            });
             __syncthreads();
         }
     }
@@ -468,35 +506,44 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
                 for (int i = 0; i < kMtMax; ++i)
                     if (mg + kWarps * i < FT) mma_bf16_16816(d[i], a[i], b0, b1);
             }
-            // p = y/x^2, q = 1/x (FP32), bf16, stored transposed: PQ_s[j][f], PQ_s[8+j][f]
+            // p = y/x^2, q = 1/x (FP32), bf16, stored transposed: PQ_s[j][f],
+            // PQ_s[8+j][f]; the loss is a separate instantiation (no logf in
+            // the iterations that do not need it)
+            auto ratios = [&](auto loss_tag) {
+                constexpr bool LOSS = decltype(loss_tag)::value != 0;
 #pragma unroll
-            for (int i = 0; i < kMtMax; ++i) {
-                const int mt = mg + kWarps * i;
-                if (mt < FT) {
-                    const int f0 = 16 * mt;
-                    const float2 ya = *reinterpret_cast<const float2 *>(yT + (f0 + g) * 8 + 2 * tq);
-                    const float2 yb =
-                        *reinterpret_cast<const float2 *>(yT + (f0 + g + 8) * 8 + 2 * tq);
-                    const float yv[4] = {ya.x, ya.y, yb.x, yb.y};
-                    float pv[4], qv[4];
+                for (int i = 0; i < kMtMax; ++i) {
+                    const int mt = mg + kWarps * i;
+                    if (mt < FT) {
+                        const int f0 = 16 * mt;
+                        const float2 ya = *reinterpret_cast<const float2 *>(yT + (f0 + g) * 8 + 2 * tq);
+                        const float2 yb =
+                            *reinterpret_cast<const float2 *>(yT + (f0 + g + 8) * 8 + 2 * tq);
+                        const float yv[4] = {ya.x, ya.y, yb.x, yb.y};
+                        float pv[4], qv[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int f = f0 + g + 8 * (e >> 1);
-                        const float q = rcp_approx(d[i][e]);
-                        const float p = yv[e] * q * q;
-                        const bool ok = f < F;
-                        pv[e] = ok ? p : 0.f;
-                        qv[e] = ok ? q : 0.f;
-                        if (want_loss && ok && (2 * tq + (e & 1)) < t.nvalid) {
-                            const float r = yv[e] * q;
-                            lacc += (r - 1.f) - logf(r);
+                        for (int e = 0; e < 4; ++e) {
+                            const int f = f0 + g + 8 * (e >> 1);
+                            const float q = rcp_approx(d[i][e]);
+                            const float p = yv[e] * q * q;
+                            const bool ok = f < F;
+                            pv[e] = ok ? p : 0.f;
+                            qv[e] = ok ? q : 0.f;
+                            if (LOSS && ok && (2 * tq + (e & 1)) < t.nvalid) {
+                                const float r = yv[e] * q;
+                                lacc += (r - 1.f) - logf(r);
+                            }
                         }
+                        stmatrix_x4_trans(PQ_s + (r8 + 8 * (mi >> 1)) * WLD + f0 + 8 * (mi & 1),
+                                          pack_bf16(pv[0], pv[1]), pack_bf16(pv[2], pv[3]),
+                                          pack_bf16(qv[0], qv[1]), pack_bf16(qv[2], qv[3]));
                     }
-                    stmatrix_x4_trans(PQ_s + (r8 + 8 * (mi >> 1)) * WLD + f0 + 8 * (mi & 1),
-                                      pack_bf16(pv[0], pv[1]), pack_bf16(pv[2], pv[3]),
-                                      pack_bf16(qv[0], qv[1]), pack_bf16(qv[2], qv[3]));
                 }
-            }
+            };
+            if (want_loss)
+                ratios(IntTag<1>{});
+            else
+                ratios(IntTag<0>{});
         }
         __syncthreads();
         if (last) break;
@@ -551,9 +598,12 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
             // n[0..1] = (W^T p)[k, k+1] of frame g, n[2..3] = (W^T q)[k, k+1]
             const float num[4] = {n0[0], n0[1], n1[0], n1[1]};
             const float den[4] = {n0[2], n0[3], n1[2], n1[3]};
+            with_gamma_mode(gamma, [&](auto gm) {
+                constexpr int GM = decltype(gm)::value;
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (den[e] > 0.f) hr[e] = hr[e] * pow_gamma(__fdividef(num[e], den[e]), gamma);
+                for (int e = 0; e < 4; ++e)
+                    if (den[e] > 0.f) hr[e] = scale_pow<GM>(hr[e], __fdividef(num[e], den[e]), gamma);
+            });
             *reinterpret_cast<uint32_t *>(H_s + g * HLD + 16 * warp + 2 * tq) =
                 pack_bf16(hr[0], hr[1]);
             *reinterpret_cast<uint32_t *>(H_s + g * HLD + 16 * warp + 8 + 2 * tq) =

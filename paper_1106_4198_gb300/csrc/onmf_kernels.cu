@@ -1,9 +1,13 @@
 // libonmf kernels: host-side launchers, the FP32 instantiation of the step
 // kernels (onmf_step.cuh), and the small helper kernels (derived images of
 // W, ordered sums, the batch W step and rescales).
+#include <algorithm>
 #include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <vector>
 
+#include "onmf_cluster.cuh"
 #include "onmf_device.cuh"
 #include "onmf_kernels.cuh"
 #include "onmf_launch.h"
@@ -149,6 +153,99 @@ const void *mixed_tile_hi(int prec, int ks);
 const void *mixed_serve_lo(int ks);
 const void *mixed_serve_hi(int ks);
 
+// Cluster h-solve kernels, instantiated per k16-slab count in
+// onmf_cluster_lo.cu (1..8) and onmf_cluster_hi.cu (9..16).
+const void *cluster_online_lo(int ks);
+const void *cluster_online_hi(int ks);
+const void *cluster_tile_lo(int ks);
+const void *cluster_tile_hi(int ks);
+
+static const void *cluster_online_fn(int ks) {
+    return ks <= 8 ? cluster_online_lo(ks) : cluster_online_hi(ks);
+}
+static const void *cluster_tile_fn(int ks) {
+    return ks <= 8 ? cluster_tile_lo(ks) : cluster_tile_hi(ks);
+}
+
+size_t cluster_smem_bytes(const Shape &s, int C, bool online) {
+    const size_t h = cl_layout(s, C).total;
+    const size_t st = online ? stats_smem_bytes(PREC_MIXED) : 0;
+    return h > st ? h : st;
+}
+
+static cudaLaunchConfig_t cluster_config(int C, int grid, size_t smem, cudaStream_t stream,
+                                         cudaLaunchAttribute *at, bool cooperative) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeCooperative;
+    at[1].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = cooperative ? 2 : 1;
+    return cfg;
+}
+
+int cluster_max_active(const Shape &s, int C, bool online) {
+    const void *fn = online ? cluster_online_fn(s.Kp / 16) : cluster_tile_fn(s.Kp / 16);
+    cudaLaunchAttribute at[2];
+    cudaLaunchConfig_t cfg =
+        cluster_config(C, C * 1024, cluster_smem_bytes(s, C, online), 0, at, false);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+// Cluster size for `frames` frames per launch round: the smallest C whose
+// 32-frame tiles give at least 3/4 of the SMs a CTA, else the largest C
+// that fits (0 if none does).
+int cluster_choose(const Shape &s, long long frames, int num_sms, size_t smem_limit, bool online) {
+    const long long tiles = (frames + kClTile - 1) / kClTile;
+    int best = 0;
+    for (int C = 1; C <= kClMaxC; C *= 2) {
+        if (!cl_supported(s, C) || cluster_smem_bytes(s, C, online) > smem_limit) continue;
+        best = C;
+        if (tiles * C >= (long long)num_sms * 3 / 4) break;
+    }
+    return best;
+}
+
+// K > 128 needs the cluster h-solve (the whole bf16 W^T no longer fits one
+// CTA's shared memory); ONMF_HSOLVE=mma|tc|cluster selects a variant where
+// the shape allows it.
+int select_prec(bool mixed, const Shape &s) {
+    if (!mixed) return PREC_FP32;
+    const char *env = getenv("ONMF_HSOLVE");
+    const bool big = s.Kp > 128;
+    if (env && strcmp(env, "tc") == 0 && !big && tc_supported(s)) return PREC_TC;
+    if (env && strcmp(env, "mma") == 0 && !big) return PREC_MIXED;
+    if (env && strcmp(env, "cluster") == 0) return PREC_CL;
+    return big ? PREC_CL : PREC_MIXED;
+}
+
+ClusterTiles cluster_tiles(const Shape &s, long long n) {
+    ClusterTiles r;
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    r.C = cluster_choose(s, n, nsm, max_dynamic_smem(), false);
+    if (r.C == 0) return r;
+    const long long tiles = (n + kClTile - 1) / kClTile;
+    const long long act = std::max(1, cluster_max_active(s, r.C, false));
+    r.grid = (int)(std::min(tiles, 2 * act) * r.C);
+    r.smem = cluster_smem_bytes(s, r.C, false);
+    r.slots = tiles * r.C;
+    return r;
+}
+
 // Serving kernels: FP32 (one variant) or mixed, one per k16-slab count.
 const void *serve_fn(int prec, int ks) {
     if (prec == PREC_FP32) return (const void *)serve_kernel<PREC_FP32, 0>;
@@ -185,6 +282,10 @@ cudaError_t configure_kernels() {
             fns.push_back(tile_fn(p, ks));
         }
     for (int ks = 1; ks <= 8; ++ks) fns.push_back(serve_fn(PREC_MIXED, ks));
+    for (int ks = 1; ks <= 16; ++ks) {
+        fns.push_back(cluster_online_fn(ks));
+        fns.push_back(cluster_tile_fn(ks));
+    }
     for (const void *fn : fns) {
         cudaFuncAttributes at;
         if ((e = cudaFuncGetAttributes(&at, fn)) != cudaSuccess) return e;
@@ -208,6 +309,10 @@ size_t max_dynamic_smem() {
             fns.push_back(online_fn(p, ks));
             fns.push_back(tile_fn(p, ks));
         }
+    for (int ks = 1; ks <= 16; ++ks) {
+        fns.push_back(cluster_online_fn(ks));
+        fns.push_back(cluster_tile_fn(ks));
+    }
     for (const void *fn : fns)
         if (cudaFuncGetAttributes(&at, fn) == cudaSuccess && at.sharedSizeBytes > worst)
             worst = at.sharedSizeBytes;
@@ -227,6 +332,50 @@ cudaError_t launch_online(const StepArgs &a, int prec, int grid, size_t smem,
     void *args[] = {&copy};
     e = cudaLaunchCooperativeKernel(online_fn(prec, a.s.Kp / 16), dim3(grid), dim3(kThreads),
                                     args, smem, stream);
+    if (e == cudaSuccess) count_launch();
+    return e;
+}
+
+// The online step on clusters of C CTAs. Cooperative where the runtime
+// accepts it together with a cluster dimension; otherwise a plain cluster
+// launch whose grid is sized to the co-resident clusters (the bounded grid
+// barrier turns a CTA that never became resident into ERR_TIMEOUT).
+cudaError_t launch_online_cluster(const StepArgs &a, int C, int grid, size_t smem,
+                                  cudaStream_t stream) {
+    static int coop_ok = -1;
+    cudaError_t e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned), stream);
+    if (e != cudaSuccess) return e;
+    StepArgs copy = a;
+    int c = C;
+    void *args[] = {&copy, &c};
+    const void *fn = cluster_online_fn(a.s.Kp / 16);
+    cudaLaunchAttribute at[2];
+    if (coop_ok != 0) {
+        cudaLaunchConfig_t cfg = cluster_config(C, grid, smem, stream, at, true);
+        e = cudaLaunchKernelExC(&cfg, fn, args);
+        if (e == cudaSuccess) {
+            coop_ok = 1;
+            count_launch();
+            return e;
+        }
+        if (coop_ok == 1) return e;
+        cudaGetLastError();
+        coop_ok = 0;
+    }
+    cudaLaunchConfig_t cfg = cluster_config(C, grid, smem, stream, at, false);
+    e = cudaLaunchKernelExC(&cfg, fn, args);
+    if (e == cudaSuccess) count_launch();
+    return e;
+}
+
+cudaError_t launch_tiles_cluster(const TileArgs &a, int C, int grid, size_t smem,
+                                 cudaStream_t stream) {
+    TileArgs copy = a;
+    int c = C;
+    void *args[] = {&copy, &c};
+    cudaLaunchAttribute at[2];
+    cudaLaunchConfig_t cfg = cluster_config(C, grid, smem, stream, at, false);
+    cudaError_t e = cudaLaunchKernelExC(&cfg, cluster_tile_fn(a.s.Kp / 16), args);
     if (e == cudaSuccess) count_launch();
     return e;
 }

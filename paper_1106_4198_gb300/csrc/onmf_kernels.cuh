@@ -7,6 +7,7 @@
 //   Wimg  Kp x WLD bf16: W^T padded for the tensor-core path; row k holds
 //         column k of W (F values, zero padded to WLD = Fp16 + 8). The +8
 //         makes 8 consecutive rows fall in distinct shared-memory banks.
+//   Wrow  F x Kp bf16: W row-major (tcgen05 and cluster h-solves).
 //   A, B  F x K  double, column-major: the sufficient statistics (Eq. aux_fun).
 //   Pg,Qg betap x Fp16: per-frame rows of P = Y/X^2 and Q = 1/X of the
 //         current minibatch (float on the FP32 path, bf16 on the mixed path).
@@ -24,8 +25,10 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kTile = 8;       // frames per h-solve tile (mma.sync and FP32 paths)
 constexpr int kTcTile = 16;    // frames per h-solve tile (tcgen05 path)
 
-// PREC_TC: the mixed-precision arithmetic with the tcgen05 (TMEM) h-solve.
-enum Prec : int { PREC_FP32 = 0, PREC_MIXED = 1, PREC_TC = 2 };
+// PREC_TC: the mixed-precision arithmetic with the tcgen05 (TMEM) h-solve;
+// PREC_CL: the same arithmetic with the cluster h-solve (W split by rows
+// over the CTAs of a thread-block cluster, 32-frame tiles).
+enum Prec : int { PREC_FP32 = 0, PREC_MIXED = 1, PREC_TC = 2, PREC_CL = 3 };
 
 struct Shape {
     int F, K;

@@ -37,6 +37,25 @@ cudaError_t launch_batch_scale_h(int K, long long N, float *H, const float *scal
                                  cudaStream_t stream);
 cudaError_t launch_batch_h0(const Shape &s, const float *V, long long ldv, long long N, float eps,
                             const float *swpart, float *H, cudaStream_t stream);
+// h-solve variant for a shape (PREC_FP32 unless mixed).
+int select_prec(bool mixed, const Shape &s);
+
+// Cluster h-solve (PREC_CL): C CTAs per cluster.
+struct ClusterTiles {
+    int C = 0, grid = 0;  // CTAs per cluster (0: shape not covered), CTAs
+    size_t smem = 0;
+    long long slots = 0;  // loss slots: 32-frame tiles x C
+};
+// Launch geometry of the cluster tile kernel for n frames.
+ClusterTiles cluster_tiles(const Shape &s, long long n);
+size_t cluster_smem_bytes(const Shape &s, int C, bool online);
+int cluster_max_active(const Shape &s, int C, bool online);
+int cluster_choose(const Shape &s, long long frames, int num_sms, size_t smem_limit, bool online);
+cudaError_t launch_online_cluster(const StepArgs &a, int C, int grid, size_t smem,
+                                  cudaStream_t stream);
+cudaError_t launch_tiles_cluster(const TileArgs &a, int C, int grid, size_t smem,
+                                 cudaStream_t stream);
+
 cudaError_t launch_wait_selftest(int which, unsigned *counter, int *err,
                                  unsigned long long *elapsed, cudaStream_t stream);
 

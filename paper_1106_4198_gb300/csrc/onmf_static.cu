@@ -10,6 +10,7 @@
 #include <mutex>
 
 #include "onmf.h"
+#include "onmf_cluster.cuh"
 #include "onmf_kernels.cuh"
 #include "onmf_launch.h"
 
@@ -60,26 +61,28 @@ extern "C" onmf_status onmf_project_static(const float *W, int32_t F, int32_t K,
         n_inner < 0 || !(eps >= 0.0) || !(h_exponent > 0.0) ||
         (precision != ONMF_FP32 && precision != ONMF_MIXED) || K > 256 || F > 8192)
         return ONMF_EINVAL;
-    if (precision == ONMF_MIXED && (K > 128 || F > 1024)) return ONMF_EINVAL;
+    if (precision == ONMF_MIXED && F > 1024) return ONMF_EINVAL;
     const Shape sh = make_shape(F, K);
-    // the same h-solve as onmf_project: tcgen05 where the shape allows it
-    int prec = PREC_FP32;
-    if (precision == ONMF_MIXED) {
-        const char *env = getenv("ONMF_HSOLVE");
-        const bool tc = env && strcmp(env, "tc") == 0;
-        prec = (tc && tc_shape_supported(sh)) ? PREC_TC : PREC_MIXED;
+    // the same h-solve as onmf_project
+    const int prec = select_prec(precision == ONMF_MIXED, sh);
+    ClusterTiles ct;
+    if (prec == PREC_CL) {
+        ct = cluster_tiles(sh, n > 0 ? n : 1);
+        if (ct.C == 0) return ONMF_EINVAL;
     }
     const int tile = prec == PREC_TC ? kTcTile : kTile;
-    const long long ntiles = (n + tile - 1) / tile;
-    // scratch layout: [W image][row-major bf16 W (tcgen05)][column sums][per-tile loss]
-    const size_t img = prec == PREC_FP32 ? (size_t)F * K * 4 : (size_t)sh.Kp * sh.WLD * 2;
-    const size_t rows = prec == PREC_TC ? (size_t)F * sh.Kp * 2 : 0;
+    const long long ntiles = prec == PREC_CL ? ct.slots : (n + tile - 1) / tile;  // loss slots
+    // scratch layout: [W image][row-major bf16 W][column sums][per-tile loss]
+    const size_t img = prec == PREC_FP32 ? (size_t)F * K * 4
+                       : prec == PREC_CL ? 0
+                                         : (size_t)sh.Kp * sh.WLD * 2;
+    const size_t rows = (prec == PREC_TC || prec == PREC_CL) ? (size_t)F * sh.Kp * 2 : 0;
     const size_t off_rows = align256(img);
     const size_t off_sw = off_rows + align256(rows);
     const size_t off_loss = off_sw + align256((size_t)K * 4);
     const size_t need = off_loss + (size_t)(ntiles > 0 ? ntiles : 1) * 8;
     if (need > ONMF_STATIC_SCRATCH_BYTES - 256) return ONMF_EINVAL;
-    size_t smem = tile_smem_bytes(sh, prec);
+    size_t smem = prec == PREC_CL ? ct.smem : tile_smem_bytes(sh, prec);
     if (prec == PREC_TC && smem < 116 * 1024) smem = 116 * 1024;  // one CTA per SM (TMEM)
     if (smem > max_dynamic_smem()) return ONMF_EINVAL;
     void *base = nullptr;
@@ -88,9 +91,9 @@ extern "C" onmf_status onmf_project_static(const float *W, int32_t F, int32_t K,
     unsigned char *b = static_cast<unsigned char *>(base);
     cudaStream_t q = reinterpret_cast<cudaStream_t>(stream);
     float *Wrm = prec == PREC_FP32 ? reinterpret_cast<float *>(b) : nullptr;
-    __nv_bfloat16 *Wimg = prec != PREC_FP32 ? reinterpret_cast<__nv_bfloat16 *>(b) : nullptr;
-    __nv_bfloat16 *Wrow =
-        prec == PREC_TC ? reinterpret_cast<__nv_bfloat16 *>(b + off_rows) : nullptr;
+    __nv_bfloat16 *Wimg =
+        (prec == PREC_MIXED || prec == PREC_TC) ? reinterpret_cast<__nv_bfloat16 *>(b) : nullptr;
+    __nv_bfloat16 *Wrow = rows ? reinterpret_cast<__nv_bfloat16 *>(b + off_rows) : nullptr;
     float *swpart = reinterpret_cast<float *>(b + off_sw);
     double *loss = reinterpret_cast<double *>(b + off_loss);
     // the padding of the bf16 image must read as zero whatever an earlier
@@ -126,11 +129,15 @@ extern "C" onmf_status onmf_project_static(const float *W, int32_t F, int32_t K,
     int *err = reinterpret_cast<int *>(b + ONMF_STATIC_SCRATCH_BYTES - 256);
     if (cudaMemsetAsync(err, 0, sizeof(int), q) != cudaSuccess) return ONMF_ECUDA;
     a.err = err;
-    int dev = 0, nsm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = (int)(ntiles < 2LL * nsm ? ntiles : 2LL * nsm);
-    if (launch_tiles(a, prec, grid, smem, q) != cudaSuccess) return ONMF_ECUDA;
+    if (prec == PREC_CL) {
+        if (launch_tiles_cluster(a, ct.C, ct.grid, smem, q) != cudaSuccess) return ONMF_ECUDA;
+    } else {
+        int dev = 0, nsm = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const int grid = (int)(ntiles < 2LL * nsm ? ntiles : 2LL * nsm);
+        if (launch_tiles(a, prec, grid, smem, q) != cudaSuccess) return ONMF_ECUDA;
+    }
     if (obj_sum && launch_sum(loss, ntiles, obj_sum, 0, q) != cudaSuccess) return ONMF_ECUDA;
     return ONMF_OK;
 }

@@ -271,8 +271,10 @@ static __device__ void normalize_columns(const Shape &s, int normalize, const fl
                     if (PREC == PREC_FP32) {
                         Wrm[(long long)f * K + k] = wv;
                     } else {
-                        Wimg[(long long)k * s.WLD + f] = __float2bfloat16_rn(wv);
-                        if (PREC == PREC_TC) Wrow[(long long)f * s.Kp + k] = __float2bfloat16_rn(wv);
+                        if (PREC != PREC_CL)
+                            Wimg[(long long)k * s.WLD + f] = __float2bfloat16_rn(wv);
+                        if (PREC == PREC_TC || PREC == PREC_CL)
+                            Wrow[(long long)f * s.Kp + k] = __float2bfloat16_rn(wv);
                     }
                 }
             }

@@ -423,10 +423,14 @@ __device__ void hsolve_tile_tc(const Shape &s, float eps, float gamma, float sw,
                 const float xe = eps + x[e];
                 qv[e] = rcp_approx(xe);
                 pv[e] = yv[e] * qv[e] * qv[e];
-                if (want_loss && jb + e < t.nvalid) {
-                    const float rr = yv[e] * qv[e];
-                    lacc += (rr - 1.f) - logf(rr);
-                }
+            }
+            if (want_loss) {  // kept out of the loop above (no predicated logf)
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    if (jb + e < t.nvalid) {
+                        const float rr = yv[e] * qv[e];
+                        lacc += (rr - 1.f) - logf(rr);
+                    }
             }
             if (last) {
                 if (t.final_pass && t.Pg) {
@@ -504,9 +508,12 @@ __device__ void hsolve_tile_tc(const Shape &s, float eps, float gamma, float sw,
                 }
             }
             if (k < K) {
+                with_gamma_mode(gamma, [&](auto gm) {
+                    constexpr int GM = decltype(gm)::value;
 #pragma unroll
-                for (int e = 0; e < 8; ++e)
-                    if (dn[e] > 0.f) hr[e] = hr[e] * pow_gamma(__fdividef(nm[e], dn[e]), gamma);
+                    for (int e = 0; e < 8; ++e)
+                        if (dn[e] > 0.f) hr[e] = scale_pow<GM>(hr[e], __fdividef(nm[e], dn[e]), gamma);
+                });
             }
             __syncthreads();  // every thread has read the tail p, q of this iteration
             write_h();

@@ -63,14 +63,17 @@ def test_invalid_config_rejected_on_host(field, value):
     assert not h.value
 
 
-def test_mixed_precision_k_limit():
+def test_mixed_precision_shape_limits():
+    """Mixed precision takes K <= 256 and F <= 1024; the host rejects the
+    rest before any device work."""
     import numpy as np
-    c = onmf.onmf_config_default(16, 200, precision=onmf.ONMF_MIXED)
-    W0 = np.ones((200, 16), dtype=np.float32) / 16
-    h = ctypes.c_void_p()
-    st = onmf.lib().onmf_init(ctypes.byref(c), W0.ctypes.data, 0, None,
-                              ctypes.byref(h))
-    assert st == 1
+    for F, K in ((16, 257), (1025, 8)):
+        c = onmf.onmf_config_default(F, K, precision=onmf.ONMF_MIXED)
+        W0 = np.ones((K, F), dtype=np.float32) / F
+        h = ctypes.c_void_p()
+        st = onmf.lib().onmf_init(ctypes.byref(c), W0.ctypes.data, 0, None,
+                                  ctypes.byref(h))
+        assert st == 1 and not h.value
 
 
 def test_null_arguments_rejected():

@@ -259,14 +259,13 @@ def test_projection_block_diagonal_closed_form():
     assert worst <= 1e-5
 
 
-@pytest.fixture(params=["mma", "tc"])
+@pytest.fixture(params=["mma", "tc", "cluster"])
 def hsolve(request, monkeypatch):
-    """Mixed precision has two h-solves: mma.sync (default) and tcgen05
-    (ONMF_HSOLVE=tc); every mixed test runs on both."""
-    if request.param == "tc":
-        monkeypatch.setenv("ONMF_HSOLVE", "tc")
-    else:
-        monkeypatch.delenv("ONMF_HSOLVE", raising=False)
+    """Mixed precision has three h-solves: mma.sync on one CTA per 8-frame
+    tile (default for K <= 128), tcgen05 (ONMF_HSOLVE=tc) and the cluster
+    h-solve (ONMF_HSOLVE=cluster; always for K > 128); every mixed test runs
+    on each."""
+    monkeypatch.setenv("ONMF_HSOLVE", request.param)
     return request.param
 
 

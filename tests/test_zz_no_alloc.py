@@ -43,7 +43,8 @@ def static(W0, V, n_inner, precision, eps=1e-12):
 def test_static_projection_matches_allocating_projection_twice():
     cases = [(513, 100, 300, 10, onmf.ONMF_FP32),
              (129, 8, 77, 5, onmf.ONMF_MIXED),
-             (513, 100, 200, 10, onmf.ONMF_MIXED)]
+             (513, 100, 200, 10, onmf.ONMF_MIXED),
+             (513, 256, 150, 10, onmf.ONMF_MIXED)]  # K > 128: the cluster h-solve
     for F, K, n, n_in, prec in cases:
         V, W0 = problem(F, K, n, seed=99)
         Hr, objr = regular(W0, V, n_in, prec)
