@@ -618,14 +618,15 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
         __nv_bfloat16 *Qg = reinterpret_cast<__nv_bfloat16 *>(t.Qg);
         __nv_bfloat16 *Hg = reinterpret_cast<__nv_bfloat16 *>(t.Hg);
         const int cpr = Fp / 8;  // 16-byte chunks per row
-        for (int i = tid; i < kTile * cpr * 2; i += kThreads) {
-            const int which = i / (kTile * cpr);
-            const int rem = i - which * kTile * cpr;
-            const int j = rem / cpr, c = rem - j * cpr;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (j < t.nvalid) v = *reinterpret_cast<const uint4 *>(PQ_s + (which * 8 + j) * WLD + 8 * c);
-            __nv_bfloat16 *dst = (which ? Qg : Pg) + (t.j0 + j) * Fp + 8 * c;
-            *reinterpret_cast<uint4 *>(dst) = v;
+        // warp per (p|q, frame) row, lanes over the chunks (no index division)
+        for (int row = warp; row < 2 * kTile; row += kWarps) {
+            const int which = row >> 3, j = row & 7;
+            __nv_bfloat16 *dst = (which ? Qg : Pg) + (t.j0 + j) * Fp;
+            for (int c = lane; c < cpr; c += 32) {
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (j < t.nvalid) v = *reinterpret_cast<const uint4 *>(PQ_s + row * WLD + 8 * c);
+                *reinterpret_cast<uint4 *>(dst + 8 * c) = v;
+            }
         }
         for (int k = tid; k < KS * 16; k += kThreads) {
             uint32_t w[4];

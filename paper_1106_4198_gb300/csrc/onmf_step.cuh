@@ -59,23 +59,23 @@ static __device__ void stats_unit_mixed(const Shape &s, int mt, int ks, const __
     for (long long cb = jb; cb < je; cb += kChunk) {
         const int nf = (int)min((long long)kChunk, je - cb);
         const int nfr = (nf + 15) / 16 * 16;  // rows touched by the k16 steps
-        for (int i = tid; i < nfr * 4; i += kThreads) {
-            const int w = i / (nfr * 2), rem = i - w * nfr * 2;
-            const int jj = rem >> 1, half = rem & 1;
-            const __nv_bfloat16 *base = w ? Qg : Pg;
+        // P and Q rows (16 values = two 16-byte chunks per frame), no index division
+        for (int i = tid; i < nfr * 2; i += kThreads) {
+            const int jj = i >> 1, half = i & 1;
             const bool ok = jj < nf;
-            const __nv_bfloat16 *src = ok ? base + (cb + jj) * Fp + f0 + 8 * half : base;
-            __nv_bfloat16 *dst = (w ? Q_s : P_s) + jj * kPS + 8 * half;
-            cp_async16(dst, src, ok ? 16 : 0);
+            const long long o = (cb + jj) * Fp + f0 + 8 * half;
+            cp_async16(P_s + jj * kPS + 8 * half, ok ? Pg + o : Pg, ok ? 16 : 0);
+            cp_async16(Q_s + jj * kPS + 8 * half, ok ? Qg + o : Qg, ok ? 16 : 0);
         }
+        // H rows k0..k0+31: warp per row, lanes over 8-frame chunks
         const int nch = nfr / 8;
-        for (int i = tid; i < 32 * nch; i += kThreads) {
-            const int kk = i / nch, ch = i - kk * nch;
-            const int jj = 8 * ch;
-            const bool ok = jj < nf;
-            const __nv_bfloat16 *src = ok ? Hg + (long long)(k0 + kk) * betap + cb + jj : Hg;
-            cp_async16(H_s + kk * kHS + jj, src, ok ? 16 : 0);
-        }
+        for (int kk = warp; kk < 32; kk += kWarps)
+            for (int ch = lane; ch < nch; ch += 32) {
+                const int jj = 8 * ch;
+                const bool ok = jj < nf;
+                const __nv_bfloat16 *src = ok ? Hg + (long long)(k0 + kk) * betap + cb + jj : Hg;
+                cp_async16(H_s + kk * kHS + jj, src, ok ? 16 : 0);
+            }
         cp_async_commit();
         cp_async_wait_all();
         __syncthreads();
