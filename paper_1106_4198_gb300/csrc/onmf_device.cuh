@@ -47,8 +47,11 @@ __device__ __forceinline__ void red_release_gpu_add(unsigned *p, unsigned v) {
 
 // Grid-wide barrier for a cooperative (co-resident) launch. `epoch` counts
 // the barriers this CTA has passed; the counter must be zero at launch.
-// The wait is bounded: on timeout the CTA flags ERR_TIMEOUT and returns
-// false, and callers leave the kernel.
+// Thread 0 arrives with a release reduction after the CTA barrier and waits
+// with acquire loads before the next CTA barrier; release and acquire are
+// cumulative, so the writes of the whole CTA before the barrier are visible
+// to every CTA after it. The wait is bounded: on timeout the CTA flags
+// ERR_TIMEOUT and returns false, and callers leave the kernel.
 __device__ __forceinline__ bool grid_sync(unsigned *counter, unsigned nblocks,
                                           unsigned &epoch, int *err) {
     __syncthreads();
@@ -56,20 +59,18 @@ __device__ __forceinline__ bool grid_sync(unsigned *counter, unsigned nblocks,
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         s_ok = 1;
-        __threadfence();
         red_release_gpu_add(counter, 1u);
         const unsigned target = epoch * nblocks;
         const uint64_t t0 = global_ns();
         unsigned spins = 0;
         while (ld_acquire_gpu(counter) < target) {
-            if (++spins > 64) __nanosleep(64);
+            if (++spins > 1024) __nanosleep(32);
             if ((spins & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
                 flag_error(err, ERR_TIMEOUT);
                 s_ok = 0;
                 break;
             }
         }
-        __threadfence();
         if (read_error(err) != 0) s_ok = 0;  // one read, so every thread agrees
     }
     __syncthreads();

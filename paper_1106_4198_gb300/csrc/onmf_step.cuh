@@ -37,7 +37,9 @@ __host__ __device__ inline size_t stats_smem_bytes(int prec) {
 
 // Accumulate sum_j P[j][f] H[j][k] and sum_j Q[j][f] H[j][k] over frames
 // [jb, je) for the output tile rows 16*mt.. and columns 32*ks.. into
-// acc[2][16][32] (shared memory). Warp w: n-tile w & 3, P (w < 4) or Q.
+// acc[2][16][32] (shared memory). Warp w: P (w < 4) or Q, and a quarter of
+// the frames of each chunk; it loads each P/Q fragment once and applies it to
+// all four n8 tiles of k. The four quarters are added in order at the end.
 static __device__ void stats_unit_mixed(const Shape &s, int mt, int ks, const __nv_bfloat16 *Pg,
                                  const __nv_bfloat16 *Qg, const __nv_bfloat16 *Hg,
                                  long long betap, long long jb, long long je, unsigned char *smem,
@@ -47,7 +49,7 @@ static __device__ void stats_unit_mixed(const Shape &s, int mt, int ks, const __
     __nv_bfloat16 *P_s = reinterpret_cast<__nv_bfloat16 *>(smem);
     __nv_bfloat16 *Q_s = P_s + kChunk * kPS;
     __nv_bfloat16 *H_s = Q_s + kChunk * kPS;
-    const int nt = warp & 3, which = warp >> 2;
+    const int quarter = warp & 3, which = warp >> 2;
     const int Fp = s.Fp16;
     const int f0 = 16 * mt, k0 = 32 * ks;
     float c[4][4];
@@ -80,26 +82,35 @@ static __device__ void stats_unit_mixed(const Shape &s, int mt, int ks, const __
         cp_async_wait_all();
         __syncthreads();
         const int nks = nfr / 16;
-        const __nv_bfloat16 *hrow = H_s + (8 * nt + g) * kHS + 2 * tq;
+        const int kb = quarter * nks / 4, ke = (quarter + 1) * nks / 4;
         const __nv_bfloat16 *xrow = X_s + (r8 + 8 * (mi >> 1)) * kPS + 8 * (mi & 1);
-        for (int k4 = 0; k4 < nks; k4 += 4) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int ksi = k4 + u;
-                if (ksi < nks) {
-                    uint32_t a[4];
-                    ldmatrix_x4_trans(a, xrow + 16 * ksi * kPS);
-                    mma_bf16_16816(c[u], a, *reinterpret_cast<const uint32_t *>(hrow + 16 * ksi),
-                                   *reinterpret_cast<const uint32_t *>(hrow + 16 * ksi + 8));
-                }
-            }
+        const __nv_bfloat16 *hrow = H_s + (r8 + 8 * (mi >> 1)) * kHS + 8 * (mi & 1);
+        for (int ksi = kb; ksi < ke; ++ksi) {
+            uint32_t a[4], b0[4], b1[4];
+            ldmatrix_x4_trans(a, xrow + 16 * ksi * kPS);
+            ldmatrix_x4(b0, hrow + 16 * ksi);             // k rows 0..15
+            ldmatrix_x4(b1, hrow + 16 * kHS + 16 * ksi);  // k rows 16..31
+            mma_bf16_16816(c[0], a, b0[0], b0[1]);
+            mma_bf16_16816(c[1], a, b0[2], b0[3]);
+            mma_bf16_16816(c[2], a, b1[0], b1[1]);
+            mma_bf16_16816(c[3], a, b1[2], b1[3]);
         }
         __syncthreads();
     }
+    // quarters -> acc, in quarter order (the chunk buffers are free now)
+    float *red = reinterpret_cast<float *>(smem);  // [8 warps][16][32]
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const int ff = g + 8 * (e >> 1), kk = 8 * nt + 2 * tq + (e & 1);
-        acc[(which * 16 + ff) * 32 + kk] = (c[0][e] + c[1][e]) + (c[2][e] + c[3][e]);
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int ff = g + 8 * (e >> 1), kk = 8 * u + 2 * tq + (e & 1);
+            red[(warp * 16 + ff) * 32 + kk] = c[u][e];
+        }
+    __syncthreads();
+    for (int e = tid; e < 2 * 512; e += kThreads) {
+        const int w4 = e >> 9, rem = e & 511;  // P (0) or Q (1), then (ff, kk)
+        const float *r = red + (w4 * 4) * 512 + rem;
+        acc[w4 * 512 + rem] = ((r[0] + r[512]) + r[1024]) + r[1536];
     }
     __syncthreads();
 }
