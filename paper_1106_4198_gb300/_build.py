@@ -7,6 +7,7 @@ any source or header is newer than the library.
 import glob
 import os
 import subprocess
+import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -62,6 +63,8 @@ def build(force=False, verbose=False):
         out, _ = p.communicate()
         if p.returncode != 0:
             failed.append((cmd, out.decode(errors="replace")))
+        elif out.strip():  # warnings: show them, do not hide them
+            sys.stderr.write(out.decode(errors="replace"))
     if failed:
         msg = "\n".join(" ".join(c) + "\n" + o for c, o in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
