@@ -112,6 +112,24 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0,
 onmf_status onmf_push_frames(onmf_state *s, const float *V, int64_t ldv,
                              int64_t n, float *H_out, int64_t ldh);
 
+/* Warm restarts over a finite data set (Section 2.3, "Fresh or warm
+ * restarts" and "Finite data sets"): one pass of Algorithm 1 over the frames
+ * V[order[0]], V[order[1]], ..., V[order[n-1]] in that order, where each
+ * frame's h-solve starts from its kept activation H[order[i]] (instead of
+ * the fresh-restart point) and the final h is written back there; the
+ * config's n_inner applies (the paper takes a single update per visit). A
+ * caller that permutes the frames anew for every pass passes a new order.
+ *   V: device, frame rows of F floats, ld ldv >= F (the whole data set).
+ *   order: device int64 array of n row indices, or NULL for rows 0..n-1.
+ *   H: device, frame rows of K floats, ld ldh >= K, read and written.
+ * Frames are grouped into minibatches in pass order; a trailing partial
+ * minibatch waits in the staging buffer for the next warm push with the
+ * same H, or for onmf_flush. The kept activations are not rescaled with W.
+ * Errors: EINVAL (host pointers, sizes), ESTATE (frames of a fresh push are
+ * staged, or staged warm frames belong to another H), ECUDA. */
+onmf_status onmf_push_frames_warm(onmf_state *s, const float *V, int64_t ldv, int64_t n,
+                                  const int64_t *order, float *H, int64_t ldh);
+
 /* Run the partial minibatch left in the staging buffer (beta' < beta frames,
  * rho = r^(beta'/n_ref)). No-op when the buffer is empty. */
 onmf_status onmf_flush(onmf_state *s);

@@ -40,7 +40,7 @@ def _lib():
         lib.or_online_minibatch.restype = None
         lib.or_online_pass.restype = _l
         lib.or_online_pass.argtypes = [_i, _i, _l, _p, _l, _i, _i, _d, _d, _d,
-                                       _l, _i, _i, _i, _p, _p, _p, _p, _p, _p]
+                                       _l, _i, _i, _i, _p, _p, _p, _p, _p, _p, _p]
         lib.or_project.restype = None
         lib.or_project.argtypes = [_i, _i, _l, _p, _l, _p, _d, _d, _i, _p, _p]
         lib.or_batch_h0.restype = None
@@ -135,9 +135,11 @@ def rho(r, nb, n_ref):
 
 def online_pass(V, W, A=None, B=None, beta=50, n_in=5, eps=1e-12, gamma=0.5,
                 r=1.0, n_ref=0, normalize=True, rho_on_new=False, flush=True,
-                want_H=True, loss_sum=0.0):
-    """One in-order pass of Algorithm 1. V (N,F), W (K,F) [A, B (K,F)].
-    Returns dict(W, A, B, H (N,K) or None, loss_sum, mb_loss, frames)."""
+                want_H=True, loss_sum=0.0, H_init=None):
+    """One in-order pass of Algorithm 1. V (N,F), W (K,F) [A, B (K,F)];
+    H_init (N,K): warm-restart start points of the frames' h-solves (None:
+    fresh restarts). Returns dict(W, A, B, H (N,K) or None, loss_sum,
+    mb_loss, frames)."""
     V = _f32(V)
     N, F = V.shape
     W = _f64(W).copy()
@@ -145,13 +147,14 @@ def online_pass(V, W, A=None, B=None, beta=50, n_in=5, eps=1e-12, gamma=0.5,
     A = np.zeros((K, F)) if A is None else _f64(A).copy()
     B = np.zeros((K, F)) if B is None else _f64(B).copy()
     H = np.zeros((N, K)) if want_H else None
+    Hi = None if H_init is None else _f64(H_init)
     nmb = (N + beta - 1) // beta
     mb = np.zeros(max(nmb, 1))
     ls = ctypes.c_double(loss_sum)
     done = _lib().or_online_pass(F, K, N, _ptr(V), F, beta, n_in, eps, gamma, r,
                                  n_ref, int(normalize), int(rho_on_new),
-                                 int(flush), _ptr(W), _ptr(A), _ptr(B), _ptr(H),
-                                 ctypes.byref(ls), _ptr(mb))
+                                 int(flush), _ptr(W), _ptr(A), _ptr(B), _ptr(Hi),
+                                 _ptr(H), ctypes.byref(ls), _ptr(mb))
     nmb_done = (done + beta - 1) // beta if flush else done // beta
     return dict(W=W, A=A, B=B, H=H, loss_sum=ls.value, mb_loss=mb[:nmb_done],
                 frames=done)

@@ -238,12 +238,15 @@ double or_rho(double r, int64_t nb, int64_t n_ref) {
 void or_online_minibatch(int F, int K, int64_t nb, const float *V, int64_t ldv,
                          int n_in, double eps, double gamma, double r,
                          int64_t n_ref, int normalize, int rho_on_new,
-                         double *W, double *A, double *B, double *H_out,
-                         double *loss_out) {
+                         double *W, double *A, double *B, const double *H_init,
+                         double *H_out, double *loss_out) {
     double *H = (double *)malloc(sizeof(double) * K * (size_t)(nb > 0 ? nb : 1));
+    /* fresh restarts (H_init NULL) or warm restarts from the kept h of each
+     * frame (Section 2.3, "Fresh or warm restarts") */
 #pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int64_t j = 0; j < nb; ++j)
-        or_hsolve(F, K, W, V + j * ldv, eps, gamma, n_in, NULL, H + j * K, NULL);
+        or_hsolve(F, K, W, V + j * ldv, eps, gamma, n_in, H_init ? H_init + j * K : NULL,
+                  H + j * K, NULL);
     double rho = or_rho(r, nb, n_ref);
     or_stats_step(F, K, nb, V, ldv, H, eps, rho, normalize, rho_on_new, W, A, B,
                   loss_out);
@@ -254,13 +257,14 @@ void or_online_minibatch(int F, int K, int64_t nb, const float *V, int64_t ldv,
 /* One pass of Algorithm 1 over N frames in order, a dictionary step every
  * beta frames. The N mod beta frames left at the end form a partial
  * minibatch that is processed only when `flush` is set.
- *   W, A, B: state, updated in place. H_out: K x N or NULL.
+ *   W, A, B: state, updated in place. H_init: K x N start points (warm
+ *   restarts) or NULL (fresh restarts). H_out: K x N or NULL.
  *   mb_loss: per-minibatch d_IS sums, or NULL. Returns frames processed. */
 int64_t or_online_pass(int F, int K, int64_t N, const float *V, int64_t ldv,
                        int beta, int n_in, double eps, double gamma, double r,
                        int64_t n_ref, int normalize, int rho_on_new, int flush,
-                       double *W, double *A, double *B, double *H_out,
-                       double *loss_sum, double *mb_loss) {
+                       double *W, double *A, double *B, const double *H_init,
+                       double *H_out, double *loss_sum, double *mb_loss) {
     int64_t done = 0;
     int64_t m = 0;
     while (done < N) {
@@ -269,6 +273,7 @@ int64_t or_online_pass(int F, int K, int64_t N, const float *V, int64_t ldv,
         double l = 0.0;
         or_online_minibatch(F, K, nb, V + done * ldv, ldv, n_in, eps, gamma, r,
                             n_ref, normalize, rho_on_new, W, A, B,
+                            H_init ? H_init + done * K : NULL,
                             H_out ? H_out + done * K : NULL, &l);
         if (mb_loss) mb_loss[m] = l;
         /* running sum of the online loss L_T (Eq. online_loss), one term per

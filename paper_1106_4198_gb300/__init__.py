@@ -23,7 +23,7 @@ __all__ = [
     "onmf_synchronize", "onmf_get_W", "onmf_get_stats", "onmf_set_state",
     "onmf_project", "nmf_batch_step", "nmf_batch_init_H", "onmf_destroy",
     "onmf_status_string", "onmf_kernel_launches", "onmf_abi_version",
-    "onmf_project_static", "OnlineISNMF", "EXPORTED",
+    "onmf_project_static", "onmf_push_frames_warm", "OnlineISNMF", "EXPORTED",
 ]
 
 ONMF_FP32 = 0
@@ -40,6 +40,7 @@ EXPORTED = [
     "onmf_server_create", "onmf_server_open_stream", "onmf_server_submit",
     "onmf_server_poll", "onmf_server_get_W", "onmf_server_close_stream",
     "onmf_server_get_stats", "onmf_server_destroy", "onmf_selftest_wait",
+    "onmf_push_frames_warm",
 ]
 
 
@@ -111,6 +112,7 @@ def lib():
     L.onmf_init.argtypes = [ctypes.POINTER(onmf_config), _vp, _i32, _vp,
                             ctypes.POINTER(_vp)]
     L.onmf_push_frames.argtypes = [_vp, _vp, _i64, _i64, _vp, _i64]
+    L.onmf_push_frames_warm.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp, _i64]
     L.onmf_flush.argtypes = [_vp]
     L.onmf_synchronize.argtypes = [_vp]
     L.onmf_get_W.argtypes = [_vp, _vp, _i32]
@@ -151,7 +153,7 @@ def lib():
                  "nmf_batch_init_H", "onmf_project_static", "onmf_server_create",
                  "onmf_server_open_stream", "onmf_server_submit", "onmf_server_poll",
                  "onmf_server_get_W", "onmf_server_close_stream",
-                 "onmf_server_get_stats", "onmf_selftest_wait"):
+                 "onmf_server_get_stats", "onmf_selftest_wait", "onmf_push_frames_warm"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -257,6 +259,21 @@ def onmf_push_frames(state, V, H_out=None, n=None):
     _check(lib().onmf_push_frames(state, pv, ldv, n, ph, ldh), "onmf_push_frames")
 
 
+def onmf_push_frames_warm(state, V, H, order=None):
+    """Warm-restart pass over device frames V (N, F): frames V[order[i]] in
+    order (all rows if order is None), each h-solve starting from H[order[i]]
+    (device (N, K), updated in place). order: int64 device tensor or None."""
+    pv, ldv = _ptr_ld(V, V.shape[1])
+    ph, ldh = _ptr_ld(H, H.shape[1])
+    if order is not None:
+        import torch
+        assert order.dtype == torch.int64 and order.is_cuda and order.is_contiguous()
+        n, po = order.numel(), order.data_ptr()
+    else:
+        n, po = V.shape[0], None
+    _check(lib().onmf_push_frames_warm(state, pv, ldv, n, po, ph, ldh), "onmf_push_frames_warm")
+
+
 def onmf_flush(state):
     _check(lib().onmf_flush(state), "onmf_flush")
 
@@ -358,6 +375,9 @@ class OnlineISNMF:
 
     def push(self, V, H_out=None):
         onmf_push_frames(self.state, V, H_out)
+
+    def push_warm(self, V, H, order=None):
+        onmf_push_frames_warm(self.state, V, H, order)
 
     def flush(self):
         onmf_flush(self.state)

@@ -121,6 +121,13 @@ struct onmf_state {
     cudaEvent_t ring_full[2] = {nullptr, nullptr};  // slot filled by the copy
     cudaStream_t copy_stream = nullptr;
     long long ring_frames = 0;
+    // warm restarts: gathered frames and h of a pass, staged start points
+    float *gV = nullptr, *gH = nullptr, *Hin_stage = nullptr;
+    long long *stage_idx = nullptr;
+    long long gcap = 0;
+    bool warm_staged = false;  // the staged frames came from a warm push
+    float *warm_H = nullptr;   // their h rows live in this array (ld warm_ldh)
+    long long warm_ldh = 0;
     double *obj_h = nullptr;  // pinned
     long long t = 0;
     int sticky = ONMF_OK;
@@ -232,7 +239,8 @@ void onmf_destroy(onmf_state *s) {
     if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
     void *dev[] = {s->Wcm, s->Wrm, s->Wn, s->swpart, s->Wimg, s->Wrow, s->A, s->B, s->loss_sum, s->Pg,
                    s->Qg, s->Hg, s->loss_part, s->tmp_sum, s->bar, s->err_d, s->staging,
-                   s->Hstage, s->vring[0], s->vring[1], s->hring[0], s->hring[1]};
+                   s->Hstage, s->vring[0], s->vring[1], s->hring[0], s->hring[1],
+                   s->gV,     s->gH,       s->Hin_stage, s->stage_idx};
     for (void *p : dev)
         if (p) cudaFree(p);
     if (s->err_h) cudaFreeHost(s->err_h);
@@ -388,7 +396,8 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
 // Run nmb minibatches (all of beta frames except the last, nb_last) read
 // from device memory V (ldv), writing h to device H (ldh) when non-NULL.
 static onmf_status run_minibatches(onmf_state *s, const float *V, long long ldv, int nmb,
-                                   int nb_last, float *H, long long ldh) {
+                                   int nb_last, float *H, long long ldh,
+                                   const float *H_in = nullptr, long long ldh_in = 0) {
     if (nmb <= 0) return ONMF_OK;
     const onmf_config &c = s->cfg;
     StepArgs a;
@@ -407,6 +416,8 @@ static onmf_status run_minibatches(onmf_state *s, const float *V, long long ldv,
     a.rho_last = rho_of(c, nb_last);
     a.H_out = H;
     a.ldh = ldh;
+    a.H_in = H_in;
+    a.ldh_in = ldh_in;
     a.Wcm = s->Wcm;
     a.Wrm = s->Wrm;
     a.Wimg = s->Wimg;
@@ -436,6 +447,19 @@ static onmf_status run_minibatches(onmf_state *s, const float *V, long long ldv,
 static onmf_status run_staged(onmf_state *s) {
     const int n = s->staged;
     if (n == 0) return ONMF_OK;
+    if (s->warm_staged) {
+        // warm restarts: start points in Hin_stage, solved in place, then back
+        // to the caller's rows named by stage_idx
+        const int K = s->cfg.K;
+        onmf_status st = run_minibatches(s, s->staging, s->cfg.F, 1, n, s->Hin_stage, K,
+                                         s->Hin_stage, K);
+        if (st != ONMF_OK) return st;
+        CK(launch_scatter_rows(s->warm_H, s->warm_ldh, s->Hin_stage, K, s->stage_idx, 0, n, K,
+                               s->stream));
+        s->staged = 0;
+        s->warm_staged = false;
+        return ONMF_OK;
+    }
     bool want_h = !s->segs.empty();
     onmf_status st = run_minibatches(s, s->staging, s->cfg.F, 1, n, want_h ? s->Hstage : nullptr,
                                      s->cfg.K);
@@ -514,6 +538,10 @@ onmf_status onmf_push_frames(onmf_state *s, const float *V, int64_t ldv, int64_t
     if (st != ONMF_OK) return st;
     if (n < 0 || (n > 0 && !V) || ldv < s->cfg.F || (H_out && ldh < s->cfg.K)) return ONMF_EINVAL;
     if (n == 0) return ONMF_OK;
+    if (s->staged > 0 && s->warm_staged) {
+        snprintf(g_msg, sizeof g_msg, "frames of a warm-restart pass are staged: flush first");
+        return ONMF_ESTATE;
+    }
     if (is_device_ptr(V)) return push_device(s, V, ldv, n, H_out, ldh);
     // host frames: copy through a double-buffered device ring, chunk by chunk,
     // on a copy stream so the copy of chunk i+1 overlaps the steps of chunk i
@@ -547,6 +575,65 @@ onmf_status onmf_push_frames(onmf_state *s, const float *V, int64_t ldv, int64_t
         i += m;
         b ^= 1;
     }
+    return ONMF_OK;
+}
+
+onmf_status onmf_push_frames_warm(onmf_state *s, const float *V, int64_t ldv, int64_t n,
+                                  const int64_t *order, float *H, int64_t ldh) {
+    if (!s) return ONMF_EINVAL;
+    onmf_status st = check_sticky(s);
+    if (st != ONMF_OK) return st;
+    const onmf_config &c = s->cfg;
+    if (n < 0 || ldv < c.F || ldh < c.K || (n > 0 && (!V || !H))) return ONMF_EINVAL;
+    if (n == 0) return ONMF_OK;
+    if (!is_device_ptr(V) || !is_device_ptr(H) || (order && !is_device_ptr(order))) {
+        snprintf(g_msg, sizeof g_msg, "warm restarts take device V, H and order");
+        return ONMF_EINVAL;
+    }
+    if (s->staged > 0 && (!s->warm_staged || s->warm_H != H || s->warm_ldh != ldh)) {
+        snprintf(g_msg, sizeof g_msg, "other frames are staged: flush first");
+        return ONMF_ESTATE;
+    }
+    cudaStream_t q = s->stream;
+    const long long *idx = reinterpret_cast<const long long *>(order);
+    if (!s->Hin_stage) {
+        s->gcap = (long long)std::max(1, (1 << 18) / c.beta) * c.beta;
+        CK(cudaMalloc((void **)&s->Hin_stage, (size_t)c.beta * c.K * 4));
+        CK(cudaMalloc((void **)&s->stage_idx, (size_t)c.beta * 8));
+        CK(cudaMalloc((void **)&s->gV, (size_t)s->gcap * c.F * 4));
+        CK(cudaMalloc((void **)&s->gH, (size_t)s->gcap * c.K * 4));
+    }
+    s->warm_H = H;
+    s->warm_ldh = ldh;
+    // frames [i, i + m) of the pass -> staging rows [staged, staged + m)
+    auto stage = [&](long long i, long long m) -> onmf_status {
+        CK(launch_gather_rows(s->staging + (size_t)s->staged * c.F, c.F, V, ldv, idx, i, m, c.F, q));
+        CK(launch_gather_rows(s->Hin_stage + (size_t)s->staged * c.K, c.K, H, ldh, idx, i, m, c.K, q));
+        CK(launch_index_rows(s->stage_idx + s->staged, idx, i, m, q));
+        s->staged += (int)m;
+        s->warm_staged = true;
+        return ONMF_OK;
+    };
+    long long i = 0;
+    if (s->staged > 0) {
+        const long long take = std::min<long long>(c.beta - s->staged, n);
+        if ((st = stage(0, take)) != ONMF_OK) return st;
+        i = take;
+        if (s->staged == c.beta && (st = run_staged(s)) != ONMF_OK) return st;
+    }
+    long long nfull = (n - i) / c.beta;
+    while (nfull > 0) {
+        const long long chunk = std::min<long long>(nfull, s->gcap / c.beta);
+        const long long m = chunk * c.beta;
+        CK(launch_gather_rows(s->gV, c.F, V, ldv, idx, i, m, c.F, q));
+        CK(launch_gather_rows(s->gH, c.K, H, ldh, idx, i, m, c.K, q));
+        st = run_minibatches(s, s->gV, c.F, (int)chunk, c.beta, s->gH, c.K, s->gH, c.K);
+        if (st != ONMF_OK) return st;
+        CK(launch_scatter_rows(H, ldh, s->gH, c.K, idx, i, m, c.K, q));
+        i += m;
+        nfull -= chunk;
+    }
+    if (i < n && (st = stage(i, n - i)) != ONMF_OK) return st;
     return ONMF_OK;
 }
 

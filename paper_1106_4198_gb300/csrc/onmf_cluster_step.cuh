@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_cluster_kernel(StepArgs a,
         const double rho = lastmb ? a.rho_last : a.rho_full;
         const float *Vm = a.V + (long long)m * a.beta * a.ldv;
         float *Hm = a.H_out ? a.H_out + (long long)m * a.beta * a.ldh : nullptr;
+        const float *Him = a.H_in ? a.H_in + (long long)m * a.beta * a.ldh_in : nullptr;
         const int ntiles = ceil_div(nb, kClTile);
         // ---- phase 1: h-solve of every 32-frame tile, one cluster per tile
         if (cid < ntiles) {
@@ -51,8 +52,8 @@ __global__ void __launch_bounds__(kThreads, 1) online_cluster_kernel(StepArgs a,
                 t.ldv = a.ldv;
                 t.nvalid = min(kClTile, nb - tile * kClTile);
                 t.j0 = (long long)tile * kClTile;
-                t.H_in = nullptr;
-                t.ldh_in = 0;
+                t.H_in = Him;
+                t.ldh_in = a.ldh_in;
                 t.H_out = Hm;
                 t.ldh = a.ldh;
                 t.n_in = a.n_in;

@@ -461,6 +461,75 @@ cudaError_t launch_batch_h0(const Shape &s, const float *V, long long ldv, long 
     return cudaGetLastError();
 }
 
+// Row gather / scatter for passes over a finite data set in a given order:
+// dst row r <- src row idx[first + r] (gather), dst row idx[first + r] <- src
+// row r (scatter); idx NULL means rows first + r. One warp per row.
+__global__ void __launch_bounds__(kThreads) gather_rows_kernel(float *dst, long long ld_dst,
+                                                              const float *src, long long ld_src,
+                                                              const long long *idx, long long first,
+                                                              long long n, int width) {
+    const int lane = threadIdx.x & 31;
+    for (long long r = blockIdx.x * (long long)kWarps + (threadIdx.x >> 5); r < n;
+         r += (long long)gridDim.x * kWarps) {
+        const long long sr = idx ? idx[first + r] : first + r;
+        for (int c = lane; c < width; c += 32) dst[r * ld_dst + c] = src[sr * ld_src + c];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) scatter_rows_kernel(float *dst, long long ld_dst,
+                                                               const float *src, long long ld_src,
+                                                               const long long *idx,
+                                                               long long first, long long n,
+                                                               int width) {
+    const int lane = threadIdx.x & 31;
+    for (long long r = blockIdx.x * (long long)kWarps + (threadIdx.x >> 5); r < n;
+         r += (long long)gridDim.x * kWarps) {
+        const long long dr = idx ? idx[first + r] : first + r;
+        for (int c = lane; c < width; c += 32) dst[dr * ld_dst + c] = src[r * ld_src + c];
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) index_rows_kernel(long long *dst, const long long *idx,
+                                                             long long first, long long n) {
+    for (long long r = blockIdx.x * (long long)kThreads + threadIdx.x; r < n;
+         r += (long long)gridDim.x * kThreads)
+        dst[r] = idx ? idx[first + r] : first + r;
+}
+
+static int rows_grid(long long n) {
+    const long long g = (n + kWarps - 1) / kWarps;
+    return (int)(g < 4096 ? (g > 0 ? g : 1) : 4096);
+}
+
+cudaError_t launch_gather_rows(float *dst, long long ld_dst, const float *src, long long ld_src,
+                               const long long *idx, long long first, long long n, int width,
+                               cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    gather_rows_kernel<<<rows_grid(n), kThreads, 0, stream>>>(dst, ld_dst, src, ld_src, idx, first,
+                                                              n, width);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_rows(float *dst, long long ld_dst, const float *src, long long ld_src,
+                                const long long *idx, long long first, long long n, int width,
+                                cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    scatter_rows_kernel<<<rows_grid(n), kThreads, 0, stream>>>(dst, ld_dst, src, ld_src, idx,
+                                                               first, n, width);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_index_rows(long long *dst, const long long *idx, long long first, long long n,
+                              cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    const long long g = (n + kThreads - 1) / kThreads;
+    index_rows_kernel<<<(int)(g < 1024 ? g : 1024), kThreads, 0, stream>>>(dst, idx, first, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
 // Fault-path self-test: runs one of the library's bounded waits on a
 // condition that can never hold, so the wait must run out, flag ERR_TIMEOUT
 // and leave the kernel with the context intact.

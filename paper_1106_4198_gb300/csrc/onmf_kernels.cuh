@@ -66,6 +66,8 @@ struct StepArgs {
     double rho_full, rho_last;
     float *H_out;  // optional K x frames (ldh)
     long long ldh;
+    const float *H_in;  // warm restarts: start points, K x frames (ldh_in), or NULL
+    long long ldh_in;
     // state
     float *Wcm;
     float *Wrm;

@@ -56,6 +56,16 @@ cudaError_t launch_online_cluster(const StepArgs &a, int C, int grid, size_t sme
 cudaError_t launch_tiles_cluster(const TileArgs &a, int C, int grid, size_t smem,
                                  cudaStream_t stream);
 
+// Row gather/scatter by an index list (NULL: consecutive rows from `first`).
+cudaError_t launch_gather_rows(float *dst, long long ld_dst, const float *src, long long ld_src,
+                               const long long *idx, long long first, long long n, int width,
+                               cudaStream_t stream);
+cudaError_t launch_scatter_rows(float *dst, long long ld_dst, const float *src, long long ld_src,
+                                const long long *idx, long long first, long long n, int width,
+                                cudaStream_t stream);
+cudaError_t launch_index_rows(long long *dst, const long long *idx, long long first, long long n,
+                              cudaStream_t stream);
+
 cudaError_t launch_wait_selftest(int which, unsigned *counter, int *err,
                                  unsigned long long *elapsed, cudaStream_t stream);
 

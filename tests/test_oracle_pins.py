@@ -342,6 +342,44 @@ def test_online_r0_full_batch_equals_first_batch_iteration():
     assert np.allclose(Hb, out["H"] * s[None, :], rtol=1e-12)
 
 
+# ------------------------------------------------- P11: warm restarts
+
+
+def test_warm_restart_from_fresh_start_point_is_the_fresh_restart():
+    """Section 2.3 "Fresh or warm restarts": a warm start from the
+    fresh-restart point itself reproduces the fresh restart, bit for bit
+    (one minibatch, so both use W0)."""
+    r = rng(41)
+    F, K, N = 20, 3, 30
+    V = rand_V(r, N, F)
+    W0 = rand_W(r, K, F)
+    fresh = oracle.online_pass(V, W0, beta=N, n_in=4)
+    warm = oracle.online_pass(V, W0, beta=N, n_in=4, H_init=oracle.batch_h0(V, W0))
+    for k in ("W", "A", "B", "H"):
+        assert np.array_equal(fresh[k], warm[k]), k
+    assert fresh["loss_sum"] == warm["loss_sum"]
+
+
+def test_warm_passes_over_the_whole_set_are_batch_iterations():
+    """With the whole finite set as one minibatch, r = 0, one h update per
+    visit and warm restarts, every pass is one batch MU cycle (Section 2.1)
+    from the same (W, H); without the rescale the kept H is the batch H."""
+    r = rng(42)
+    F, K, N = 24, 3, 40
+    V = rand_V(r, N, F)
+    W0 = rand_W(r, K, F)
+    H = r.gamma(1.0, 1.0, size=(N, K)) + 0.1
+    W, A, B = W0, None, None
+    Hk = H.copy()
+    for _ in range(3):
+        out = oracle.online_pass(V, W, A, B, beta=N, n_in=1, r=0.0, n_ref=N,
+                                 normalize=False, H_init=Hk)
+        W, A, B, Hk = out["W"], out["A"], out["B"], out["H"]
+    Wb, Hb, _ = oracle.batch(V, W0, H, n_iter=3, normalize=False)
+    assert np.max(np.abs(W - Wb) / Wb) < 1e-12
+    assert np.max(np.abs(Hk - Hb) / Hb) < 1e-12
+
+
 # ------------------------------------------- P8: scale equivariance (exact)
 
 
