@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--cpu-sample-minibatches", type=int, default=120)
     p.add_argument("--skip-c2", action="store_true",
                    help="skip the objective-vs-time comparison (online vs batch)")
+    p.add_argument("--skip-study", action="store_true",
+                   help="skip the forgetting-factor / init / warm-restart study")
     p.add_argument("--serve-seconds", type=float, default=30.0,
                    help="wall window of the serving replay (0 skips serving)")
     p.add_argument("--serve-streams", type=int, default=256)
@@ -509,6 +511,99 @@ def run_c2(precision):
     return out
 
 
+# ------------------------------------------------ study: r, beta, init, passes
+
+STUDY_R = (0.5, 0.7, 0.9, 1.0)
+STUDY_BETA = (1, 10, 100, 1000)
+
+
+def run_study(precision):
+    """The parameter study of the paper's experiments (Section 3) on the
+    112,500 x 513 gamma-model spectrogram with K = 50, split into 100,000
+    training frames and 12,500 held-out frames. Every score is the mean
+    d_IS per held-out frame with W fixed and h re-solved from the fresh
+    restart (10 iterations); times are CUDA-event device times of training.
+      - forgetting factor: one pass for every r in {0.5, 0.7, 0.9, 1} and
+        beta in {1, 10, 100, 1000}, rho = r^(beta / 100,000);
+      - initial dictionary: random Gamma(1,1) columns against 50 training
+        frames (normalized), at beta = 1000, r = 0.7;
+      - warm restarts: 5 passes with a new permutation each, one h update
+        per visit, kept activations started at the batch start point."""
+    import torch
+
+    import paper_1106_4198_gb300 as onmf
+    import synth
+
+    F_, K_, N_ = C2_F, C2_K, C2_N
+    n_train = 100_000
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    seed = synth.DATA_SEED + 2
+    Wstar = torch.as_tensor(synth.dictionary(F_, K_, seed), dtype=torch.float32, device=dev)
+    V = synth.device_frames(F_, K_, N_, seed=seed, chunk=0, Wstar=Wstar)
+    Vtr, Vte = V[:n_train], V[n_train:]
+    Hte = torch.empty((N_ - n_train, K_), device=dev)
+    W0 = synth.init_dictionary(F_, K_)
+
+    def score(W):
+        s = onmf.OnlineISNMF(F_, K_, W, stream=stream, beta=1000, n_inner=N_IN,
+                             precision=precision)
+        obj = s.project(Vte, Hte, n_inner=N_IN, want_obj=True)
+        s.close()
+        return obj / (N_ - n_train)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    def one_pass(W_init, beta, r):
+        m = onmf.OnlineISNMF(F_, K_, W_init, stream=stream, beta=beta, n_inner=N_IN,
+                             precision=precision, r=r, n_ref=n_train)
+        ms = timed(lambda: (m.push(Vtr), m.flush()))
+        W = m.W()
+        m.close()
+        return W, ms
+
+    grid = []
+    for r in STUDY_R:
+        for beta in STUDY_BETA:
+            W, ms = one_pass(W0, beta, r)
+            sc = score(W)
+            grid.append({"r": r, "beta": beta, "score": sc if np.isfinite(sc) else None,
+                         "ms": ms})
+    # initial dictionary from training frames (the paper's protocol)
+    pick = np.random.default_rng(8).choice(n_train, K_, replace=False)
+    Wd = Vtr[torch.as_tensor(pick, device=dev)].cpu().numpy().astype(np.float64)
+    Wd /= Wd.sum(axis=1, keepdims=True)
+    init = {}
+    for name, Wi in (("gamma", W0), ("training_frames", Wd.astype(np.float32))):
+        W, ms = one_pass(Wi, 1000, 0.7)
+        init[name] = {"score_start": score(Wi), "score": score(W), "ms": ms}
+    # warm restarts: several permuted passes, one h update per visit
+    m = onmf.OnlineISNMF(F_, K_, W0, stream=stream, beta=1000, n_inner=1,
+                         precision=precision, r=0.7, n_ref=n_train)
+    Wt = torch.as_tensor(np.asarray(W0, dtype=np.float32), device=dev).contiguous()
+    Hk = torch.zeros((n_train, K_), device=dev)
+    onmf.nmf_batch_init_H(Vtr, Wt, Hk, stream=stream)
+    rng = np.random.default_rng(9)
+    warm, t = [], 0.0
+    for p in range(5):
+        order = torch.as_tensor(rng.permutation(n_train), dtype=torch.int64, device=dev)
+        t += timed(lambda: (m.push_warm(Vtr, Hk, order), m.flush()))
+        warm.append({"pass": p + 1, "ms": t, "score": score(m.W())})
+    m.close()
+    best = min((g for g in grid if g["score"] is not None), key=lambda g: g["score"])
+    return {"workload": "F=513 K=50 gamma-model spectrogram, 100,000 training and 12,500 "
+                        "held-out frames; score = mean d_IS per held-out frame",
+            "precision": "mixed" if precision == onmf.ONMF_MIXED else "fp32",
+            "score_of_initial_W": score(W0),
+            "r_beta_grid": grid, "best": best, "init": init, "warm_passes": warm}
+
+
 def cpu_oracle_rate(n_mb, threads):
     """Frames/s of the FP64 oracle on a bounded sample of the workload."""
     import numpy as np
@@ -582,6 +677,9 @@ def main():
         if not args.skip_c2 and world == 1:
             import paper_1106_4198_gb300 as onmf
             out["objective_vs_time"] = run_c2(onmf.ONMF_MIXED)
+        if not args.skip_study and world == 1:
+            import paper_1106_4198_gb300 as onmf
+            out["study"] = run_study(onmf.ONMF_MIXED)
         if args.serve_seconds > 0 and world == 1:
             import paper_1106_4198_gb300 as onmf
             out["serving"] = run_serving(args, onmf.ONMF_MIXED)
