@@ -547,7 +547,9 @@ onmf_status onmf_push_frames(onmf_state *s, const float *V, int64_t ldv, int64_t
     // on a copy stream so the copy of chunk i+1 overlaps the steps of chunk i
     const onmf_config &c = s->cfg;
     if (!s->vring[0]) {
-        s->ring_frames = (long long)std::max(1, (1 << 18) / c.beta) * c.beta;
+        // slots of ~64k frames: small enough that the copy of a push's first
+        // slot (the one part not hidden behind compute) stays short
+        s->ring_frames = (long long)std::max(1, (1 << 16) / c.beta) * c.beta;
         CK(cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking));
         for (int b = 0; b < 2; ++b) {
             CK(cudaMalloc((void **)&s->vring[b], (size_t)s->ring_frames * c.F * 4));
