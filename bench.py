@@ -30,7 +30,6 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 F, K, BETA, N_IN = 513, 100, 1000, 10
-HSOLVE = os.environ.get("ONMF_HSOLVE", "mma")  # h-solve variant the library selects
 FLOP_PER_FRAME = (6 * N_IN + 6) * F * K  # algorithmic flops of one frame
 METRIC = "online IS-NMF frames/s (F=513,K=100)"
 WORKLOAD = "online IS-NMF long stream F=513 K=100 beta=1000 n_inner=10, 1e6 frames/step"
@@ -204,9 +203,16 @@ def run_ours(args):
               for c in range(args.steps)]
     torch.cuda.synchronize()
 
+    # the mixed path runs the h-solve kernel the autotuner measures fastest
+    tune_cfg = onmf.onmf_config_default(F, K, precision=onmf.ONMF_MIXED, beta=BETA,
+                                        n_inner=N_IN)
+    hsolve, tune_us, _ = onmf.onmf_autotune(tune_cfg, stream=stream)
+    hname = onmf.HSOLVE_NAMES[hsolve]
+
     def timed_pass(precision, record_launch_times=False):
         m = onmf.OnlineISNMF(F, K, W0, stream=stream, beta=BETA, n_inner=N_IN,
-                             precision=precision)
+                             precision=precision,
+                             hsolve=hsolve if precision == onmf.ONMF_MIXED else 0)
         for w in range(args.warmup):
             m.push(chunks[w % len(chunks)])
         m.sync()
@@ -242,7 +248,7 @@ def run_ours(args):
         host[0].copy_(chunks[0])
         host[1].copy_(chunks[1 % len(chunks)])
         m = onmf.OnlineISNMF(F, K, W0, stream=stream, beta=BETA, n_inner=N_IN,
-                             precision=onmf.ONMF_MIXED)
+                             precision=onmf.ONMF_MIXED, hsolve=hsolve)
         for w in range(args.warmup):
             m.push(host[w % 2].numpy())
         m.sync()
@@ -272,11 +278,11 @@ def run_ours(args):
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": (NCU_TRAFFIC_PER_FRAME[HSOLVE] * fps
-                            if HSOLVE in NCU_TRAFFIC_PER_FRAME else None),
+                "traffic": (NCU_TRAFFIC_PER_FRAME[hname] * fps
+                            if hname in NCU_TRAFFIC_PER_FRAME else None),
                 "traffic_note": "DRAM bytes per launch of %d frames, scaled from an ncu "
                                 "capture of 64,000 frames" % fps,
-                "kernel": "online step kernel, mixed precision, %s h-solve" % HSOLVE,
+                "kernel": "online step kernel, mixed precision, %s h-solve" % hname,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"
                 if peaks else "fallback"}
         out = {
@@ -289,6 +295,8 @@ def run_ours(args):
                        "n_inner": N_IN, "frames_per_step": fps,
                        "global_batch": fps * world,
                        "l2": "inputs 2.05 GB/step > L2, no flush",
+                       "hsolve": hname,
+                       "autotune_us_per_minibatch": tune_us,
                        "parallelism": "replicas" if world > 1 else "single"},
             "fp32_value": (total_frames / (fp32["ms"] / 1e3)) if fp32 else None,
             "speedup_vs_fp32": (fp32["ms"] / mixed["ms"]) if fp32 else None,

@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define ONMF_ABI_VERSION 1
+#define ONMF_ABI_VERSION 2
 
 typedef struct onmf_state onmf_state;
 
@@ -58,6 +58,23 @@ typedef enum {
                        (K > 128: the cluster h-solve; serving: K <= 128) */
 } onmf_precision;
 
+/* Kernel of the mixed-precision h-solve (no counterpart in the paper; the
+ * arithmetic is the same, the order of the sums differs):
+ *   AUTO     mma for K <= 128, cluster for K > 128 (the environment variable
+ *            ONMF_HSOLVE=mma|tc|cluster overrides AUTO where the shape allows);
+ *   MMA      one CTA per 8-frame tile, W^T in shared memory, mma.sync (K <= 128);
+ *   TC       tcgen05 with W in tensor memory, 16-frame tiles (K <= 128, F >= 128
+ *            with at most 32 rows past the last 128-row tile);
+ *   CLUSTER  a cluster of CTAs per 32-frame tile, W split by rows (K <= 256).
+ * A choice the shape does not allow is rejected with EINVAL. onmf_autotune
+ * picks one by measurement. Ignored on the FP32 path. */
+typedef enum {
+    ONMF_HSOLVE_AUTO = 0,
+    ONMF_HSOLVE_MMA = 1,
+    ONMF_HSOLVE_TC = 2,
+    ONMF_HSOLVE_CLUSTER = 3
+} onmf_hsolve;
+
 /* Parameters of Algorithm 1 (Section 2.3). */
 typedef struct {
     int32_t F;          /* frequency bins (rows of V and W), >= 1              */
@@ -72,12 +89,12 @@ typedef struct {
     int32_t rho_on_new; /* 0: A <- rho*A + sum a (past scaled, default);
                            1: A <- A + rho*sum a (literal Algorithm 1)          */
     int32_t precision;  /* onmf_precision                                       */
-    int32_t reserved;   /* must be 0                                            */
+    int32_t hsolve;     /* onmf_hsolve: h-solve kernel of the mixed path (0 = auto) */
 } onmf_config;
 
 /* Fill *cfg with the defaults for an F x K problem: beta = 1000,
  * n_inner = 10, eps = 1e-12, r = 1, n_ref = 0, h_exponent = 0.5,
- * normalize = 1, rho_on_new = 0, precision = ONMF_FP32. */
+ * normalize = 1, rho_on_new = 0, precision = ONMF_FP32, hsolve = AUTO. */
 void onmf_config_default(onmf_config *cfg, int32_t F, int32_t K);
 
 /* Create an online state (Algorithm 1, "Input": W^(0), A^(0) = B^(0) = 0).
@@ -323,6 +340,20 @@ int64_t onmf_kernel_launches(void);
  * Returns ETIMEOUT when the wait ran out as designed, OK if it did not,
  * EINVAL (which out of range), ENOMEM, ECUDA. */
 onmf_status onmf_selftest_wait(int32_t which, void *stream, int64_t *elapsed_ns);
+
+/* Autotuner (no counterpart in the paper): time every mixed-precision
+ * h-solve kernel the shape in *cfg allows (cfg->hsolve is ignored) on a
+ * synthetic stream of 23 minibatches on `stream` (3 warm-up, 20 timed with
+ * CUDA events) and return the fastest in *hsolve_out (ONMF_HSOLVE_*).
+ *   cache_path: NULL, or a file of JSON lines keyed by the device name, F,
+ *       K, beta and n_inner; a hit returns the stored choice without timing
+ *       (*from_cache = 1), a miss appends the new result.
+ *   us_out: NULL or 4 doubles, microseconds per minibatch indexed by
+ *       ONMF_HSOLVE_* (-1 for kernels not timed).
+ * On the FP32 path it returns AUTO without timing. Blocks until done.
+ * Errors: EINVAL (no kernel fits the shape), ENOMEM, ECUDA. */
+onmf_status onmf_autotune(const onmf_config *cfg, void *stream, const char *cache_path,
+                          int32_t *hsolve_out, double *us_out, int32_t *from_cache);
 
 /* ABI version (ONMF_ABI_VERSION). */
 int32_t onmf_abi_version(void);

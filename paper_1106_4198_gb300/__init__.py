@@ -23,11 +23,14 @@ __all__ = [
     "onmf_synchronize", "onmf_get_W", "onmf_get_stats", "onmf_set_state",
     "onmf_project", "nmf_batch_step", "nmf_batch_init_H", "onmf_destroy",
     "onmf_status_string", "onmf_kernel_launches", "onmf_abi_version",
-    "onmf_project_static", "onmf_push_frames_warm", "OnlineISNMF", "EXPORTED",
+    "onmf_project_static", "onmf_push_frames_warm", "onmf_autotune", "OnlineISNMF", "EXPORTED",
 ]
 
 ONMF_FP32 = 0
 ONMF_MIXED = 1
+# h-solve kernels of the mixed path (onmf_config.hsolve)
+ONMF_HSOLVE_AUTO, ONMF_HSOLVE_MMA, ONMF_HSOLVE_TC, ONMF_HSOLVE_CLUSTER = 0, 1, 2, 3
+HSOLVE_NAMES = {0: "auto", 1: "mma", 2: "tc", 3: "cluster"}
 ONMF_ETIMEOUT = 6
 
 # Every symbol include/onmf.h declares.
@@ -40,7 +43,7 @@ EXPORTED = [
     "onmf_server_create", "onmf_server_open_stream", "onmf_server_submit",
     "onmf_server_poll", "onmf_server_get_W", "onmf_server_close_stream",
     "onmf_server_get_stats", "onmf_server_destroy", "onmf_selftest_wait",
-    "onmf_push_frames_warm",
+    "onmf_push_frames_warm", "onmf_autotune",
 ]
 
 
@@ -51,7 +54,7 @@ class onmf_config(ctypes.Structure):
         ("eps", ctypes.c_double), ("r", ctypes.c_double),
         ("n_ref", ctypes.c_int64), ("h_exponent", ctypes.c_double),
         ("normalize", ctypes.c_int32), ("rho_on_new", ctypes.c_int32),
-        ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("hsolve", ctypes.c_int32),
     ]
 
 
@@ -113,6 +116,9 @@ def lib():
                             ctypes.POINTER(_vp)]
     L.onmf_push_frames.argtypes = [_vp, _vp, _i64, _i64, _vp, _i64]
     L.onmf_push_frames_warm.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp, _i64]
+    L.onmf_autotune.argtypes = [ctypes.POINTER(onmf_config), _vp, ctypes.c_char_p,
+                                ctypes.POINTER(_i32), ctypes.POINTER(_d * 4),
+                                ctypes.POINTER(_i32)]
     L.onmf_flush.argtypes = [_vp]
     L.onmf_synchronize.argtypes = [_vp]
     L.onmf_get_W.argtypes = [_vp, _vp, _i32]
@@ -153,7 +159,8 @@ def lib():
                  "nmf_batch_init_H", "onmf_project_static", "onmf_server_create",
                  "onmf_server_open_stream", "onmf_server_submit", "onmf_server_poll",
                  "onmf_server_get_W", "onmf_server_close_stream",
-                 "onmf_server_get_stats", "onmf_selftest_wait", "onmf_push_frames_warm"):
+                 "onmf_server_get_stats", "onmf_selftest_wait", "onmf_push_frames_warm",
+                 "onmf_autotune"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -272,6 +279,20 @@ def onmf_push_frames_warm(state, V, H, order=None):
     else:
         n, po = V.shape[0], None
     _check(lib().onmf_push_frames_warm(state, pv, ldv, n, po, ph, ldh), "onmf_push_frames_warm")
+
+
+def onmf_autotune(cfg, cache_path=None, stream=None):
+    """Time every mixed h-solve kernel the shape of cfg allows; returns
+    (hsolve, {name: us per minibatch}, from_cache)."""
+    h = _i32(0)
+    us = (_d * 4)()
+    fc = _i32(0)
+    _check(lib().onmf_autotune(ctypes.byref(cfg), _stream_handle(stream),
+                               cache_path.encode() if cache_path else None,
+                               ctypes.byref(h), ctypes.byref(us), ctypes.byref(fc)),
+           "onmf_autotune")
+    times = {HSOLVE_NAMES[i]: us[i] for i in (1, 2, 3) if us[i] >= 0}
+    return int(h.value), times, bool(fc.value)
 
 
 def onmf_flush(state):

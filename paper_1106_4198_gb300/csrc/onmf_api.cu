@@ -79,8 +79,8 @@ size_t tc_min_smem(int prec, size_t smem) {
     return (prec == PREC_TC && smem < one_per_sm) ? one_per_sm : smem;
 }
 
-int pick_prec(int precision, const Shape &sh) {
-    return select_prec(precision == ONMF_MIXED, sh);
+int pick_prec(int precision, const Shape &sh, int hsolve = ONMF_HSOLVE_AUTO) {
+    return select_prec(precision == ONMF_MIXED, sh, hsolve);
 }
 
 onmf_status ensure_configured() {
@@ -261,7 +261,7 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
     const onmf_config &c = *cfg;
     if (c.F < 1 || c.F > 8192 || c.K < 1 || c.K > 256 || c.beta < 1 || c.beta > (1 << 20) ||
         c.n_inner < 0 || c.n_inner > 100000 || !(c.eps >= 0.0) || !std::isfinite(c.eps) ||
-        !(c.r >= 0.0 && c.r <= 1.0) || !(c.h_exponent > 0.0) || c.reserved != 0 ||
+        !(c.r >= 0.0 && c.r <= 1.0) || !(c.h_exponent > 0.0) || c.hsolve < 0 || c.hsolve > 3 ||
         (c.precision != ONMF_FP32 && c.precision != ONMF_MIXED))
         return ONMF_EINVAL;
     if (c.precision == ONMF_MIXED && c.F > 1024) {
@@ -274,7 +274,12 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
     s->cfg = c;
     s->s = make_shape(c.F, c.K);
     s->stream = reinterpret_cast<cudaStream_t>(stream);
-    s->prec = pick_prec(c.precision, s->s);
+    s->prec = pick_prec(c.precision, s->s, c.hsolve);
+    if (s->prec < 0) {
+        snprintf(g_msg, sizeof g_msg, "h-solve %d does not support F=%d K=%d", c.hsolve, c.F, c.K);
+        delete s;
+        return ONMF_EINVAL;
+    }
     const Shape &sh = s->s;
     const size_t FK = (size_t)c.F * c.K;
     s->betap = (c.beta + 15) / 16 * 16;

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <vector>
 
+#include "onmf.h"
 #include "onmf_cluster.cuh"
 #include "onmf_device.cuh"
 #include "onmf_kernels.cuh"
@@ -218,13 +219,22 @@ int cluster_choose(const Shape &s, long long frames, int num_sms, size_t smem_li
     return best;
 }
 
-// K > 128 needs the cluster h-solve (the whole bf16 W^T no longer fits one
-// CTA's shared memory); ONMF_HSOLVE=mma|tc|cluster selects a variant where
+// The h-solve kernel for a shape and an onmf_hsolve choice, or -1 if the
+// shape does not allow that choice. K > 128 needs the cluster h-solve (the
+// whole bf16 W^T no longer fits one CTA's shared memory). Under AUTO the
+// environment variable ONMF_HSOLVE=mma|tc|cluster selects a variant where
 // the shape allows it.
-int select_prec(bool mixed, const Shape &s) {
+int select_prec(bool mixed, const Shape &s, int hsolve) {
     if (!mixed) return PREC_FP32;
-    const char *env = getenv("ONMF_HSOLVE");
     const bool big = s.Kp > 128;
+    switch (hsolve) {
+    case ONMF_HSOLVE_MMA: return big ? -1 : PREC_MIXED;
+    case ONMF_HSOLVE_TC: return (!big && tc_supported(s)) ? PREC_TC : -1;
+    case ONMF_HSOLVE_CLUSTER: return PREC_CL;
+    case ONMF_HSOLVE_AUTO: break;
+    default: return -1;
+    }
+    const char *env = getenv("ONMF_HSOLVE");
     if (env && strcmp(env, "tc") == 0 && !big && tc_supported(s)) return PREC_TC;
     if (env && strcmp(env, "mma") == 0 && !big) return PREC_MIXED;
     if (env && strcmp(env, "cluster") == 0) return PREC_CL;

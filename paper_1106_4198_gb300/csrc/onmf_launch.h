@@ -37,8 +37,9 @@ cudaError_t launch_batch_scale_h(int K, long long N, float *H, const float *scal
                                  cudaStream_t stream);
 cudaError_t launch_batch_h0(const Shape &s, const float *V, long long ldv, long long N, float eps,
                             const float *swpart, float *H, cudaStream_t stream);
-// h-solve variant for a shape (PREC_FP32 unless mixed).
-int select_prec(bool mixed, const Shape &s);
+// h-solve variant for a shape and an onmf_hsolve choice (PREC_FP32 unless
+// mixed; -1 if the shape does not allow the choice).
+int select_prec(bool mixed, const Shape &s, int hsolve);
 
 // Cluster h-solve (PREC_CL): C CTAs per cluster.
 struct ClusterTiles {

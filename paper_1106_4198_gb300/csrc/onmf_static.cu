@@ -64,7 +64,7 @@ extern "C" onmf_status onmf_project_static(const float *W, int32_t F, int32_t K,
     if (precision == ONMF_MIXED && F > 1024) return ONMF_EINVAL;
     const Shape sh = make_shape(F, K);
     // the same h-solve as onmf_project
-    const int prec = select_prec(precision == ONMF_MIXED, sh);
+    const int prec = select_prec(precision == ONMF_MIXED, sh, ONMF_HSOLVE_AUTO);
     ClusterTiles ct;
     if (prec == PREC_CL) {
         ct = cluster_tiles(sh, n > 0 ? n : 1);

@@ -1,0 +1,149 @@
+// onmf_autotune: picks the mixed-precision h-solve kernel for a shape by
+// timing every kernel the shape allows on a synthetic stream (CUDA events on
+// the caller's stream), with an optional cache file of JSON lines keyed by
+// the device name and the shape.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "onmf.h"
+
+namespace {
+
+// Positive synthetic frames v = -log(u) + 1e-3 with u uniform from a
+// counter hash (Wellons' "lowbias32" integer hash); only the timing of the
+// kernels matters here, not the values.
+__global__ void tune_fill(float *V, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        unsigned x = (unsigned)i * 2654435761u + 0x9e3779b9u;
+        x ^= x >> 16;
+        x *= 0x7feb352du;
+        x ^= x >> 15;
+        x *= 0x846ca68bu;
+        x ^= x >> 16;
+        const float u = (float)(x >> 8) * (1.0f / 16777216.0f) + 1e-7f;
+        V[i] = -logf(u) + 1e-3f;
+    }
+}
+
+struct Key {
+    std::string device;
+    int F, K, beta, n_inner;
+};
+
+bool same(const Key &a, const Key &b) {
+    return a.device == b.device && a.F == b.F && a.K == b.K && a.beta == b.beta &&
+           a.n_inner == b.n_inner;
+}
+
+// One cache line: {"device": "...", "F": 513, "K": 100, "beta": 1000,
+// "n_inner": 10, "hsolve": 1, "us_per_minibatch": [a, b, c, d]}
+bool parse(const char *line, Key &k, int &hsolve, double (&us)[4]) {
+    const char *d = strstr(line, "\"device\": \"");
+    if (!d) return false;
+    d += strlen("\"device\": \"");
+    const char *e = strchr(d, '"');
+    if (!e) return false;
+    k.device.assign(d, e - d);
+    return sscanf(e + 1,
+                  ", \"F\": %d, \"K\": %d, \"beta\": %d, \"n_inner\": %d, \"hsolve\": %d, "
+                  "\"us_per_minibatch\": [%lf, %lf, %lf, %lf]}",
+                  &k.F, &k.K, &k.beta, &k.n_inner, &hsolve, &us[0], &us[1], &us[2], &us[3]) == 9;
+}
+
+}  // namespace
+
+extern "C" onmf_status onmf_autotune(const onmf_config *cfg, void *stream, const char *cache_path,
+                                     int32_t *hsolve_out, double *us_out, int32_t *from_cache) {
+    if (!cfg || !hsolve_out) return ONMF_EINVAL;
+    double us[4] = {-1.0, -1.0, -1.0, -1.0};
+    if (from_cache) *from_cache = 0;
+    if (cfg->precision != ONMF_MIXED) {
+        *hsolve_out = ONMF_HSOLVE_AUTO;  // the FP32 path has one h-solve
+        if (us_out) memcpy(us_out, us, sizeof us);
+        return ONMF_OK;
+    }
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+        return ONMF_ECUDA;
+    const Key key{prop.name, cfg->F, cfg->K, cfg->beta, cfg->n_inner};
+    if (cache_path) {
+        if (FILE *f = fopen(cache_path, "r")) {
+            char line[1024];
+            int found = -1;
+            double cus[4];
+            while (fgets(line, sizeof line, f)) {
+                Key k;
+                int h;
+                if (parse(line, k, h, cus) && same(k, key)) {
+                    found = h;
+                    memcpy(us, cus, sizeof us);
+                }
+            }
+            fclose(f);
+            if (found > 0) {
+                *hsolve_out = found;
+                if (us_out) memcpy(us_out, us, sizeof us);
+                if (from_cache) *from_cache = 1;
+                return ONMF_OK;
+            }
+        }
+    }
+    cudaStream_t q = reinterpret_cast<cudaStream_t>(stream);
+    const int warm = 3, timed = 20;
+    const long long frames = (long long)(warm + timed) * cfg->beta;
+    float *V = nullptr;
+    if (cudaMalloc((void **)&V, (size_t)frames * cfg->F * 4) != cudaSuccess) return ONMF_ENOMEM;
+    tune_fill<<<1024, 256, 0, q>>>(V, frames * cfg->F);
+    std::vector<float> W0((size_t)cfg->F * cfg->K);
+    for (size_t i = 0; i < W0.size(); ++i) W0[i] = 1.0f / cfg->F * (1.0f + 0.5f * (float)((i * 7919) % 13) / 13.f);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = -1;
+    onmf_status rc = ONMF_OK;
+    for (int h = ONMF_HSOLVE_MMA; h <= ONMF_HSOLVE_CLUSTER && rc == ONMF_OK; ++h) {
+        onmf_config c = *cfg;
+        c.hsolve = h;
+        onmf_state *s = nullptr;
+        if (onmf_init(&c, W0.data(), 0, stream, &s) != ONMF_OK) continue;  // not for this shape
+        rc = onmf_push_frames(s, V, c.F, (long long)warm * c.beta, nullptr, 0);
+        if (rc == ONMF_OK) rc = onmf_synchronize(s);
+        if (rc == ONMF_OK) {
+            cudaEventRecord(e0, q);
+            rc = onmf_push_frames(s, V + (size_t)warm * c.beta * c.F, c.F,
+                                  (long long)timed * c.beta, nullptr, 0);
+            cudaEventRecord(e1, q);
+        }
+        if (rc == ONMF_OK) rc = onmf_synchronize(s);
+        onmf_destroy(s);
+        if (rc != ONMF_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        us[h] = 1e3 * ms / timed;
+        if (best < 0 || us[h] < us[best]) best = h;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(V);
+    if (rc != ONMF_OK) return rc;
+    if (best < 0) return ONMF_EINVAL;
+    *hsolve_out = best;
+    if (us_out) memcpy(us_out, us, sizeof us);
+    if (cache_path) {
+        if (FILE *f = fopen(cache_path, "a")) {
+            fprintf(f,
+                    "{\"device\": \"%s\", \"F\": %d, \"K\": %d, \"beta\": %d, \"n_inner\": %d, "
+                    "\"hsolve\": %d, \"us_per_minibatch\": [%.3f, %.3f, %.3f, %.3f]}\n",
+                    key.device.c_str(), key.F, key.K, key.beta, key.n_inner, best, us[0], us[1],
+                    us[2], us[3]);
+            fclose(f);
+        }
+    }
+    return ONMF_OK;
+}
