@@ -9,6 +9,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "onmf.h"
 #include "onmf_cluster.cuh"
 #include "onmf_device.cuh"
@@ -20,6 +22,15 @@ using namespace onmf;
 namespace {
 
 thread_local char g_msg[512] = "";
+
+// NVTX range around a library call (shows in Nsight timelines; no cost
+// without a tool attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 void set_msg(const char *what, cudaError_t e) {
     snprintf(g_msg, sizeof g_msg, "%s: %s", what, cudaGetErrorString(e));
@@ -403,6 +414,7 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
 static onmf_status run_minibatches(onmf_state *s, const float *V, long long ldv, int nmb,
                                    int nb_last, float *H, long long ldh,
                                    const float *H_in = nullptr, long long ldh_in = 0) {
+    Range range_("online step launch");
     if (nmb <= 0) return ONMF_OK;
     const onmf_config &c = s->cfg;
     StepArgs a;
@@ -538,6 +550,7 @@ extern "C" {
 
 onmf_status onmf_push_frames(onmf_state *s, const float *V, int64_t ldv, int64_t n, float *H_out,
                              int64_t ldh) {
+    Range range_("onmf_push_frames");
     if (!s) return ONMF_EINVAL;
     onmf_status st = check_sticky(s);
     if (st != ONMF_OK) return st;
@@ -587,6 +600,7 @@ onmf_status onmf_push_frames(onmf_state *s, const float *V, int64_t ldv, int64_t
 
 onmf_status onmf_push_frames_warm(onmf_state *s, const float *V, int64_t ldv, int64_t n,
                                   const int64_t *order, float *H, int64_t ldh) {
+    Range range_("onmf_push_frames_warm");
     if (!s) return ONMF_EINVAL;
     onmf_status st = check_sticky(s);
     if (st != ONMF_OK) return st;
@@ -645,6 +659,7 @@ onmf_status onmf_push_frames_warm(onmf_state *s, const float *V, int64_t ldv, in
 }
 
 onmf_status onmf_flush(onmf_state *s) {
+    Range range_("onmf_flush");
     if (!s) return ONMF_EINVAL;
     onmf_status st = check_sticky(s);
     if (st != ONMF_OK) return st;
@@ -701,6 +716,7 @@ onmf_status onmf_set_state(onmf_state *s, const float *W, const double *A, const
 
 onmf_status onmf_project(onmf_state *s, const float *V, int64_t ldv, int64_t n, float *H_out,
                          int64_t ldh, int32_t n_inner, double *obj_sum) {
+    Range range_("onmf_project");
     if (!s) return ONMF_EINVAL;
     onmf_status st = check_sticky(s);
     if (st != ONMF_OK) return st;
@@ -800,6 +816,7 @@ onmf_status nmf_batch_init_H(const float *V, int64_t ldv, const float *W, float 
 onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int32_t F, int32_t K,
                            int64_t N, double eps, double h_exponent, int32_t n_iter,
                            int32_t normalize, int32_t precision, double *obj_out, void *stream) {
+    Range range_("nmf_batch_step");
     if (!V || !W || !H || F < 1 || F > 8192 || K < 1 || K > 256 || N < 1 || ldv < F ||
         n_iter < 0 || !(eps >= 0.0) || !(h_exponent > 0.0) ||
         (precision != ONMF_FP32 && precision != ONMF_MIXED))

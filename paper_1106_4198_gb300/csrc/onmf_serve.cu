@@ -27,6 +27,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "onmf.h"
 #include "onmf_launch.h"
 #include "onmf_serve.cuh"
@@ -239,7 +241,16 @@ static void release_stream(onmf_server *sv, int64_t id) {
 }
 
 // Form and launch one batch on a free slot. Returns true if launched.
+static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex> &lk);
+
 static bool launch_batch(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex> &lk) {
+    nvtxRangePushA("serve batch");
+    const bool r = launch_batch_(sv, sl, lk);
+    nvtxRangePop();
+    return r;
+}
+
+static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex> &lk) {
     const int F = sv->cfg.F;
     std::vector<std::pair<int64_t, Chunk>> picked;
     size_t frames = 0;
