@@ -258,8 +258,18 @@ ClusterTiles cluster_tiles(const Shape &s, long long n) {
 
 // Serving kernels: FP32 (one variant) or mixed, one per k16-slab count.
 const void *serve_fn(int prec, int ks) {
-    if (prec == PREC_FP32) return (const void *)serve_kernel<PREC_FP32, 0>;
+    if (prec == PREC_FP32) return (const void *)serve_hsolve_kernel<PREC_FP32, 0>;
     return ks <= 4 ? mixed_serve_lo(ks) : mixed_serve_hi(ks);
+}
+
+// Serving phases 2 and 3 (not specialized by dictionary size).
+const void *serve_stats_fn(int prec) {
+    return prec == PREC_FP32 ? (const void *)serve_stats_kernel<PREC_FP32>
+                             : (const void *)serve_stats_kernel<PREC_MIXED>;
+}
+const void *serve_rescale_fn(int prec) {
+    return prec == PREC_FP32 ? (const void *)serve_rescale_kernel<PREC_FP32>
+                             : (const void *)serve_rescale_kernel<PREC_MIXED>;
 }
 
 static const void *online_fn(int prec, int ks) {
@@ -292,6 +302,7 @@ cudaError_t configure_kernels() {
             fns.push_back(tile_fn(p, ks));
         }
     for (int ks = 1; ks <= 8; ++ks) fns.push_back(serve_fn(PREC_MIXED, ks));
+    for (int p = PREC_FP32; p <= PREC_MIXED; ++p) fns.push_back(serve_stats_fn(p));
     for (int ks = 1; ks <= 16; ++ks) {
         fns.push_back(cluster_online_fn(ks));
         fns.push_back(cluster_tile_fn(ks));

@@ -36,10 +36,10 @@ const void *mixed_tile_hi(int prec, int ks) {
 
 const void *mixed_serve_hi(int ks) {
     switch (ks) {
-    case 5: return (const void *)serve_kernel<PREC_MIXED, 5>;
-    case 6: return (const void *)serve_kernel<PREC_MIXED, 6>;
-    case 7: return (const void *)serve_kernel<PREC_MIXED, 7>;
-    case 8: return (const void *)serve_kernel<PREC_MIXED, 8>;
+    case 5: return (const void *)serve_hsolve_kernel<PREC_MIXED, 5>;
+    case 6: return (const void *)serve_hsolve_kernel<PREC_MIXED, 6>;
+    case 7: return (const void *)serve_hsolve_kernel<PREC_MIXED, 7>;
+    case 8: return (const void *)serve_hsolve_kernel<PREC_MIXED, 8>;
     }
     return nullptr;
 }

@@ -36,10 +36,10 @@ const void *mixed_tile_lo(int prec, int ks) {
 
 const void *mixed_serve_lo(int ks) {
     switch (ks) {
-    case 1: return (const void *)serve_kernel<PREC_MIXED, 1>;
-    case 2: return (const void *)serve_kernel<PREC_MIXED, 2>;
-    case 3: return (const void *)serve_kernel<PREC_MIXED, 3>;
-    case 4: return (const void *)serve_kernel<PREC_MIXED, 4>;
+    case 1: return (const void *)serve_hsolve_kernel<PREC_MIXED, 1>;
+    case 2: return (const void *)serve_hsolve_kernel<PREC_MIXED, 2>;
+    case 3: return (const void *)serve_hsolve_kernel<PREC_MIXED, 3>;
+    case 4: return (const void *)serve_hsolve_kernel<PREC_MIXED, 4>;
     }
     return nullptr;
 }

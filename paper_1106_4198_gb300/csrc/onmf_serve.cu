@@ -1,12 +1,14 @@
 // Serving: many concurrent runs of Algorithm 1 (arXiv:1106.4198), one per
 // stream, fed chunk by chunk; every chunk is one minibatch of its stream.
 //
-// Device side: serve_kernel executes a batch of chunks of different streams,
-// dictionary sizes and lengths in one launch. Each chunk is one CTA doing the
-// whole step at CTA scope (h-solve of its 8-frame tiles, statistics and
-// A/B/W' on (16 x 32) tiles, column rescale), with the same tile functions
-// as the persistent single-stream kernel and a fixed order of operations,
-// so a chunk's result does not depend on the batch it runs in.
+// Device side (onmf_serve.cuh): a batch of chunks of different streams,
+// dictionary sizes and lengths runs as three phases, each one launch over
+// all (chunk, work unit) pairs so even one chunk spreads over the GPU: the
+// h-solve of every 8-frame tile (one launch per dictionary size, on forked
+// streams), the statistics and W' of every (16 x 32) output tile, and the
+// column rescale with the chunk's loss. They use the tile functions of the
+// persistent single-stream kernel in the same order, so a chunk's result
+// does not depend on the batch it runs in.
 //
 // Host side: a worker thread forms batches from the queued chunks of
 // admitted streams that have nothing in flight (oldest chunk first), packs
@@ -129,6 +131,7 @@ struct Slot {
     cudaEvent_t ev_fork = nullptr, ev_join[8] = {};
     bool busy = false;
     ServeItem *d_items = nullptr, *h_items = nullptr;
+    int *d_off = nullptr, *h_off = nullptr;  // work offsets: tiles, units, columns (3 x (n+1))
     float *d_V = nullptr, *h_V = nullptr;
     float *d_H = nullptr, *h_H = nullptr;
     char *d_scratch = nullptr;
@@ -345,20 +348,35 @@ static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex
     }
     const int n = (int)picked.size();
     cudaStream_t q = sl.stream;
+    // work offsets of the three phases: 8-frame tiles, (16 x 32) output
+    // tiles, columns + the loss
+    int *t_off = sl.h_off, *u_off = sl.h_off + (n + 1), *c_off = sl.h_off + 2 * (n + 1);
+    t_off[0] = u_off[0] = c_off[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        const Shape &s = recs[i]->s;
+        t_off[i + 1] = t_off[i] + ceil_div(sl.h_items[i].n, kTile);
+        u_off[i + 1] = u_off[i] + (s.Fp16 / 16) * (s.Kh / 32);
+        c_off[i + 1] = c_off[i] + s.K + 1;
+    }
+    int *dt = sl.d_off, *du = sl.d_off + (n + 1), *dc = sl.d_off + 2 * (n + 1);
     bool ok = soff <= sl.scratch_bytes;
     if (ok) ok = cudaMemsetAsync(sl.d_err, 0, sizeof(int), q) == cudaSuccess;
     if (ok) ok = cudaMemcpyAsync(sl.d_V, sl.h_V, voff * F * 4, cudaMemcpyHostToDevice, q) == cudaSuccess;
     if (ok) ok = cudaMemcpyAsync(sl.d_items, sl.h_items, n * sizeof(ServeItem), cudaMemcpyHostToDevice, q) == cudaSuccess;
+    if (ok) ok = cudaMemcpyAsync(sl.d_off, sl.h_off, 3 * (n + 1) * sizeof(int), cudaMemcpyHostToDevice, q) == cudaSuccess;
     int nlaunch = 0;
+    auto launch = [&](const void *fn, int grid, size_t smem, cudaStream_t st, ServeItem *items,
+                      int *off, int cnt) {
+        void *args[] = {&items, &off, &cnt};
+        ++nlaunch;
+        return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, smem, st) == cudaSuccess;
+    };
+    const int nsm = sv->nsm;
+    // phase 1: the h-solve; on the mixed path one launch per dictionary size
+    // on its own stream (the kernels are specialized by size), then join
     if (ok && sv->prec == PREC_FP32) {
-        ServeItem *items = sl.d_items;
-        int cnt = n;
-        void *args[] = {&items, &cnt};
-        ok = cudaLaunchKernel(serve_fn(PREC_FP32, 0), dim3(n), dim3(kThreads), args, sv->smem,
-                              q) == cudaSuccess;
-        nlaunch = 1;
+        ok = launch(serve_fn(PREC_FP32, 0), std::min(t_off[n], nsm), sv->smem, q, sl.d_items, dt, n);
     } else if (ok) {
-        // fork: one launch per dictionary size on its own stream, then join
         ok = cudaEventRecord(sl.ev_fork, q) == cudaSuccess;
         int i0 = 0;
         while (ok && i0 < n) {
@@ -366,18 +384,19 @@ static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex
             int i1 = i0;
             while (i1 < n && recs[i1]->s.Kp / 16 == ks) ++i1;
             cudaStream_t qs = sl.sub[ks - 1];
-            ServeItem *items = sl.d_items + i0;
-            int cnt = i1 - i0;
-            void *args[] = {&items, &cnt};
             ok = cudaStreamWaitEvent(qs, sl.ev_fork, 0) == cudaSuccess &&
-                 cudaLaunchKernel(serve_fn(PREC_MIXED, ks), dim3(cnt), dim3(kThreads), args,
-                                  sv->smem, qs) == cudaSuccess &&
+                 launch(serve_fn(PREC_MIXED, ks), std::min(t_off[i1] - t_off[i0], nsm), sv->smem,
+                        qs, sl.d_items + i0, dt + i0, i1 - i0) &&
                  cudaEventRecord(sl.ev_join[ks - 1], qs) == cudaSuccess &&
                  cudaStreamWaitEvent(q, sl.ev_join[ks - 1], 0) == cudaSuccess;
-            ++nlaunch;
             i0 = i1;
         }
     }
+    // phases 2 and 3 over every item of the batch
+    if (ok)
+        ok = launch(serve_stats_fn(sv->prec), std::min(u_off[n], nsm),
+                    stats_smem_bytes(sv->prec), q, sl.d_items, du, n);
+    if (ok) ok = launch(serve_rescale_fn(sv->prec), std::min(c_off[n], 4 * nsm), 0, q, sl.d_items, dc, n);
     if (ok) ok = cudaMemcpyAsync(sl.h_loss, sl.d_loss, n * 8, cudaMemcpyDeviceToHost, q) == cudaSuccess;
     if (ok && hoff) ok = cudaMemcpyAsync(sl.h_H, sl.d_H, hoff * 4, cudaMemcpyDeviceToHost, q) == cudaSuccess;
     if (ok) ok = cudaMemcpyAsync(sl.h_err, sl.d_err, 4, cudaMemcpyDeviceToHost, q) == cudaSuccess;
@@ -454,10 +473,10 @@ static void worker_main(onmf_server *sv) {
 static void free_server(onmf_server *sv) {
     for (auto &sl : sv->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
-        void *dev[] = {sl.d_items, sl.d_V, sl.d_H, sl.d_scratch, sl.d_loss, sl.d_err};
+        void *dev[] = {sl.d_items, sl.d_off, sl.d_V, sl.d_H, sl.d_scratch, sl.d_loss, sl.d_err};
         for (void *p : dev)
             if (p) cudaFree(p);
-        void *host[] = {sl.h_items, sl.h_V, sl.h_H, sl.h_loss, sl.h_err};
+        void *host[] = {sl.h_items, sl.h_off, sl.h_V, sl.h_H, sl.h_loss, sl.h_err};
         for (void *p : host)
             if (p) cudaFreeHost(p);
         if (sl.ev) cudaEventDestroy(sl.ev);
@@ -515,6 +534,8 @@ onmf_status onmf_server_create(const onmf_server_config *cfg, onmf_server **out)
             cudaEventCreateWithFlags(&sl.ev_fork, cudaEventDisableTiming) == cudaSuccess &&
             cudaMalloc((void **)&sl.d_items, c.max_batch * sizeof(ServeItem)) == cudaSuccess &&
             cudaHostAlloc((void **)&sl.h_items, c.max_batch * sizeof(ServeItem), 0) == cudaSuccess &&
+            cudaMalloc((void **)&sl.d_off, 3 * (c.max_batch + 1) * sizeof(int)) == cudaSuccess &&
+            cudaHostAlloc((void **)&sl.h_off, 3 * (c.max_batch + 1) * sizeof(int), 0) == cudaSuccess &&
             cudaMalloc((void **)&sl.d_V, sv->cap_frames * c.F * 4) == cudaSuccess &&
             cudaHostAlloc((void **)&sl.h_V, sv->cap_frames * c.F * 4, 0) == cudaSuccess &&
             cudaMalloc((void **)&sl.d_H, sv->cap_frames * 128 * 4) == cudaSuccess &&

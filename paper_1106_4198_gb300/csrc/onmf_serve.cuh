@@ -1,9 +1,6 @@
-// Device side of serving (see onmf_serve.cu): one CTA runs the whole
-// Algorithm 1 step (arXiv:1106.4198) of one chunk of one stream at CTA
-// scope: the h-solve of its 8-frame tiles, statistics and A/B/W' on
-// (16 x 32) tiles, and the column rescale, with the same tile functions as
-// the persistent single-stream kernel and a fixed order of operations, so a
-// chunk's result does not depend on the batch it runs in.
+// Device side of serving (see onmf_serve.cu): the Algorithm 1 step
+// (arXiv:1106.4198) of a batch of chunks of different streams, one
+// minibatch per chunk, in three launches (below).
 #pragma once
 
 #include "onmf_step.cuh"
@@ -29,22 +26,59 @@ struct ServeItem {
     int *err;
 };
 
-template <int PREC, int KS>
-static __device__ __forceinline__ void run_item_(const ServeItem *__restrict__ ip, unsigned char *smem, uint64_t *mbar,
-                                unsigned &wpar, unsigned &vpar, float *s_tmp, float *s_red8,
-                                double *s_red, float *acc) {
-    // fields are read from the work list (global memory) where they are used,
-    // rather than copied into registers for the whole item
-    const ServeItem &it = *ip;
-    const Shape s = it.s;
-    const int ntiles = ceil_div(it.n, kTile);
-    const float sw = sum_w(it.swpart, s.K, s_tmp);
-    WStage ws{&mbar[0], &wpar, false};
-    if (PREC == PREC_MIXED) {
-        issue_wimg(s, it.Wimg, smem, &mbar[0]);
-        ws.pending = true;
+// Serving runs a batch of chunks (one minibatch each, of streams with
+// different dictionaries and lengths) as three launches, so the work of
+// even a single chunk spreads over the GPU: the h-solve of every (chunk,
+// 8-frame tile) pair, the statistics of every (chunk, 16x32 output tile)
+// pair, and the rescale of every (chunk, column) pair; the kernel boundaries
+// separate the phases. The tile, statistics and rescale functions are those
+// of the persistent single-stream kernel, so a chunk's result does not
+// depend on the batch it runs in. off[i] is the first work pair of item i
+// and off[n] one past the last (a launch over items i0.. passes off + i0);
+// pairs are taken in grid-stride order.
+
+// Item owning work pair p: the largest i with off[i] <= p.
+__device__ __forceinline__ int serve_item_of(const int *off, int n, int p) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= p)
+            lo = mid;
+        else
+            hi = mid - 1;
     }
-    for (int tile = 0; tile < ntiles; ++tile) {
+    return lo;
+}
+
+// Phase 1: h-solve of (chunk, tile) pairs; every item of the launch has
+// Kp = 16*KS (KS = 0 on the FP32 path, which is not specialized).
+template <int PREC, int KS>
+__global__ void __launch_bounds__(kThreads, 1) serve_hsolve_kernel(const ServeItem *items,
+                                                                  const int *off, int nitems) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ float s_tmp;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned wpar = 0, vpar = 0;
+    WStage ws{&mbar[0], &wpar, false};
+    int staged = -1;  // item whose W^T image is in shared memory
+    const int base = off[0], total = off[nitems] - base;
+    for (int p = blockIdx.x; p < total; p += gridDim.x) {
+        const int i = serve_item_of(off, nitems, base + p);
+        const ServeItem &it = items[i];
+        const Shape s = it.s;
+        const int tile = base + p - off[i];
+        const float sw = sum_w(it.swpart, s.K, &s_tmp);
+        if (PREC == PREC_MIXED && i != staged) {
+            issue_wimg(s, it.Wimg, smem, &mbar[0]);
+            ws.pending = true;
+            staged = i;
+        }
         TileJob t;
         t.Vt = it.V + (long long)tile * kTile * s.F;
         t.ldv = s.F;
@@ -65,48 +99,53 @@ static __device__ __forceinline__ void run_item_(const ServeItem *__restrict__ i
         hsolve_tile<PREC, KS>(s, it.eps, it.gamma, it.Wcm, it.Wrm, sw, t, smem, ws, &mbar[1], vpar,
                               it.err);
     }
-    __threadfence();
-    __syncthreads();
-    const int FT = s.Fp16 / 16, KT = s.Kh / 32;
-    for (int u = 0; u < FT * KT; ++u) {
+}
+
+// Phase 2: statistics, A, B and W' = sqrt(A/B) of (chunk, output tile) pairs.
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1) serve_stats_kernel(const ServeItem *items,
+                                                                 const int *off, int nitems) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *acc = reinterpret_cast<float *>(smem + stats_smem_bytes(PREC) - 2 * 16 * 32 * 4);
+    const int base = off[0], total = off[nitems] - base;
+    for (int p = blockIdx.x; p < total; p += gridDim.x) {
+        const int i = serve_item_of(off, nitems, base + p);
+        const ServeItem &it = items[i];
+        const Shape s = it.s;
+        const int FT = s.Fp16 / 16, u = base + p - off[i];
         const int mt = u % FT, ks = u / FT;
         stats_unit<PREC>(s, mt, ks, it.Pg, it.Qg, it.Hg, it.betap, 0, it.n, smem, acc);
         epilogue_unit(s, it.Wcm, it.A, it.B, it.Wn, it.rho, it.rho_on_new, mt, ks, acc);
         __syncthreads();
     }
-    __threadfence();
-    __syncthreads();
-    normalize_columns<PREC>(s, it.normalize, it.Wn, it.Wcm, it.Wrm, it.Wimg, nullptr, it.A, it.B,
-                            it.swpart, it.err, s_red8, 0, 1);
-    const double l = block_sum_ordered(it.loss_part, ntiles, s_red);
-    if (threadIdx.x == 0) {
-        *it.chunk_loss = l;
-        *it.loss_sum += l;
-    }
-    if (PREC != PREC_FP32) asm volatile("fence.proxy.async.global;\n" ::: "memory");
-    __threadfence();
-    __syncthreads();
 }
 
-// One launch per dictionary size: every item of the launch has Kp = 16*KS
-// (KS = 0 on the FP32 path, which is not specialized).
-template <int PREC, int KS>
-__global__ void __launch_bounds__(kThreads, 1) serve_kernel(const ServeItem *items, int nitems) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ float s_tmp;
+// Phase 3: the rescale of (chunk, column) pairs; pair K of an item (one
+// past its last column) adds the chunk's loss.
+template <int PREC>
+__global__ void __launch_bounds__(kThreads) serve_rescale_kernel(const ServeItem *items,
+                                                                const int *off, int nitems) {
     __shared__ float s_red8[kWarps];
     __shared__ double s_red[kThreads];
-    if (threadIdx.x == 0) {
-        mbar_init(&mbar[0], 1);
-        mbar_init(&mbar[1], 1);
-        fence_mbar_init();
+    const int base = off[0], total = off[nitems] - base;
+    for (int p = blockIdx.x; p < total; p += gridDim.x) {
+        const int i = serve_item_of(off, nitems, base + p);
+        const ServeItem &it = items[i];
+        const Shape s = it.s;
+        const int k = base + p - off[i];
+        if (k < s.K) {
+            normalize_columns<PREC>(s, it.normalize, it.Wn, it.Wcm, it.Wrm, it.Wimg, nullptr,
+                                    it.A, it.B, it.swpart, it.err, s_red8, k, s.K);
+        } else {
+            const double l = block_sum_ordered(it.loss_part, ceil_div(it.n, kTile), s_red);
+            if (threadIdx.x == 0) {
+                *it.chunk_loss = l;
+                *it.loss_sum += l;
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    unsigned wpar = 0, vpar = 0;
-    float *acc = reinterpret_cast<float *>(smem + stats_smem_bytes(PREC) - 2 * 16 * 32 * 4);
-    for (int i = blockIdx.x; i < nitems; i += gridDim.x)
-        run_item_<PREC, KS>(items + i, smem, mbar, wpar, vpar, &s_tmp, s_red8, s_red, acc);
+    if (PREC != PREC_FP32) asm volatile("fence.proxy.async.global;\n" ::: "memory");
 }
 
 }  // namespace onmf

@@ -34,13 +34,19 @@ def errors(g, o):
 
 @pytest.mark.parametrize("K", [64, 100, 256])
 @pytest.mark.parametrize("beta", [512, 2048])
-def test_sweep_setting_one_minibatch(K, beta):
+@pytest.mark.parametrize("hsolve", ["cluster", "mma", "tc"])
+def test_sweep_setting_one_minibatch(K, beta, hsolve, monkeypatch):
+    """The K x beta sweep at F = 513 on every h-solve kernel that takes the
+    shape (mma and tcgen05 stop at K = 128)."""
+    if hsolve != "cluster" and K > 128:
+        pytest.skip("%s h-solve takes K <= 128" % hsolve)
+    monkeypatch.setenv("ONMF_HSOLVE", hsolve)
     F, n_in = 513, 10
     V, W0 = problem(F, K, beta, seed=31)
     g = run_gpu(V, W0, beta=beta, n_inner=n_in, precision=MIXED)
     o = run_oracle(V, W0, beta, n_in)
     e = errors(g, o)
-    print("F=%d K=%d beta=%d cluster:" % (F, K, beta), {k: "%.2e" % v for k, v in e.items()})
+    print("F=%d K=%d beta=%d %s:" % (F, K, beta, hsolve), {k: "%.2e" % v for k, v in e.items()})
     assert e["loss"] <= 1e-3
     for k in ("W", "A", "B", "H"):
         assert e[k] <= 1e-2, (k, e)
