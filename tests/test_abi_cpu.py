@@ -86,3 +86,18 @@ def test_null_arguments_rejected():
     # an unknown wait kind is refused before any device work
     assert L.onmf_selftest_wait(7, None, None) == 1
     assert L.onmf_selftest_wait(-1, None, None) == 1
+
+
+def test_c_client_compiles_against_the_header():
+    """The C ABI is plain C99: a C client builds against include/onmf.h
+    with every warning an error (it runs in tests/test_gpu_c_client.py)."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(root, "include"),
+                        os.path.join(root, "tests", "c", "onmf_c_smoke.c")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
