@@ -310,7 +310,6 @@ static __device__ void hsolve_tile_fp32(const Shape &s, float eps, float gamma, 
 // ----------------------------------------------------------------- MIXED
 
 constexpr int kMtMax = 5;    // m16 row tiles of x = eps + W h per warp per pass
-constexpr int kFtCache = 0;  // f16 steps of W^T kept in registers (0: read from shared memory)
 
 struct MixedLayout {
     size_t w, pq, h, yraw, yt, misc, total;  // byte offsets
@@ -411,11 +410,6 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
                 y_raw[i] = __ldg(t.Vt + (long long)j * t.ldv + f);
             }
         }
-        if (ws.pending) {
-            mbar_wait_bounded(ws.bar, *ws.parity, err);
-            *ws.parity ^= 1u;
-            ws.pending = false;
-        }
         if (bulk) {
             mbar_wait_bounded(vbar, vparity, err);
             vparity ^= 1u;
@@ -463,19 +457,14 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
         *reinterpret_cast<uint32_t *>(H_s + g * HLD + 16 * warp + 8 + 2 * tq) =
             pack_bf16(hr[2], hr[3]);
     }
-    __syncthreads();
-
-    // step B can keep W^T's fragments in registers for the whole tile
-    // (kFtCache f16 steps); at 256 threads that costs more in register
-    // pressure than it saves in shared-memory traffic, so it is off
-    const bool wcached = kFtCache > 0 && FT <= kFtCache;
-    uint32_t wb[kFtCache > 0 ? kFtCache : 1][4];
-    if (hown && wcached) {
-        const __nv_bfloat16 *brow = W_s + (16 * warp + r8 + 8 * (mi >> 1)) * WLD + 8 * (mi & 1);
-#pragma unroll
-        for (int fs = 0; fs < kFtCache; ++fs)
-            if (fs < FT) ldmatrix_x4(wb[fs], brow + 16 * fs);
+    // W^T is first read by step A: its bulk copy (issued before the frame
+    // tile) overlaps the frame sums and the start point above
+    if (ws.pending) {
+        mbar_wait_bounded(ws.bar, *ws.parity, err);
+        *ws.parity ^= 1u;
+        ws.pending = false;
     }
+    __syncthreads();
 
     float lacc = 0.f;
     for (int it = 0;; ++it) {
@@ -556,38 +545,21 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
 #pragma unroll
                 for (int e = 0; e < 4; ++e) c0[u][e] = c1[u][e] = 0.f;
             const __nv_bfloat16 *arow = PQ_s + (r8 + 8 * (mi & 1)) * WLD + 8 * (mi >> 1);
-            if (wcached) {
+            const __nv_bfloat16 *brow = W_s + (16 * warp + r8 + 8 * (mi >> 1)) * WLD + 8 * (mi & 1);
+            for (int fs = 0; fs < FT; fs += 4) {
+                uint32_t a[4][4], b[4][4];
 #pragma unroll
-                for (int fs = 0; fs < kFtCache; fs += 4) {
-                    uint32_t a[4][4];
+                for (int u = 0; u < 4; ++u)
+                    if (fs + u < FT) {
+                        ldmatrix_x4(a[u], arow + 16 * (fs + u));
+                        ldmatrix_x4(b[u], brow + 16 * (fs + u));
+                    }
 #pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (fs + u < kFtCache && fs + u < FT) ldmatrix_x4(a[u], arow + 16 * (fs + u));
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (fs + u < kFtCache && fs + u < FT) {
-                            mma_bf16_16816(c0[u], a[u], wb[fs + u][0], wb[fs + u][1]);
-                            mma_bf16_16816(c1[u], a[u], wb[fs + u][2], wb[fs + u][3]);
-                        }
-                }
-            } else {
-                const __nv_bfloat16 *brow =
-                    W_s + (16 * warp + r8 + 8 * (mi >> 1)) * WLD + 8 * (mi & 1);
-                for (int fs = 0; fs < FT; fs += 4) {
-                    uint32_t a[4][4], b[4][4];
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (fs + u < FT) {
-                            ldmatrix_x4(a[u], arow + 16 * (fs + u));
-                            ldmatrix_x4(b[u], brow + 16 * (fs + u));
-                        }
-#pragma unroll
-                    for (int u = 0; u < 4; ++u)
-                        if (fs + u < FT) {
-                            mma_bf16_16816(c0[u], a[u], b[u][0], b[u][1]);
-                            mma_bf16_16816(c1[u], a[u], b[u][2], b[u][3]);
-                        }
-                }
+                for (int u = 0; u < 4; ++u)
+                    if (fs + u < FT) {
+                        mma_bf16_16816(c0[u], a[u], b[u][0], b[u][1]);
+                        mma_bf16_16816(c1[u], a[u], b[u][2], b[u][3]);
+                    }
             }
             float n0[4], n1[4];
 #pragma unroll
