@@ -42,6 +42,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--frames-per-step", type=int, default=1_000_000)
+    p.add_argument("--hsolve", default="auto", choices=["auto", "mma", "tc", "cluster"],
+                   help="h-solve kernel of the mixed path; auto: the autotuner's choice")
     p.add_argument("--skip-fp32", action="store_true")
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-cpu", action="store_true")
@@ -203,10 +205,15 @@ def run_ours(args):
               for c in range(args.steps)]
     torch.cuda.synchronize()
 
-    # the mixed path runs the h-solve kernel the autotuner measures fastest
+    # the mixed path runs the h-solve kernel the autotuner measures fastest,
+    # unless --hsolve names one
     tune_cfg = onmf.onmf_config_default(F, K, precision=onmf.ONMF_MIXED, beta=BETA,
                                         n_inner=N_IN)
-    hsolve, tune_us, _ = onmf.onmf_autotune(tune_cfg, stream=stream)
+    if args.hsolve == "auto":
+        hsolve, tune_us, _ = onmf.onmf_autotune(tune_cfg, stream=stream)
+    else:
+        hsolve = [k for k, v in onmf.HSOLVE_NAMES.items() if v == args.hsolve][0]
+        tune_us = None
     hname = onmf.HSOLVE_NAMES[hsolve]
 
     def timed_pass(precision, record_launch_times=False):

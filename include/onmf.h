@@ -351,7 +351,11 @@ onmf_status onmf_selftest_wait(int32_t which, void *stream, int64_t *elapsed_ns)
  *   us_out: NULL or 4 doubles, microseconds per minibatch indexed by
  *       ONMF_HSOLVE_* (-1 for kernels not timed).
  * On the FP32 path it returns AUTO without timing. Blocks until done.
- * Errors: EINVAL (no kernel fits the shape), ENOMEM, ECUDA. */
+ * A kernel whose run ends with an error that leaves the CUDA context usable
+ * (a device wait that timed out, a launch its entry check refused) is left
+ * out of the choice, its time -1; a context error ends the call.
+ * Errors: EINVAL (no kernel fits the shape), ENOMEM, ECUDA, ETIMEOUT (every
+ * kernel that fits failed: the status of the last one). */
 onmf_status onmf_autotune(const onmf_config *cfg, void *stream, const char *cache_path,
                           int32_t *hsolve_out, double *us_out, int32_t *from_cache);
 

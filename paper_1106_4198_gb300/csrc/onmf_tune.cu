@@ -106,7 +106,7 @@ extern "C" onmf_status onmf_autotune(const onmf_config *cfg, void *stream, const
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int best = -1;
-    onmf_status rc = ONMF_OK;
+    onmf_status rc = ONMF_OK, dropped = ONMF_OK;
     for (int h = ONMF_HSOLVE_MMA; h <= ONMF_HSOLVE_CLUSTER && rc == ONMF_OK; ++h) {
         onmf_config c = *cfg;
         c.hsolve = h;
@@ -122,7 +122,17 @@ extern "C" onmf_status onmf_autotune(const onmf_config *cfg, void *stream, const
         }
         if (rc == ONMF_OK) rc = onmf_synchronize(s);
         onmf_destroy(s);
-        if (rc != ONMF_OK) break;
+        if (rc != ONMF_OK) {
+            // A kernel that reported an error through its status word (a
+            // wait that timed out, a launch shape its entry check refused)
+            // leaves the context usable: drop that candidate and go on. A
+            // CUDA error that the context keeps ends the tuning.
+            if (cudaStreamSynchronize(q) != cudaSuccess || cudaPeekAtLastError() != cudaSuccess)
+                break;
+            dropped = rc;
+            rc = ONMF_OK;
+            continue;
+        }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
         us[h] = 1e3 * ms / timed;
@@ -132,7 +142,7 @@ extern "C" onmf_status onmf_autotune(const onmf_config *cfg, void *stream, const
     cudaEventDestroy(e1);
     cudaFree(V);
     if (rc != ONMF_OK) return rc;
-    if (best < 0) return ONMF_EINVAL;
+    if (best < 0) return dropped != ONMF_OK ? dropped : ONMF_EINVAL;
     *hsolve_out = best;
     if (us_out) memcpy(us_out, us, sizeof us);
     if (cache_path) {
