@@ -54,6 +54,8 @@ def parse():
                    help="skip the forgetting-factor / init / warm-restart study")
     p.add_argument("--serve-seconds", type=float, default=30.0,
                    help="wall window of the serving replay (0 skips serving)")
+    p.add_argument("--serve-direct-seconds", type=float, default=10.0,
+                   help="window of a second replay with direct launches (0 skips it)")
     p.add_argument("--serve-streams", type=int, default=256)
     p.add_argument("--serve-budget", type=int, default=1 << 30)
     return p.parse_args()
@@ -354,14 +356,17 @@ def serving_schedule(n_streams, window_s, rng):
     return streams, events
 
 
-def run_serving(args, precision):
+def run_serving(args, precision, launch=0, window_s=None):
+    """launch: 0 = each batch one captured CUDA graph, 1 = direct launches."""
     import paper_1106_4198_gb300 as onmf
     import synth
+    window_s = window_s or args.serve_seconds
     rng = np.random.default_rng(4321)
-    Ks, events = serving_schedule(args.serve_streams, args.serve_seconds, rng)
+    Ks, events = serving_schedule(args.serve_streams, window_s, rng)
     pool = synth.spectrogram(F, 64, 65536, seed=synth.DATA_SEED + 17)  # gamma-model frames
     srv = onmf.onmf_server_create(F, max_chunk=512, max_batch=256, slots=2,
-                                  budget_bytes=args.serve_budget, precision=precision)
+                                  budget_bytes=args.serve_budget, precision=precision,
+                                  launch=launch)
     lat, frames_done = [], 0
     try:
         ids = []
@@ -411,10 +416,11 @@ def run_serving(args, precision):
     finally:
         onmf.onmf_server_destroy(srv)
     lat_ms = np.array(lat) * 1e3
-    offered = sum(n for _, _, n in events) / args.serve_seconds
+    offered = sum(n for _, _, n in events) / window_s
     return {
         "workload": "%d streams, K in {16,32,64,128}, F=513, chunks 8-512 frames, "
-                    "Poisson arrivals at 4x real time, %.0f s replay" % (len(Ks), args.serve_seconds),
+                    "Poisson arrivals at 4x real time, %.0f s replay" % (len(Ks), window_s),
+        "launch": "cuda graph per batch" if launch == 0 else "direct kernel launches",
         "chunks": len(events), "frames": int(frames_done),
         "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat) else None,
         "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat) else None,
@@ -698,6 +704,12 @@ def main():
         if args.serve_seconds > 0 and world == 1:
             import paper_1106_4198_gb300 as onmf
             out["serving"] = run_serving(args, onmf.ONMF_MIXED)
+            if args.serve_direct_seconds > 0:
+                d = run_serving(args, onmf.ONMF_MIXED, launch=onmf.ONMF_SERVE_DIRECT,
+                                window_s=args.serve_direct_seconds)
+                out["serving"]["direct_launch"] = {
+                    k: d[k] for k in ("workload", "p50_ms", "p99_ms", "max_ms",
+                                      "saturation_frames_per_s", "launches")}
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define ONMF_ABI_VERSION 2
+#define ONMF_ABI_VERSION 3
 
 typedef struct onmf_state onmf_state;
 
@@ -244,13 +244,25 @@ void onmf_destroy(onmf_state *s);
  * fed chunk by chunk. Every chunk is one minibatch of that stream (beta' =
  * chunk length, rho = r^(beta'/n_ref)): h-solve with the stream's W, then
  * the statistics and the dictionary step. A worker thread batches the
- * queued chunks of all admitted streams that have no chunk on the GPU into
- * one kernel launch (continuous batching: chunks that arrive while a batch
- * runs join the next one, and up to `slots` batches are in flight on
- * separate CUDA streams). A chunk is computed by one CTA with a fixed order
- * of operations, so its result does not depend on what it is batched with.
- * Streams are admitted by a device-memory budget: a stream whose state does
- * not fit waits (its chunks queue) until closed streams free memory. */
+ * queued chunks of all admitted streams that have no chunk on the GPU
+ * (continuous batching: chunks that arrive while a batch runs join the next
+ * one, and up to `slots` batches are in flight on separate CUDA streams).
+ * A batch runs as three phases over all its (chunk, work unit) pairs: the
+ * h-solve of every 8-frame tile (one kernel per dictionary size), the
+ * statistics of every output tile, the rescale of every column. By default
+ * the phases of a batch are one CUDA graph launch: the graph is captured
+ * once per slot and set of dictionary sizes present, and reads the batch's
+ * layout from device memory, so a batch needs no capture or update. Every
+ * work unit is computed in a fixed order of operations, so a chunk's result
+ * does not depend on what it is batched with. Streams are admitted by a
+ * device-memory budget: a stream whose state does not fit waits (its chunks
+ * queue) until closed streams free memory. */
+
+/* How a serving batch is launched (onmf_server_config.launch). */
+typedef enum {
+    ONMF_SERVE_GRAPH = 0,  /* replay a captured CUDA graph (default)        */
+    ONMF_SERVE_DIRECT = 1  /* launch the phase kernels one by one           */
+} onmf_serve_launch;
 
 typedef struct onmf_server onmf_server;
 
@@ -261,7 +273,7 @@ typedef struct {
     int32_t slots;          /* batches in flight (1..4)                      */
     int64_t budget_bytes;   /* device memory for stream states               */
     int32_t precision;      /* onmf_precision for all streams                */
-    int32_t reserved;       /* must be 0                                     */
+    int32_t launch;         /* onmf_serve_launch                             */
 } onmf_server_config;
 
 typedef struct {

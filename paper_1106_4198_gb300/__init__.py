@@ -31,6 +31,7 @@ ONMF_MIXED = 1
 # h-solve kernels of the mixed path (onmf_config.hsolve)
 ONMF_HSOLVE_AUTO, ONMF_HSOLVE_MMA, ONMF_HSOLVE_TC, ONMF_HSOLVE_CLUSTER = 0, 1, 2, 3
 HSOLVE_NAMES = {0: "auto", 1: "mma", 2: "tc", 3: "cluster"}
+ONMF_SERVE_GRAPH, ONMF_SERVE_DIRECT = 0, 1
 ONMF_ETIMEOUT = 6
 
 # Every symbol include/onmf.h declares.
@@ -63,7 +64,7 @@ class onmf_server_config(ctypes.Structure):
         ("F", ctypes.c_int32), ("max_chunk", ctypes.c_int32),
         ("max_batch", ctypes.c_int32), ("slots", ctypes.c_int32),
         ("budget_bytes", ctypes.c_int64), ("precision", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("launch", ctypes.c_int32),
     ]
 
 
@@ -438,9 +439,11 @@ class OnlineISNMF:
 
 
 def onmf_server_create(F, max_chunk=512, max_batch=256, slots=2,
-                       budget_bytes=1 << 30, precision=ONMF_MIXED):
+                       budget_bytes=1 << 30, precision=ONMF_MIXED, launch=0):
+    """launch: ONMF_SERVE_GRAPH (0, a captured CUDA graph per batch) or
+    ONMF_SERVE_DIRECT (1, the phase kernels one by one)."""
     c = onmf_server_config(F, max_chunk, max_batch, slots, budget_bytes,
-                           precision, 0)
+                           precision, launch)
     h = _vp()
     _check(lib().onmf_server_create(ctypes.byref(c), ctypes.byref(h)),
            "onmf_server_create")

@@ -12,8 +12,12 @@
 //
 // Host side: a worker thread forms batches from the queued chunks of
 // admitted streams that have nothing in flight (oldest chunk first), packs
-// their frames into a pinned staging buffer, launches on one of `slots`
-// CUDA streams and records an event; completed batches are turned into
+// their frames into a pinned staging buffer, copies them and a header of
+// the batch's layout to the device and launches the three phases on one of
+// `slots` CUDA streams, by default as one CUDA graph captured once per slot
+// and set of dictionary sizes (the kernels read the layout from the header,
+// so the graph serves every such batch unchanged); it records an event, and
+// completed batches are turned into
 // completion records with submit/done timestamps. Stream states live in a
 // device pool of budget_bytes reserved at creation (first-fit free list);
 // a stream that does not fit waits in FIFO order until others close.
@@ -131,7 +135,13 @@ struct Slot {
     cudaEvent_t ev_fork = nullptr, ev_join[8] = {};
     bool busy = false;
     ServeItem *d_items = nullptr, *h_items = nullptr;
-    int *d_off = nullptr, *h_off = nullptr;  // work offsets: tiles, units, columns (3 x (n+1))
+    // batch header (hdr_ints(max_batch) ints, fixed layout): the work
+    // offsets of the three phases (tiles, units, columns; max_batch + 1
+    // each), then item ranges: [0, n) and one per k16-slab count 1..8
+    int *d_off = nullptr, *h_off = nullptr;
+    // captured phase graphs by the set of k16-slab counts present (bit ks-1;
+    // 0 on the FP32 path), with the number of kernels in each
+    std::map<unsigned, std::pair<cudaGraphExec_t, int>> graphs;
     float *d_V = nullptr, *h_V = nullptr;
     float *d_H = nullptr, *h_H = nullptr;
     char *d_scratch = nullptr;
@@ -246,6 +256,78 @@ static void release_stream(onmf_server *sv, int64_t id) {
 // Form and launch one batch on a free slot. Returns true if launched.
 static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex> &lk);
 
+static int hdr_ints(int max_batch) { return 3 * (max_batch + 1) + 2 * 9; }
+
+// The phases of one batch on the slot's stream, reading the batch's layout
+// from the header in device memory. work[0..8] are the tiles per k16-slab
+// count (work[0]: the FP32 path), work[9] the statistics units, work[10]
+// the columns. `fixed` gives every launch its largest grid (grid-stride
+// loops take any work size), as a captured graph that serves every batch
+// with the same set `mask` of slab counts needs; otherwise each grid is cut
+// to its work.
+static bool enqueue_phases(onmf_server *sv, Slot &sl, unsigned mask, const int *work, bool fixed,
+                           int &nlaunch) {
+    cudaStream_t q = sl.stream;
+    const int nsm = sv->nsm, M1 = sv->cfg.max_batch + 1;
+    const int *dt = sl.d_off, *du = dt + M1, *dc = du + M1, *dr = dc + M1;
+    auto grid = [&](int w, int cap) { return fixed ? cap : std::min(w, cap); };
+    auto launch = [&](const void *fn, int g, size_t smem, cudaStream_t st, const int *off,
+                      const int *range) {
+        const ServeItem *items = sl.d_items;
+        void *args[] = {&items, &off, &range};
+        ++nlaunch;
+        return cudaLaunchKernel(fn, dim3(g), dim3(kThreads), args, smem, st) == cudaSuccess;
+    };
+    bool ok = cudaMemsetAsync(sl.d_err, 0, sizeof(int), q) == cudaSuccess;
+    // phase 1: the h-solve; on the mixed path one launch per dictionary size
+    // on its own stream (the kernels are specialized by size), then join
+    if (ok && sv->prec == PREC_FP32) {
+        ok = launch(serve_fn(PREC_FP32, 0), grid(work[0], nsm), sv->smem, q, dt, dr);
+    } else if (ok) {
+        ok = cudaEventRecord(sl.ev_fork, q) == cudaSuccess;
+        for (int ks = 1; ok && ks <= 8; ++ks) {
+            if (!((mask >> (ks - 1)) & 1u)) continue;
+            cudaStream_t qs = sl.sub[ks - 1];
+            ok = cudaStreamWaitEvent(qs, sl.ev_fork, 0) == cudaSuccess &&
+                 launch(serve_fn(PREC_MIXED, ks), grid(work[ks], nsm), sv->smem, qs, dt,
+                        dr + 2 * ks) &&
+                 cudaEventRecord(sl.ev_join[ks - 1], qs) == cudaSuccess &&
+                 cudaStreamWaitEvent(q, sl.ev_join[ks - 1], 0) == cudaSuccess;
+        }
+    }
+    // phases 2 and 3 over every item of the batch
+    if (ok)
+        ok = launch(serve_stats_fn(sv->prec), grid(work[9], nsm), stats_smem_bytes(sv->prec), q,
+                    du, dr);
+    if (ok) ok = launch(serve_rescale_fn(sv->prec), grid(work[10], 4 * nsm), 0, q, dc, dr);
+    return ok;
+}
+
+// Launches the phases as the slot's graph for `mask`, capturing and
+// instantiating it on first use.
+static bool launch_graph(onmf_server *sv, Slot &sl, unsigned mask, int &nlaunch) {
+    auto it = sl.graphs.find(mask);
+    if (it == sl.graphs.end()) {
+        cudaStream_t q = sl.stream;
+        int kernels = 0;
+        if (cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+        const int none[11] = {};
+        const bool queued = enqueue_phases(sv, sl, mask, none, true, kernels);
+        cudaGraph_t g = nullptr;
+        const bool ended = cudaStreamEndCapture(q, &g) == cudaSuccess;
+        cudaGraphExec_t ex = nullptr;
+        const bool ok = queued && ended && g && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        if (!ok) {
+            cudaGetLastError();
+            return false;
+        }
+        it = sl.graphs.emplace(mask, std::make_pair(ex, kernels)).first;
+    }
+    nlaunch += it->second.second;
+    return cudaGraphLaunch(it->second.first, sl.stream) == cudaSuccess;
+}
+
 static bool launch_batch(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex> &lk) {
     nvtxRangePushA("serve batch");
     const bool r = launch_batch_(sv, sl, lk);
@@ -348,9 +430,10 @@ static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex
     }
     const int n = (int)picked.size();
     cudaStream_t q = sl.stream;
-    // work offsets of the three phases: 8-frame tiles, (16 x 32) output
-    // tiles, columns + the loss
-    int *t_off = sl.h_off, *u_off = sl.h_off + (n + 1), *c_off = sl.h_off + 2 * (n + 1);
+    // the batch header: work offsets of the three phases (8-frame tiles,
+    // (16 x 32) output tiles, columns + the loss) and the item ranges
+    const int M1 = sv->cfg.max_batch + 1;
+    int *t_off = sl.h_off, *u_off = t_off + M1, *c_off = u_off + M1, *rng = c_off + M1;
     t_off[0] = u_off[0] = c_off[0] = 0;
     for (int i = 0; i < n; ++i) {
         const Shape &s = recs[i]->s;
@@ -358,45 +441,35 @@ static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex
         u_off[i + 1] = u_off[i] + (s.Fp16 / 16) * (s.Kh / 32);
         c_off[i + 1] = c_off[i] + s.K + 1;
     }
-    int *dt = sl.d_off, *du = sl.d_off + (n + 1), *dc = sl.d_off + 2 * (n + 1);
-    bool ok = soff <= sl.scratch_bytes;
-    if (ok) ok = cudaMemsetAsync(sl.d_err, 0, sizeof(int), q) == cudaSuccess;
-    if (ok) ok = cudaMemcpyAsync(sl.d_V, sl.h_V, voff * F * 4, cudaMemcpyHostToDevice, q) == cudaSuccess;
-    if (ok) ok = cudaMemcpyAsync(sl.d_items, sl.h_items, n * sizeof(ServeItem), cudaMemcpyHostToDevice, q) == cudaSuccess;
-    if (ok) ok = cudaMemcpyAsync(sl.d_off, sl.h_off, 3 * (n + 1) * sizeof(int), cudaMemcpyHostToDevice, q) == cudaSuccess;
-    int nlaunch = 0;
-    auto launch = [&](const void *fn, int grid, size_t smem, cudaStream_t st, ServeItem *items,
-                      int *off, int cnt) {
-        void *args[] = {&items, &off, &cnt};
-        ++nlaunch;
-        return cudaLaunchKernel(fn, dim3(grid), dim3(kThreads), args, smem, st) == cudaSuccess;
-    };
-    const int nsm = sv->nsm;
-    // phase 1: the h-solve; on the mixed path one launch per dictionary size
-    // on its own stream (the kernels are specialized by size), then join
-    if (ok && sv->prec == PREC_FP32) {
-        ok = launch(serve_fn(PREC_FP32, 0), std::min(t_off[n], nsm), sv->smem, q, sl.d_items, dt, n);
-    } else if (ok) {
-        ok = cudaEventRecord(sl.ev_fork, q) == cudaSuccess;
-        int i0 = 0;
-        while (ok && i0 < n) {
+    rng[0] = 0;
+    rng[1] = n;
+    int work[11] = {};
+    work[0] = t_off[n];
+    work[9] = u_off[n];
+    work[10] = c_off[n];
+    unsigned mask = 0;
+    if (sv->prec != PREC_FP32) {
+        for (int i0 = 0; i0 < n;) {
             const int ks = recs[i0]->s.Kp / 16;
             int i1 = i0;
             while (i1 < n && recs[i1]->s.Kp / 16 == ks) ++i1;
-            cudaStream_t qs = sl.sub[ks - 1];
-            ok = cudaStreamWaitEvent(qs, sl.ev_fork, 0) == cudaSuccess &&
-                 launch(serve_fn(PREC_MIXED, ks), std::min(t_off[i1] - t_off[i0], nsm), sv->smem,
-                        qs, sl.d_items + i0, dt + i0, i1 - i0) &&
-                 cudaEventRecord(sl.ev_join[ks - 1], qs) == cudaSuccess &&
-                 cudaStreamWaitEvent(q, sl.ev_join[ks - 1], 0) == cudaSuccess;
+            rng[2 * ks] = i0;
+            rng[2 * ks + 1] = i1;
+            work[ks] = t_off[i1] - t_off[i0];
+            mask |= 1u << (ks - 1);
             i0 = i1;
         }
     }
-    // phases 2 and 3 over every item of the batch
+    bool ok = soff <= sl.scratch_bytes;
+    if (ok) ok = cudaMemcpyAsync(sl.d_V, sl.h_V, voff * F * 4, cudaMemcpyHostToDevice, q) == cudaSuccess;
+    if (ok) ok = cudaMemcpyAsync(sl.d_items, sl.h_items, n * sizeof(ServeItem), cudaMemcpyHostToDevice, q) == cudaSuccess;
     if (ok)
-        ok = launch(serve_stats_fn(sv->prec), std::min(u_off[n], nsm),
-                    stats_smem_bytes(sv->prec), q, sl.d_items, du, n);
-    if (ok) ok = launch(serve_rescale_fn(sv->prec), std::min(c_off[n], 4 * nsm), 0, q, sl.d_items, dc, n);
+        ok = cudaMemcpyAsync(sl.d_off, sl.h_off, hdr_ints(sv->cfg.max_batch) * sizeof(int),
+                             cudaMemcpyHostToDevice, q) == cudaSuccess;
+    int nlaunch = 0;
+    if (ok)
+        ok = sv->cfg.launch == ONMF_SERVE_GRAPH ? launch_graph(sv, sl, mask, nlaunch)
+                                                : enqueue_phases(sv, sl, mask, work, false, nlaunch);
     if (ok) ok = cudaMemcpyAsync(sl.h_loss, sl.d_loss, n * 8, cudaMemcpyDeviceToHost, q) == cudaSuccess;
     if (ok && hoff) ok = cudaMemcpyAsync(sl.h_H, sl.d_H, hoff * 4, cudaMemcpyDeviceToHost, q) == cudaSuccess;
     if (ok) ok = cudaMemcpyAsync(sl.h_err, sl.d_err, 4, cudaMemcpyDeviceToHost, q) == cudaSuccess;
@@ -473,6 +546,7 @@ static void worker_main(onmf_server *sv) {
 static void free_server(onmf_server *sv) {
     for (auto &sl : sv->slots) {
         if (sl.stream) cudaStreamSynchronize(sl.stream);
+        for (auto &g : sl.graphs) cudaGraphExecDestroy(g.second.first);
         void *dev[] = {sl.d_items, sl.d_off, sl.d_V, sl.d_H, sl.d_scratch, sl.d_loss, sl.d_err};
         for (void *p : dev)
             if (p) cudaFree(p);
@@ -499,7 +573,8 @@ onmf_status onmf_server_create(const onmf_server_config *cfg, onmf_server **out)
     *out = nullptr;
     const onmf_server_config &c = *cfg;
     if (c.F < 1 || c.F > 1024 || c.max_chunk < 1 || c.max_chunk > 4096 || c.max_batch < 1 ||
-        c.max_batch > 4096 || c.slots < 1 || c.slots > 4 || c.budget_bytes < 1 || c.reserved ||
+        c.max_batch > 4096 || c.slots < 1 || c.slots > 4 || c.budget_bytes < 1 ||
+        (c.launch != ONMF_SERVE_GRAPH && c.launch != ONMF_SERVE_DIRECT) ||
         (c.precision != ONMF_FP32 && c.precision != ONMF_MIXED))
         return ONMF_EINVAL;
     if (configure_kernels() != cudaSuccess) return ONMF_ECUDA;
@@ -534,8 +609,8 @@ onmf_status onmf_server_create(const onmf_server_config *cfg, onmf_server **out)
             cudaEventCreateWithFlags(&sl.ev_fork, cudaEventDisableTiming) == cudaSuccess &&
             cudaMalloc((void **)&sl.d_items, c.max_batch * sizeof(ServeItem)) == cudaSuccess &&
             cudaHostAlloc((void **)&sl.h_items, c.max_batch * sizeof(ServeItem), 0) == cudaSuccess &&
-            cudaMalloc((void **)&sl.d_off, 3 * (c.max_batch + 1) * sizeof(int)) == cudaSuccess &&
-            cudaHostAlloc((void **)&sl.h_off, 3 * (c.max_batch + 1) * sizeof(int), 0) == cudaSuccess &&
+            cudaMalloc((void **)&sl.d_off, hdr_ints(c.max_batch) * sizeof(int)) == cudaSuccess &&
+            cudaHostAlloc((void **)&sl.h_off, hdr_ints(c.max_batch) * sizeof(int), 0) == cudaSuccess &&
             cudaMalloc((void **)&sl.d_V, sv->cap_frames * c.F * 4) == cudaSuccess &&
             cudaHostAlloc((void **)&sl.h_V, sv->cap_frames * c.F * 4, 0) == cudaSuccess &&
             cudaMalloc((void **)&sl.d_H, sv->cap_frames * 128 * 4) == cudaSuccess &&

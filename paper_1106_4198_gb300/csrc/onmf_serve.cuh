@@ -34,8 +34,9 @@ struct ServeItem {
 // separate the phases. The tile, statistics and rescale functions are those
 // of the persistent single-stream kernel, so a chunk's result does not
 // depend on the batch it runs in. off[i] is the first work pair of item i
-// and off[n] one past the last (a launch over items i0.. passes off + i0);
-// pairs are taken in grid-stride order.
+// and off[n] one past the last; a launch covers items range[0] <=
+// i < range[1], read from device memory so that one captured launch serves
+// every batch; pairs are taken in grid-stride order.
 
 // Item owning work pair p: the largest i with off[i] <= p.
 __device__ __forceinline__ int serve_item_of(const int *off, int n, int p) {
@@ -54,7 +55,7 @@ __device__ __forceinline__ int serve_item_of(const int *off, int n, int p) {
 // Kp = 16*KS (KS = 0 on the FP32 path, which is not specialized).
 template <int PREC, int KS>
 __global__ void __launch_bounds__(kThreads, 1) serve_hsolve_kernel(const ServeItem *items,
-                                                                  const int *off, int nitems) {
+                                                                  const int *off, const int *range) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ float s_tmp;
@@ -67,6 +68,9 @@ __global__ void __launch_bounds__(kThreads, 1) serve_hsolve_kernel(const ServeIt
     unsigned wpar = 0, vpar = 0;
     WStage ws{&mbar[0], &wpar, false};
     int staged = -1;  // item whose W^T image is in shared memory
+    const int i0 = range[0], nitems = range[1] - i0;
+    items += i0;
+    off += i0;
     const int base = off[0], total = off[nitems] - base;
     for (int p = blockIdx.x; p < total; p += gridDim.x) {
         const int i = serve_item_of(off, nitems, base + p);
@@ -104,9 +108,12 @@ __global__ void __launch_bounds__(kThreads, 1) serve_hsolve_kernel(const ServeIt
 // Phase 2: statistics, A, B and W' = sqrt(A/B) of (chunk, output tile) pairs.
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1) serve_stats_kernel(const ServeItem *items,
-                                                                 const int *off, int nitems) {
+                                                                 const int *off, const int *range) {
     extern __shared__ __align__(128) unsigned char smem[];
     float *acc = reinterpret_cast<float *>(smem + stats_smem_bytes(PREC) - 2 * 16 * 32 * 4);
+    const int i0 = range[0], nitems = range[1] - i0;
+    items += i0;
+    off += i0;
     const int base = off[0], total = off[nitems] - base;
     for (int p = blockIdx.x; p < total; p += gridDim.x) {
         const int i = serve_item_of(off, nitems, base + p);
@@ -124,9 +131,13 @@ __global__ void __launch_bounds__(kThreads, 1) serve_stats_kernel(const ServeIte
 // past its last column) adds the chunk's loss.
 template <int PREC>
 __global__ void __launch_bounds__(kThreads) serve_rescale_kernel(const ServeItem *items,
-                                                                const int *off, int nitems) {
+                                                                const int *off,
+                                                                const int *range) {
     __shared__ float s_red8[kWarps];
     __shared__ double s_red[kThreads];
+    const int i0 = range[0], nitems = range[1] - i0;
+    items += i0;
+    off += i0;
     const int base = off[0], total = off[nitems] - base;
     for (int p = blockIdx.x; p < total; p += gridDim.x) {
         const int i = serve_item_of(off, nitems, base + p);

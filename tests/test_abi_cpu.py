@@ -38,7 +38,7 @@ def test_config_layout_and_defaults():
     assert c.eps == 1e-12 and c.r == 1.0 and c.n_ref == 0
     assert c.h_exponent == 0.5 and c.normalize == 1 and c.rho_on_new == 0
     assert c.precision == onmf.ONMF_FP32 and c.hsolve == onmf.ONMF_HSOLVE_AUTO
-    assert onmf.onmf_abi_version() == 2
+    assert onmf.onmf_abi_version() == 3
 
 
 def test_status_strings():
@@ -74,6 +74,19 @@ def test_mixed_precision_shape_limits():
         st = onmf.lib().onmf_init(ctypes.byref(c), W0.ctypes.data, 0, None,
                                   ctypes.byref(h))
         assert st == 1 and not h.value
+
+
+@pytest.mark.parametrize("field,value", [
+    ("F", 0), ("max_chunk", 4097), ("max_batch", 0), ("slots", 5), ("budget_bytes", 0),
+    ("precision", 3), ("launch", 2),
+])
+def test_invalid_server_config_rejected_on_host(field, value):
+    c = onmf.onmf_server_config(129, 512, 64, 2, 1 << 20, onmf.ONMF_MIXED,
+                                onmf.ONMF_SERVE_GRAPH)
+    setattr(c, field, value)
+    h = ctypes.c_void_p()
+    assert onmf.lib().onmf_server_create(ctypes.byref(c), ctypes.byref(h)) == 1  # ONMF_EINVAL
+    assert ctypes.sizeof(onmf.onmf_server_config) == 32
 
 
 def test_null_arguments_rejected():

@@ -9,7 +9,9 @@ Checked here:
   - parity with the FP64 oracle run chunk by chunk (FP32 <= 1e-5; mixed
     within the stated 1e-2 on W, 1e-3 on the losses);
   - admission by the memory budget: streams that do not fit wait and run
-    once others close.
+    once others close;
+  - batches launched as captured CUDA graphs (the default) and as direct
+    kernel launches give the same bits.
 """
 import numpy as np
 import pytest
@@ -28,12 +30,13 @@ def chunks_of(n_total, rng, lo=8, hi=64):
     return sizes
 
 
-def serve(streams, precision, budget=1 << 30, max_batch=64, close_early=None):
+def serve(streams, precision, budget=1 << 30, max_batch=64, close_early=None,
+          launch=onmf.ONMF_SERVE_GRAPH):
     """streams: list of (V (N,F), W0 (K,F), sizes, cfg kwargs). Submits every
     chunk of every stream interleaved; returns per-stream (W, chunk losses)."""
     F = streams[0][0].shape[1]
     srv = onmf.onmf_server_create(F, max_chunk=512, max_batch=max_batch, slots=2,
-                                  budget_bytes=budget, precision=precision)
+                                  budget_bytes=budget, precision=precision, launch=launch)
     try:
         ids = []
         for V, W0, sizes, kw in streams:
@@ -181,3 +184,24 @@ def test_admission_by_budget():
         assert st["streams_admitted"] == 4 and st["streams_pending"] == 0
     finally:
         onmf.onmf_server_destroy(srv)
+
+
+@pytest.mark.parametrize("precision", [onmf.ONMF_FP32, onmf.ONMF_MIXED])
+def test_graph_launch_equals_direct_launch(precision):
+    """Every K of the serving mix, ragged chunks, small batches (so that the
+    same set of dictionary sizes recurs with other layouts and each slot
+    replays its graphs many times)."""
+    rng = np.random.default_rng(5)
+    F = 129
+    streams = []
+    for i, K in enumerate([16, 32, 64, 128, 16, 64]):
+        N = int(rng.integers(150, 500))
+        V, W0 = problem(F, K, N, seed=200 + i)
+        streams.append((V, W0, chunks_of(N, rng, 8, 200), dict(n_inner=4)))
+    g, sg = serve(streams, precision, max_batch=4, launch=onmf.ONMF_SERVE_GRAPH)
+    d, sd = serve(streams, precision, max_batch=4, launch=onmf.ONMF_SERVE_DIRECT)
+    print("graph:", sg, "direct:", sd)
+    for (Wg, lg), (Wd, ld) in zip(g, d):
+        assert np.array_equal(Wg, Wd)
+        assert lg == ld
+    assert sg["chunks"] == sd["chunks"] == sum(len(s[2]) for s in streams)
