@@ -290,6 +290,10 @@ typedef struct {
 typedef struct {
     int64_t launches, chunks, frames, batches_overlapped;
     int64_t streams_admitted, streams_pending, bytes_in_use;
+    int64_t host_batch_ns;  /* worker time forming batches (items, offsets)    */
+    int64_t device_ns;      /* sum over batches of device time from the first
+                               copy to the last (slots overlap, so this can
+                               exceed the wall time)                          */
 } onmf_server_stats;
 
 /* Create a server (allocates the per-slot device buffers; the budget covers
@@ -306,10 +310,21 @@ onmf_status onmf_server_open_stream(onmf_server *srv, const onmf_config *cfg,
 /* Queue a chunk of n frames (F x n host memory, leading dimension ldv) for
  * a stream; the frames are copied before the call returns. H_out: NULL or
  * host memory K x n (ld K) that receives the chunk's h when it completes.
- * Errors: EINVAL (n < 1, n > max_chunk, unknown or closing stream). */
+ * Errors: EINVAL (n < 1, n > max_chunk, unknown or closing stream),
+ * ESTATE (an earlier chunk of the stream failed), ENOMEM (host memory). */
 onmf_status onmf_server_submit(onmf_server *srv, int64_t stream_id,
                                const float *V, int64_t ldv, int64_t n,
                                float *H_out, int64_t tag);
+
+/* Queue several chunks in one call, each under the rules of
+ * onmf_server_submit: chunk i is stream_ids[i], V[i] (F x n[i] host memory,
+ * leading dimension ldv[i]), H_out[i] (NULL, or host K x n[i]; H_out itself
+ * may be NULL: no h for any chunk) and tags[i]. Chunks of one stream run in
+ * the order given. Stops at the first chunk that is refused and returns its
+ * status; *queued (may be NULL) receives how many were queued. */
+onmf_status onmf_server_submit_many(onmf_server *srv, int32_t count, const int64_t *stream_ids,
+                                    const float *const *V, const int64_t *ldv, const int64_t *n,
+                                    float *const *H_out, const int64_t *tags, int32_t *queued);
 
 /* Take up to max completions (oldest first), waiting up to wait_ms for the
  * first one. *count receives how many were written (0 on timeout). */

@@ -44,7 +44,7 @@ EXPORTED = [
     "onmf_server_create", "onmf_server_open_stream", "onmf_server_submit",
     "onmf_server_poll", "onmf_server_get_W", "onmf_server_close_stream",
     "onmf_server_get_stats", "onmf_server_destroy", "onmf_selftest_wait",
-    "onmf_push_frames_warm", "onmf_autotune",
+    "onmf_push_frames_warm", "onmf_autotune", "onmf_server_submit_many",
 ]
 
 
@@ -80,7 +80,8 @@ class onmf_completion(ctypes.Structure):
 class onmf_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "launches", "chunks", "frames", "batches_overlapped",
-        "streams_admitted", "streams_pending", "bytes_in_use")]
+        "streams_admitted", "streams_pending", "bytes_in_use", "host_batch_ns",
+        "device_ns")]
 
 
 class OnmfError(RuntimeError):
@@ -141,6 +142,8 @@ def lib():
     L.onmf_server_open_stream.argtypes = [_vp, ctypes.POINTER(onmf_config), _vp,
                                           ctypes.POINTER(_i64)]
     L.onmf_server_submit.argtypes = [_vp, _i64, _vp, _i64, _i64, _vp, _i64]
+    L.onmf_server_submit_many.argtypes = [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
+                                          ctypes.POINTER(_i32)]
     L.onmf_server_poll.argtypes = [_vp, ctypes.POINTER(onmf_completion), _i32,
                                    ctypes.POINTER(_i32), _i32]
     L.onmf_server_get_W.argtypes = [_vp, _i64, _vp]
@@ -161,7 +164,7 @@ def lib():
                  "onmf_server_open_stream", "onmf_server_submit", "onmf_server_poll",
                  "onmf_server_get_W", "onmf_server_close_stream",
                  "onmf_server_get_stats", "onmf_selftest_wait", "onmf_push_frames_warm",
-                 "onmf_autotune"):
+                 "onmf_autotune", "onmf_server_submit_many"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -465,6 +468,26 @@ def onmf_server_submit(srv, sid, V, tag=0, H_out=None):
     ph = H_out.ctypes.data if H_out is not None else None
     _check(lib().onmf_server_submit(srv, sid, V.ctypes.data, V.shape[1], V.shape[0],
                                     ph, int(tag)), "onmf_server_submit")
+
+
+def onmf_server_submit_many(srv, sids, Vs, tags, H_outs=None):
+    """Queue chunks Vs[i] ((n_i, F) float32 host arrays) for streams sids[i]
+    in one call; H_outs: None or a list of (n_i, K) host arrays or None.
+    Returns how many were queued (all, or raises at the first refused)."""
+    m = len(Vs)
+    Vs = [np.ascontiguousarray(v, dtype=np.float32) for v in Vs]
+    pv = (ctypes.c_void_p * m)(*[v.ctypes.data for v in Vs])
+    ld = (_i64 * m)(*[v.shape[1] for v in Vs])
+    nn = (_i64 * m)(*[v.shape[0] for v in Vs])
+    ids = (_i64 * m)(*[int(x) for x in sids])
+    tg = (_i64 * m)(*[int(x) for x in tags])
+    ph = None
+    if H_outs is not None:
+        ph = (ctypes.c_void_p * m)(*[h.ctypes.data if h is not None else None for h in H_outs])
+    q = _i32(0)
+    _check(lib().onmf_server_submit_many(srv, m, ids, pv, ld, nn, ph, tg, ctypes.byref(q)),
+           "onmf_server_submit_many")
+    return int(q.value)
 
 
 def onmf_server_poll(srv, max_n=1024, wait_ms=0):

@@ -267,6 +267,7 @@ const void *serve_stats_fn(int prec) {
     return prec == PREC_FP32 ? (const void *)serve_stats_kernel<PREC_FP32>
                              : (const void *)serve_stats_kernel<PREC_MIXED>;
 }
+const void *serve_gather_fn() { return (const void *)serve_gather_kernel<kGatherU>; }
 const void *serve_rescale_fn(int prec) {
     return prec == PREC_FP32 ? (const void *)serve_rescale_kernel<PREC_FP32>
                              : (const void *)serve_rescale_kernel<PREC_MIXED>;

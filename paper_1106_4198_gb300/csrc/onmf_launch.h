@@ -23,6 +23,7 @@ cudaError_t launch_tiles(const TileArgs &a, int prec, int grid, size_t smem, cud
 cudaError_t launch_prepare(const Shape &s, const float *Wcm, float *Wrm, __nv_bfloat16 *Wimg,
                            float *swpart, cudaStream_t stream, __nv_bfloat16 *Wrow = nullptr);
 bool tc_shape_supported(const Shape &s);
+const void *serve_gather_fn();                // serving phase 0 (frames to the device)
 const void *serve_fn(int prec, int ks);       // serving phase 1 (h-solve)
 const void *serve_stats_fn(int prec);         // serving phase 2 (statistics, W')
 const void *serve_rescale_fn(int prec);       // serving phase 3 (rescale, loss)

@@ -106,10 +106,91 @@ struct Pool {
     }
 };
 
+// Pinned host memory for queued chunks, mapped into the device's address
+// space so that a batch's first kernel reads the frames from it: size
+// classes of 8 << c frames (c = 0..9), each a free list of buffers carved
+// from slabs of at least 8 MB that live until the server is destroyed.
+struct HostBuf {
+    float *h = nullptr;        // host address
+    const float *d = nullptr;  // device address of the same memory
+    int cls = 0;
+};
+
+struct HostArena {
+    static constexpr int kClasses = 10;
+    int F = 1;
+    std::mutex mu;
+    std::vector<HostBuf> free_[kClasses];
+    std::vector<void *> slabs;
+    static int class_of(int n) {
+        int c = 0;
+        while ((8 << c) < n) ++c;
+        return c;
+    }
+    size_t buf_bytes(int c) const { return ((size_t)(8 << c) * F * 4 + 255) / 256 * 256; }
+    bool get(int n, HostBuf &b) {
+        const int c = class_of(n);
+        std::lock_guard<std::mutex> lk(mu);
+        if (free_[c].empty()) {
+            const size_t bb = buf_bytes(c), count = std::max<size_t>(1, (size_t(8) << 20) / bb);
+            void *h = nullptr, *d = nullptr;
+            if (cudaHostAlloc(&h, bb * count, cudaHostAllocMapped | cudaHostAllocPortable) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+                cudaGetLastError();
+                cudaFreeHost(h);
+                return false;
+            }
+            slabs.push_back(h);
+            for (size_t i = 0; i < count; ++i)
+                free_[c].push_back(HostBuf{reinterpret_cast<float *>((char *)h + i * bb),
+                                           reinterpret_cast<const float *>((char *)d + i * bb), c});
+        }
+        b = free_[c].back();
+        free_[c].pop_back();
+        return true;
+    }
+    void put(const HostBuf &b) {
+        std::lock_guard<std::mutex> lk(mu);
+        free_[b.cls].push_back(b);
+    }
+    ~HostArena() {
+        for (void *h : slabs) cudaFreeHost(h);
+    }
+};
+
+// A buffer of the arena, given back when destroyed.
+struct Frames {
+    HostArena *a = nullptr;
+    HostBuf b;
+    Frames() = default;
+    Frames(HostArena *a_, const HostBuf &b_) : a(a_), b(b_) {}
+    Frames(Frames &&o) noexcept : a(o.a), b(o.b) { o.a = nullptr; }
+    Frames &operator=(Frames &&o) noexcept {
+        if (this != &o) {
+            reset();
+            a = o.a;
+            b = o.b;
+            o.a = nullptr;
+        }
+        return *this;
+    }
+    Frames(const Frames &) = delete;
+    Frames &operator=(const Frames &) = delete;
+    ~Frames() { reset(); }
+    void reset() {
+        if (a) a->put(b);
+        a = nullptr;
+    }
+};
+
 struct Chunk {
     int64_t tag;
     int n;
-    std::vector<float> v;  // F x n frames
+    Frames v;  // F x n frames
     float *H_host;
     double t_submit;
 };
@@ -130,19 +211,20 @@ struct StreamRec {
 
 struct Slot {
     cudaStream_t stream = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr, ev0 = nullptr;  // end and start of the batch on the device
     cudaStream_t sub[8] = {};      // one per k16-slab count, joined back into `stream`
     cudaEvent_t ev_fork = nullptr, ev_join[8] = {};
     bool busy = false;
     ServeItem *d_items = nullptr, *h_items = nullptr;
     // batch header (hdr_ints(max_batch) ints, fixed layout): the work
-    // offsets of the three phases (tiles, units, columns; max_batch + 1
-    // each), then item ranges: [0, n) and one per k16-slab count 1..8
+    // offsets of the phases (tiles, units, columns, gather blocks;
+    // max_batch + 1 each), then item ranges: [0, n) and one per k16-slab
+    // count 1..8
     int *d_off = nullptr, *h_off = nullptr;
     // captured phase graphs by the set of k16-slab counts present (bit ks-1;
     // 0 on the FP32 path), with the number of kernels in each
     std::map<unsigned, std::pair<cudaGraphExec_t, int>> graphs;
-    float *d_V = nullptr, *h_V = nullptr;
+    float *d_V = nullptr;  // the batch's frames, each chunk's slice 16-byte aligned
     float *d_H = nullptr, *h_H = nullptr;
     char *d_scratch = nullptr;
     size_t scratch_bytes = 0;
@@ -155,6 +237,7 @@ struct Slot {
         float *H_host;
         size_t h_off;
         int K;
+        Frames v;  // held until the batch is done
     };
     std::vector<Done> chunks;
 };
@@ -163,6 +246,7 @@ struct Slot {
 
 struct onmf_server {
     onmf_server_config cfg;
+    HostArena arena;  // declared before the slots and streams that hold its buffers
     int prec;
     int nsm = 1;
     size_t smem = 0;
@@ -256,12 +340,12 @@ static void release_stream(onmf_server *sv, int64_t id) {
 // Form and launch one batch on a free slot. Returns true if launched.
 static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex> &lk);
 
-static int hdr_ints(int max_batch) { return 3 * (max_batch + 1) + 2 * 9; }
+static int hdr_ints(int max_batch) { return 4 * (max_batch + 1) + 2 * 9; }
 
 // The phases of one batch on the slot's stream, reading the batch's layout
 // from the header in device memory. work[0..8] are the tiles per k16-slab
 // count (work[0]: the FP32 path), work[9] the statistics units, work[10]
-// the columns. `fixed` gives every launch its largest grid (grid-stride
+// the columns, work[11] the gather blocks. `fixed` gives every launch its largest grid (grid-stride
 // loops take any work size), as a captured graph that serves every batch
 // with the same set `mask` of slab counts needs; otherwise each grid is cut
 // to its work.
@@ -269,7 +353,7 @@ static bool enqueue_phases(onmf_server *sv, Slot &sl, unsigned mask, const int *
                            int &nlaunch) {
     cudaStream_t q = sl.stream;
     const int nsm = sv->nsm, M1 = sv->cfg.max_batch + 1;
-    const int *dt = sl.d_off, *du = dt + M1, *dc = du + M1, *dr = dc + M1;
+    const int *dt = sl.d_off, *du = dt + M1, *dc = du + M1, *dg = dc + M1, *dr = dg + M1;
     auto grid = [&](int w, int cap) { return fixed ? cap : std::min(w, cap); };
     auto launch = [&](const void *fn, int g, size_t smem, cudaStream_t st, const int *off,
                       const int *range) {
@@ -279,6 +363,8 @@ static bool enqueue_phases(onmf_server *sv, Slot &sl, unsigned mask, const int *
         return cudaLaunchKernel(fn, dim3(g), dim3(kThreads), args, smem, st) == cudaSuccess;
     };
     bool ok = cudaMemsetAsync(sl.d_err, 0, sizeof(int), q) == cudaSuccess;
+    // phase 0: the frames from mapped host memory to the device
+    if (ok) ok = launch(serve_gather_fn(), grid(work[11], 4 * nsm), 0, q, dg, dr);
     // phase 1: the h-solve; on the mixed path one launch per dictionary size
     // on its own stream (the kernels are specialized by size), then join
     if (ok && sv->prec == PREC_FP32) {
@@ -311,7 +397,7 @@ static bool launch_graph(onmf_server *sv, Slot &sl, unsigned mask, int &nlaunch)
         cudaStream_t q = sl.stream;
         int kernels = 0;
         if (cudaStreamBeginCapture(q, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
-        const int none[11] = {};
+        const int none[12] = {};
         const bool queued = enqueue_phases(sv, sl, mask, none, true, kernels);
         cudaGraph_t g = nullptr;
         const bool ended = cudaStreamEndCapture(q, &g) == cudaSuccess;
@@ -354,8 +440,9 @@ static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex
             ++it;
             continue;
         }
-        if (frames + r.queue.front().n > sv->cap_frames) break;
-        frames += r.queue.front().n;
+        const size_t padded = (r.queue.front().n + 3) & ~3;
+        if (frames + padded > sv->cap_frames) break;
+        frames += padded;
         picked.emplace_back(r.id, std::move(r.queue.front()));
         r.queue.pop_front();
         r.in_flight = true;
@@ -382,6 +469,7 @@ static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex
         recs.swap(r2);
     }
     sl.chunks.clear();
+    const auto t_form = std::chrono::steady_clock::now();
     size_t voff = 0, hoff = 0, soff = 0;
     const int elem = sv->prec == PREC_FP32 ? 4 : 2;
     for (size_t i = 0; i < picked.size(); ++i) {
@@ -389,7 +477,6 @@ static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex
         StreamRec &r = *recs[i];
         const Shape &s = r.s;
         const int betap = (c.n + 15) / 16 * 16;
-        memcpy(sl.h_V + voff * F, c.v.data(), (size_t)c.n * F * 4);
         ServeItem it;
         memset(&it, 0, sizeof it);
         it.s = s;
@@ -400,7 +487,8 @@ static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex
         it.normalize = r.cfg.normalize;
         it.rho_on_new = r.cfg.rho_on_new;
         it.rho = r.cfg.n_ref > 0 ? std::pow(r.cfg.r, (double)c.n / (double)r.cfg.n_ref) : 1.0;
-        it.V = sl.d_V + voff * F;
+        it.V = sl.d_V + voff * F;  // voff is a multiple of 4 frames: 16-byte aligned
+        it.Vsrc = c.v.b.d;
         it.H_out = c.H_host ? sl.d_H + hoff : nullptr;
         it.Wcm = r.Wcm;
         it.Wrm = r.Wrm;
@@ -424,8 +512,9 @@ static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex
         it.chunk_loss = sl.d_loss + i;
         it.err = sl.d_err;
         sl.h_items[i] = it;
-        sl.chunks.push_back({picked[i].first, c.tag, c.n, c.t_submit, c.H_host, hoff, s.K});
-        voff += c.n;
+        sl.chunks.push_back(
+            {picked[i].first, c.tag, c.n, c.t_submit, c.H_host, hoff, s.K, std::move(c.v)});
+        voff += (c.n + 3) & ~3;
         if (c.H_host) hoff += (size_t)c.n * s.K;
     }
     const int n = (int)picked.size();
@@ -433,20 +522,24 @@ static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex
     // the batch header: work offsets of the three phases (8-frame tiles,
     // (16 x 32) output tiles, columns + the loss) and the item ranges
     const int M1 = sv->cfg.max_batch + 1;
-    int *t_off = sl.h_off, *u_off = t_off + M1, *c_off = u_off + M1, *rng = c_off + M1;
-    t_off[0] = u_off[0] = c_off[0] = 0;
+    int *t_off = sl.h_off, *u_off = t_off + M1, *c_off = u_off + M1, *g_off = c_off + M1;
+    int *rng = g_off + M1;
+    t_off[0] = u_off[0] = c_off[0] = g_off[0] = 0;
     for (int i = 0; i < n; ++i) {
         const Shape &s = recs[i]->s;
         t_off[i + 1] = t_off[i] + ceil_div(sl.h_items[i].n, kTile);
         u_off[i + 1] = u_off[i] + (s.Fp16 / 16) * (s.Kh / 32);
         c_off[i + 1] = c_off[i] + s.K + 1;
+        const long long f4 = ((long long)sl.h_items[i].n * F + 3) / 4;
+        g_off[i + 1] = g_off[i] + (int)((f4 + kGatherF4 - 1) / kGatherF4);
     }
     rng[0] = 0;
     rng[1] = n;
-    int work[11] = {};
+    int work[12] = {};
     work[0] = t_off[n];
     work[9] = u_off[n];
     work[10] = c_off[n];
+    work[11] = g_off[n];
     unsigned mask = 0;
     if (sv->prec != PREC_FP32) {
         for (int i0 = 0; i0 < n;) {
@@ -461,11 +554,13 @@ static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex
         }
     }
     bool ok = soff <= sl.scratch_bytes;
-    if (ok) ok = cudaMemcpyAsync(sl.d_V, sl.h_V, voff * F * 4, cudaMemcpyHostToDevice, q) == cudaSuccess;
+    if (ok) ok = cudaEventRecord(sl.ev0, q) == cudaSuccess;
     if (ok) ok = cudaMemcpyAsync(sl.d_items, sl.h_items, n * sizeof(ServeItem), cudaMemcpyHostToDevice, q) == cudaSuccess;
     if (ok)
         ok = cudaMemcpyAsync(sl.d_off, sl.h_off, hdr_ints(sv->cfg.max_batch) * sizeof(int),
                              cudaMemcpyHostToDevice, q) == cudaSuccess;
+    const int64_t form_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                std::chrono::steady_clock::now() - t_form).count();
     int nlaunch = 0;
     if (ok)
         ok = sv->cfg.launch == ONMF_SERVE_GRAPH ? launch_graph(sv, sl, mask, nlaunch)
@@ -481,6 +576,7 @@ static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex
     sl.busy = true;
     if (!ok) *sl.h_err = -1;
     sv->st.launches += nlaunch;
+    sv->st.host_batch_ns += form_ns;
     if (busy_other) sv->st.batches_overlapped++;
     return true;
 }
@@ -488,6 +584,9 @@ static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex
 static void finish_batch(onmf_server *sv, Slot &sl) {
     const double t = now_s();
     const int err = *sl.h_err;
+    float ms = 0.f;
+    if (err == 0 && cudaEventElapsedTime(&ms, sl.ev0, sl.ev) == cudaSuccess)
+        sv->st.device_ns += (int64_t)(1e6 * ms);
     for (size_t i = 0; i < sl.chunks.size(); ++i) {
         auto &c = sl.chunks[i];
         onmf_completion cp;
@@ -500,6 +599,7 @@ static void finish_batch(onmf_server *sv, Slot &sl) {
         cp.t_done = t;
         cp.status = err == 0 ? ONMF_OK : (err < 0 ? ONMF_ECUDA : ONMF_ENUMERIC);
         if (c.H_host) memcpy(c.H_host, sl.h_H + c.h_off, (size_t)c.n * c.K * 4);
+        c.v.reset();  // the frames have been read: the buffer goes back to the arena
         sv->done.push_back(cp);
         sv->st.chunks++;
         sv->st.frames += c.n;
@@ -550,10 +650,11 @@ static void free_server(onmf_server *sv) {
         void *dev[] = {sl.d_items, sl.d_off, sl.d_V, sl.d_H, sl.d_scratch, sl.d_loss, sl.d_err};
         for (void *p : dev)
             if (p) cudaFree(p);
-        void *host[] = {sl.h_items, sl.h_off, sl.h_V, sl.h_H, sl.h_loss, sl.h_err};
+        void *host[] = {sl.h_items, sl.h_off, sl.h_H, sl.h_loss, sl.h_err};
         for (void *p : host)
             if (p) cudaFreeHost(p);
         if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.ev0) cudaEventDestroy(sl.ev0);
         if (sl.ev_fork) cudaEventDestroy(sl.ev_fork);
         for (int g = 0; g < 8; ++g) {
             if (sl.ev_join[g]) cudaEventDestroy(sl.ev_join[g]);
@@ -580,6 +681,7 @@ onmf_status onmf_server_create(const onmf_server_config *cfg, onmf_server **out)
     if (configure_kernels() != cudaSuccess) return ONMF_ECUDA;
     onmf_server *sv = new onmf_server();
     sv->cfg = c;
+    sv->arena.F = c.F;
     sv->prec = c.precision == ONMF_MIXED ? PREC_MIXED : PREC_FP32;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -590,7 +692,9 @@ onmf_status onmf_server_create(const onmf_server_config *cfg, onmf_server **out)
         return ONMF_EINVAL;
     }
     // frames per batch: enough for max_batch average chunks, at least one largest chunk
-    sv->cap_frames = std::max<size_t>((size_t)c.max_chunk, std::min<size_t>((size_t)c.max_batch * 128, 65536));
+    // (chunk slices start at multiples of 4 frames)
+    sv->cap_frames = std::max<size_t>(((size_t)c.max_chunk + 3) & ~size_t(3),
+                                      std::min<size_t>((size_t)c.max_batch * 128, 65536));
     const Shape worst = make_shape(c.F, 128);
     const int elem = sv->prec == PREC_FP32 ? 4 : 2;
     const size_t per_frame = (size_t)worst.Fp16 * elem * 2 + (size_t)worst.Kh * elem + 8;
@@ -605,14 +709,13 @@ onmf_status onmf_server_create(const onmf_server_config *cfg, onmf_server **out)
         sl.scratch_bytes = (sv->cap_frames + 16 * (size_t)c.max_batch) * per_frame + 1024 * (size_t)c.max_batch;
         bool ok =
             cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
-            cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreate(&sl.ev) == cudaSuccess && cudaEventCreate(&sl.ev0) == cudaSuccess &&
             cudaEventCreateWithFlags(&sl.ev_fork, cudaEventDisableTiming) == cudaSuccess &&
             cudaMalloc((void **)&sl.d_items, c.max_batch * sizeof(ServeItem)) == cudaSuccess &&
             cudaHostAlloc((void **)&sl.h_items, c.max_batch * sizeof(ServeItem), 0) == cudaSuccess &&
             cudaMalloc((void **)&sl.d_off, hdr_ints(c.max_batch) * sizeof(int)) == cudaSuccess &&
             cudaHostAlloc((void **)&sl.h_off, hdr_ints(c.max_batch) * sizeof(int), 0) == cudaSuccess &&
             cudaMalloc((void **)&sl.d_V, sv->cap_frames * c.F * 4) == cudaSuccess &&
-            cudaHostAlloc((void **)&sl.h_V, sv->cap_frames * c.F * 4, 0) == cudaSuccess &&
             cudaMalloc((void **)&sl.d_H, sv->cap_frames * 128 * 4) == cudaSuccess &&
             cudaHostAlloc((void **)&sl.h_H, sv->cap_frames * 128 * 4, 0) == cudaSuccess &&
             cudaMalloc((void **)&sl.d_scratch, sl.scratch_bytes) == cudaSuccess &&
@@ -673,8 +776,13 @@ onmf_status onmf_server_submit(onmf_server *sv, int64_t id, const float *V, int6
     c.n = (int)n;
     c.H_host = H_out;
     const int F = sv->cfg.F;
-    c.v.resize((size_t)n * F);
-    for (int64_t j = 0; j < n; ++j) memcpy(c.v.data() + j * F, V + j * ldv, (size_t)F * 4);
+    HostBuf b;
+    if (!sv->arena.get((int)n, b)) return ONMF_ENOMEM;
+    c.v = Frames(&sv->arena, b);
+    if (ldv == F)
+        memcpy(b.h, V, (size_t)n * F * 4);
+    else
+        for (int64_t j = 0; j < n; ++j) memcpy(b.h + j * F, V + j * ldv, (size_t)F * 4);
     c.t_submit = now_s();
     {
         std::lock_guard<std::mutex> lk(sv->mu);
@@ -685,6 +793,21 @@ onmf_status onmf_server_submit(onmf_server *sv, int64_t id, const float *V, int6
         sv->arrivals.push_back(id);
     }
     sv->cv_work.notify_one();
+    return ONMF_OK;
+}
+
+onmf_status onmf_server_submit_many(onmf_server *sv, int32_t count, const int64_t *stream_ids,
+                                    const float *const *V, const int64_t *ldv, const int64_t *n,
+                                    float *const *H_out, const int64_t *tags, int32_t *queued) {
+    if (queued) *queued = 0;
+    if (!sv || count < 0 || (count > 0 && (!stream_ids || !V || !ldv || !n || !tags)))
+        return ONMF_EINVAL;
+    for (int32_t i = 0; i < count; ++i) {
+        const onmf_status st = onmf_server_submit(sv, stream_ids[i], V[i], ldv[i], n[i],
+                                                  H_out ? H_out[i] : nullptr, tags[i]);
+        if (st != ONMF_OK) return st;
+        if (queued) *queued = i + 1;
+    }
     return ONMF_OK;
 }
 

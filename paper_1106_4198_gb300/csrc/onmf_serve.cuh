@@ -1,6 +1,6 @@
 // Device side of serving (see onmf_serve.cu): the Algorithm 1 step
 // (arXiv:1106.4198) of a batch of chunks of different streams, one
-// minibatch per chunk, in three launches (below).
+// minibatch per chunk, in three phases after a copy of the frames (below).
 #pragma once
 
 #include "onmf_step.cuh"
@@ -14,7 +14,8 @@ struct ServeItem {
     float eps, gamma;
     int normalize, rho_on_new;
     double rho;
-    const float *V;  // F x n, ld F
+    const float *V;     // F x n, ld F, in the batch's device frame buffer
+    const float *Vsrc;  // the same frames in mapped pinned host memory
     float *H_out;    // K x n, ld K (device) or null
     float *Wcm, *Wrm, *Wn, *swpart;
     __nv_bfloat16 *Wimg;
@@ -49,6 +50,43 @@ __device__ __forceinline__ int serve_item_of(const int *off, int n, int p) {
             hi = mid - 1;
     }
     return lo;
+}
+
+// Phase 0: the frames of every chunk from the pinned host buffer it was
+// submitted into (mapped into the device's address space) to its slice of
+// the batch's device frame buffer. Work pairs are (chunk, block of
+// kGatherF4 float4, U per thread, loads before stores); both ends are
+// 16-byte aligned and padded to a whole float4, so the copy is in float4
+// throughout.
+constexpr int kGatherU = 4, kGatherF4 = kGatherU * kThreads;
+
+template <int U>
+__global__ void __launch_bounds__(kThreads) serve_gather_kernel(const ServeItem *items,
+                                                                const int *off,
+                                                                const int *range) {
+    const int i0 = range[0], nitems = range[1] - i0;
+    items += i0;
+    off += i0;
+    const int base = off[0], total = off[nitems] - base;
+    for (int p = blockIdx.x; p < total; p += gridDim.x) {
+        const int i = serve_item_of(off, nitems, base + p);
+        const ServeItem &it = items[i];
+        const long long nv = ((long long)it.n * it.s.F + 3) >> 2;
+        const long long v0 = (long long)(base + p - off[i]) * kGatherF4 + threadIdx.x;
+        const float4 *src = reinterpret_cast<const float4 *>(it.Vsrc);
+        float4 *dst = reinterpret_cast<float4 *>(const_cast<float *>(it.V));
+        float4 r[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long v = v0 + u * kThreads;
+            if (v < nv) r[u] = src[v];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const long long v = v0 + u * kThreads;
+            if (v < nv) dst[v] = r[u];
+        }
+    }
 }
 
 // Phase 1: h-solve of (chunk, tile) pairs; every item of the launch has

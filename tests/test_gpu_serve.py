@@ -205,3 +205,46 @@ def test_graph_launch_equals_direct_launch(precision):
         assert np.array_equal(Wg, Wd)
         assert lg == ld
     assert sg["chunks"] == sd["chunks"] == sum(len(s[2]) for s in streams)
+
+
+def test_submit_many_equals_submit_one_by_one():
+    """One onmf_server_submit_many call per stream gives the bits of one
+    onmf_server_submit call per chunk; H_out rows arrive for the chunks that
+    ask for them."""
+    rng = np.random.default_rng(9)
+    F = 129
+    streams = []
+    for i, K in enumerate([16, 64, 32]):
+        N = int(rng.integers(120, 300))
+        V, W0 = problem(F, K, N, seed=300 + i)
+        streams.append((V, W0, chunks_of(N, rng, 8, 100), dict(n_inner=3)))
+    ref, _ = serve(streams, onmf.ONMF_MIXED)
+    srv = onmf.onmf_server_create(F, max_chunk=512, max_batch=8, slots=2,
+                                  precision=onmf.ONMF_MIXED)
+    try:
+        ids, total, Hs = [], 0, []
+        for V, W0, sizes, kw in streams:
+            cfg = onmf.onmf_config_default(F, W0.shape[0], precision=onmf.ONMF_MIXED, **kw)
+            ids.append(onmf.onmf_server_open_stream(srv, cfg, W0))
+        for (V, W0, sizes, kw), sid in zip(streams, ids):
+            starts = np.cumsum([0] + sizes[:-1])
+            Vs = [V[a:a + n] for a, n in zip(starts, sizes)]
+            H = [np.zeros((n, W0.shape[0]), np.float32) if c % 2 == 0 else None
+                 for c, n in enumerate(sizes)]
+            Hs.append(H)
+            assert onmf.onmf_server_submit_many(srv, [sid] * len(sizes), Vs,
+                                                list(range(len(sizes))), H) == len(sizes)
+            total += len(sizes)
+        got = 0
+        while got < total:
+            for cp in onmf.onmf_server_poll(srv, 256, wait_ms=2000):
+                assert cp.status == 0
+                got += 1
+        for i, ((V, W0, sizes, kw), sid) in enumerate(zip(streams, ids)):
+            W = onmf.onmf_server_get_W(srv, sid, W0.shape[0], F)
+            assert np.array_equal(W, ref[i][0])
+            assert all(h is None or (np.all(np.isfinite(h)) and h.max() > 0) for h in Hs[i])
+        with pytest.raises(onmf.OnmfError):  # unknown stream: refused
+            onmf.onmf_server_submit_many(srv, [12345], [V[:8]], [0])
+    finally:
+        onmf.onmf_server_destroy(srv)
