@@ -45,6 +45,10 @@ def parse():
     p.add_argument("--hsolve", default="auto", choices=["auto", "mma", "tc", "cluster"],
                    help="h-solve kernel of the mixed path; auto: the autotuner's choice")
     p.add_argument("--skip-fp32", action="store_true")
+    p.add_argument("--accumulate", default="auto",
+                   choices=["auto", "fp64", "fp32", "fp32_compensated"],
+                   help="arithmetic of A, B on the mixed path; auto: measure the drift of "
+                        "each over one pass and take the fastest within bounds")
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-cpu", action="store_true")
     p.add_argument("--cpu-sample-minibatches", type=int, default=120)
@@ -78,6 +82,19 @@ def init_dist(world, backend):
         os.environ.setdefault("MASTER_PORT", "29511")
         dist.init_process_group(backend=backend)
     return dist if world > 1 else None
+
+
+DRIFT_W, DRIFT_AB = 1e-6, 1e-9
+
+
+def choose_accumulate(drift):
+    """The fastest arithmetic of A, B whose drift against the FP64 sums over
+    the measured pass stays within DRIFT_W (W) and DRIFT_AB (A, B); FP64
+    itself always qualifies."""
+    ok = [n for n in ("fp64", "fp32", "fp32_compensated") if n in drift and (
+        n == "fp64" or (drift[n]["W_rel"] <= DRIFT_W and drift[n]["A_rel"] <= DRIFT_AB
+                        and drift[n]["B_rel"] <= DRIFT_AB))]
+    return min(ok, key=lambda n: drift[n]["ms_per_1e6_frames"])
 
 
 def barrier(dist, device=None):
@@ -218,10 +235,56 @@ def run_ours(args):
         tune_us = None
     hname = onmf.HSOLVE_NAMES[hsolve]
 
+    # drift of the running statistics A, B over the whole stream in each
+    # arithmetic (FP64 sums as the reference); one pass of all the chunks
+    drift = None
+    acc = {v: k for k, v in onmf.ACC_NAMES.items()}.get(args.accumulate, onmf.ONMF_ACC_FP64)
+    if rank == 0 and args.accumulate == "auto":
+        runs = {}
+        # two rounds, the modes interleaved; the time of a mode is its faster
+        # pass (the results are deterministic, the same in both rounds)
+        for _ in range(2):
+            for mode in (onmf.ONMF_ACC_FP64, onmf.ONMF_ACC_FP32, onmf.ONMF_ACC_FP32_COMP):
+                m = onmf.OnlineISNMF(F, K, W0, stream=stream, beta=BETA, n_inner=N_IN,
+                                     precision=onmf.ONMF_MIXED, hsolve=hsolve, accumulate=mode)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for c in chunks:
+                    m.push(c)
+                e1.record(stream)
+                m.sync()
+                A, B, t, ls = m.stats()
+                name = onmf.ACC_NAMES[mode]
+                ms = e0.elapsed_time(e1)
+                if name in runs:
+                    ms = min(ms, runs[name]["ms"])
+                runs[name] = dict(W=m.W(), A=A, B=B, t=t, loss=ls, ms=ms)
+                m.close()
+        ref = runs["fp64"]
+
+        def rel(a, b):
+            return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        drift = {"frames": int(ref["t"]), "minibatches": int(ref["t"]) // BETA,
+                 "reference": "the same pass with FP64 sums"}
+        for name, r in runs.items():
+            drift[name] = {"ms_per_1e6_frames": r["ms"] / (r["t"] / 1e6)}
+            if name != "fp64":
+                drift[name].update(W_rel=rel(r["W"], ref["W"]), A_rel=rel(r["A"], ref["A"]),
+                                   B_rel=rel(r["B"], ref["B"]),
+                                   loss_rel=abs(r["loss"] - ref["loss"]) / ref["loss"])
+        drift["rule"] = ("fastest arithmetic whose W drifts <= %g and A, B <= %g "
+                         "relative to FP64 sums" % (DRIFT_W, DRIFT_AB))
+        name = choose_accumulate(drift)
+        drift["choice"] = name
+        acc = {v: k for k, v in onmf.ACC_NAMES.items()}[name]
+    acc = int(max_over_ranks(dist, float(acc) if rank == 0 else -1.0, dev))
+
     def timed_pass(precision, record_launch_times=False):
         m = onmf.OnlineISNMF(F, K, W0, stream=stream, beta=BETA, n_inner=N_IN,
                              precision=precision,
-                             hsolve=hsolve if precision == onmf.ONMF_MIXED else 0)
+                             hsolve=hsolve if precision == onmf.ONMF_MIXED else 0,
+                             accumulate=acc if precision == onmf.ONMF_MIXED else 0)
         for w in range(args.warmup):
             m.push(chunks[w % len(chunks)])
         m.sync()
@@ -257,7 +320,7 @@ def run_ours(args):
         host[0].copy_(chunks[0])
         host[1].copy_(chunks[1 % len(chunks)])
         m = onmf.OnlineISNMF(F, K, W0, stream=stream, beta=BETA, n_inner=N_IN,
-                             precision=onmf.ONMF_MIXED, hsolve=hsolve)
+                             precision=onmf.ONMF_MIXED, hsolve=hsolve, accumulate=acc)
         for w in range(args.warmup):
             m.push(host[w % 2].numpy())
         m.sync()
@@ -305,6 +368,7 @@ def run_ours(args):
                        "global_batch": fps * world,
                        "l2": "inputs 2.05 GB/step > L2, no flush",
                        "hsolve": hname,
+                       "accumulate": onmf.ACC_NAMES[acc],
                        "autotune_us_per_minibatch": tune_us,
                        "parallelism": "replicas" if world > 1 else "single"},
             "fp32_value": (total_frames / (fp32["ms"] / 1e3)) if fp32 else None,
@@ -317,6 +381,7 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": mixed["launches"],
             "clocks": mixed["clocks"],
+            "accumulator_drift": drift,
         }
     return out, dist
 

@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define ONMF_ABI_VERSION 3
+#define ONMF_ABI_VERSION 4
 
 typedef struct onmf_state onmf_state;
 
@@ -75,6 +75,20 @@ typedef enum {
     ONMF_HSOLVE_CLUSTER = 3
 } onmf_hsolve;
 
+/* Arithmetic of the running statistics A and B (onmf_config.accumulate).
+ * Each entry takes 8 bytes on the device in every mode:
+ *   FP64       a double (default);
+ *   FP32       a float;
+ *   FP32_COMP  a pair of floats (hi, lo) with hi = fl(hi + lo): the sum is
+ *              carried to about twice float precision by error-free
+ *              transformations (compensated summation).
+ * onmf_get_stats and onmf_set_state convert to and from doubles. */
+typedef enum {
+    ONMF_ACC_FP64 = 0,
+    ONMF_ACC_FP32 = 1,
+    ONMF_ACC_FP32_COMP = 2
+} onmf_accumulate;
+
 /* Parameters of Algorithm 1 (Section 2.3). */
 typedef struct {
     int32_t F;          /* frequency bins (rows of V and W), >= 1              */
@@ -90,11 +104,14 @@ typedef struct {
                            1: A <- A + rho*sum a (literal Algorithm 1)          */
     int32_t precision;  /* onmf_precision                                       */
     int32_t hsolve;     /* onmf_hsolve: h-solve kernel of the mixed path (0 = auto) */
+    int32_t accumulate; /* onmf_accumulate: arithmetic of A and B (0 = FP64)    */
+    int32_t reserved;   /* must be 0                                            */
 } onmf_config;
 
 /* Fill *cfg with the defaults for an F x K problem: beta = 1000,
  * n_inner = 10, eps = 1e-12, r = 1, n_ref = 0, h_exponent = 0.5,
- * normalize = 1, rho_on_new = 0, precision = ONMF_FP32, hsolve = AUTO. */
+ * normalize = 1, rho_on_new = 0, precision = ONMF_FP32, hsolve = AUTO,
+ * accumulate = FP64. */
 void onmf_config_default(onmf_config *cfg, int32_t F, int32_t K);
 
 /* Create an online state (Algorithm 1, "Input": W^(0), A^(0) = B^(0) = 0).
@@ -160,14 +177,18 @@ onmf_status onmf_get_W(onmf_state *s, float *W_out, int32_t on_device);
 
 /* Copy the sufficient statistics and counters to host memory. Any pointer
  * may be NULL. A, B: F x K float64 (Eq. aux_fun, accumulated as in
- * Algorithm 1). t: frames processed by completed minibatches. loss_sum:
+ * Algorithm 1 in the state's onmf_accumulate arithmetic and converted to
+ * double; device pointers are taken only with ONMF_ACC_FP64, else EINVAL).
+ * t: frames processed by completed minibatches. loss_sum:
  * running sum of d_IS(eps + v_t, eps + W h_t) over those frames (the online
  * loss of Eq. online_loss times t). Synchronizes. */
 onmf_status onmf_get_stats(onmf_state *s, double *A, double *B, int64_t *t,
                            double *loss_sum);
 
 /* Restore a state (checkpoint/resume). W: F x K float32, A, B: F x K
- * float64, all host memory; t and loss_sum as returned by onmf_get_stats.
+ * float64, all host memory (device pointers: EINVAL); t and loss_sum as
+ * returned by onmf_get_stats. A and B are rounded to the state's
+ * onmf_accumulate arithmetic (a float pair holds a double to about 2^-48).
  * Clears the staging buffer and any sticky error. Synchronizes. */
 onmf_status onmf_set_state(onmf_state *s, const float *W, const double *A,
                            const double *B, int64_t t, double loss_sum);
@@ -301,7 +322,8 @@ typedef struct {
 onmf_status onmf_server_create(const onmf_server_config *cfg, onmf_server **out);
 
 /* Open a stream with its own parameters (cfg->F must equal the server's F;
- * K <= 128; cfg->beta is ignored: chunks are the minibatches) and initial
+ * K <= 128; hsolve AUTO or MMA; accumulate FP64; cfg->beta is ignored:
+ * chunks are the minibatches) and initial
  * dictionary W0 (F x K, host). Returns its id; the stream is admitted now if
  * its state fits the budget, else it waits in FIFO order. */
 onmf_status onmf_server_open_stream(onmf_server *srv, const onmf_config *cfg,

@@ -32,6 +32,8 @@ ONMF_MIXED = 1
 ONMF_HSOLVE_AUTO, ONMF_HSOLVE_MMA, ONMF_HSOLVE_TC, ONMF_HSOLVE_CLUSTER = 0, 1, 2, 3
 HSOLVE_NAMES = {0: "auto", 1: "mma", 2: "tc", 3: "cluster"}
 ONMF_SERVE_GRAPH, ONMF_SERVE_DIRECT = 0, 1
+ONMF_ACC_FP64, ONMF_ACC_FP32, ONMF_ACC_FP32_COMP = 0, 1, 2
+ACC_NAMES = {0: "fp64", 1: "fp32", 2: "fp32_compensated"}
 ONMF_ETIMEOUT = 6
 
 # Every symbol include/onmf.h declares.
@@ -56,6 +58,7 @@ class onmf_config(ctypes.Structure):
         ("n_ref", ctypes.c_int64), ("h_exponent", ctypes.c_double),
         ("normalize", ctypes.c_int32), ("rho_on_new", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("hsolve", ctypes.c_int32),
+        ("accumulate", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 

@@ -273,7 +273,8 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
     if (c.F < 1 || c.F > 8192 || c.K < 1 || c.K > 256 || c.beta < 1 || c.beta > (1 << 20) ||
         c.n_inner < 0 || c.n_inner > 100000 || !(c.eps >= 0.0) || !std::isfinite(c.eps) ||
         !(c.r >= 0.0 && c.r <= 1.0) || !(c.h_exponent > 0.0) || c.hsolve < 0 || c.hsolve > 3 ||
-        (c.precision != ONMF_FP32 && c.precision != ONMF_MIXED))
+        (c.precision != ONMF_FP32 && c.precision != ONMF_MIXED) || c.accumulate < 0 ||
+        c.accumulate > 2 || c.reserved)
         return ONMF_EINVAL;
     if (c.precision == ONMF_MIXED && c.F > 1024) {
         snprintf(g_msg, sizeof g_msg, "mixed precision supports F <= 1024");
@@ -424,6 +425,7 @@ static onmf_status run_minibatches(onmf_state *s, const float *V, long long ldv,
     a.n_in = c.n_inner;
     a.normalize = c.normalize;
     a.rho_on_new = c.rho_on_new;
+    a.acc = c.accumulate;
     a.V = V;
     a.ldv = ldv;
     a.nmb = nmb;
@@ -682,10 +684,23 @@ onmf_status onmf_get_W(onmf_state *s, float *W_out, int32_t on_device) {
 
 onmf_status onmf_get_stats(onmf_state *s, double *A, double *B, int64_t *t, double *loss_sum) {
     if (!s) return ONMF_EINVAL;
+    if (s->cfg.accumulate != ONMF_ACC_FP64 && ((A && is_device_ptr(A)) || (B && is_device_ptr(B))))
+        return ONMF_EINVAL;  // the conversion to doubles runs on the host
     onmf_status st = sync_and_check(s);
     const size_t FK = (size_t)s->cfg.F * s->cfg.K;
     if (A) CK(cudaMemcpy(A, s->A, FK * 8, cudaMemcpyDefault));
     if (B) CK(cudaMemcpy(B, s->B, FK * 8, cudaMemcpyDefault));
+    if (s->cfg.accumulate != ONMF_ACC_FP64) {
+        // float pairs (hi, lo) in the same 8 bytes -> hi + lo as a double
+        for (double *X : {A, B}) {
+            if (!X) continue;
+            for (size_t i = 0; i < FK; ++i) {
+                float v[2];
+                memcpy(v, X + i, 8);
+                X[i] = (double)v[0] + (double)v[1];
+            }
+        }
+    }
     if (loss_sum) CK(cudaMemcpy(loss_sum, s->loss_sum, 8, cudaMemcpyDefault));
     if (t) *t = s->t;
     return st;
@@ -694,14 +709,30 @@ onmf_status onmf_get_stats(onmf_state *s, double *A, double *B, int64_t *t, doub
 onmf_status onmf_set_state(onmf_state *s, const float *W, const double *A, const double *B,
                            int64_t t, double loss_sum) {
     if (!s || !W || !A || !B || t < 0) return ONMF_EINVAL;
+    if (is_device_ptr(W) || is_device_ptr(A) || is_device_ptr(B)) return ONMF_EINVAL;
     CK(cudaStreamSynchronize(s->stream));
     const size_t FK = (size_t)s->cfg.F * s->cfg.K;
     for (size_t i = 0; i < FK; ++i)
         if (!(W[i] >= 0.f) || std::isinf(W[i]) || !(A[i] >= 0.0) || !(B[i] >= 0.0))
             return ONMF_EINVAL;
     CK(cudaMemcpy(s->Wcm, W, FK * 4, cudaMemcpyDefault));
-    CK(cudaMemcpy(s->A, A, FK * 8, cudaMemcpyDefault));
-    CK(cudaMemcpy(s->B, B, FK * 8, cudaMemcpyDefault));
+    if (s->cfg.accumulate == ONMF_ACC_FP64) {
+        CK(cudaMemcpy(s->A, A, FK * 8, cudaMemcpyDefault));
+        CK(cudaMemcpy(s->B, B, FK * 8, cudaMemcpyDefault));
+    } else {
+        // doubles -> (hi, lo) float pairs (lo = 0 for plain FP32)
+        std::vector<float> pair(2 * FK);
+        for (int which = 0; which < 2; ++which) {
+            const double *X = which ? B : A;
+            for (size_t i = 0; i < FK; ++i) {
+                const float hi = (float)X[i];
+                pair[2 * i] = hi;
+                pair[2 * i + 1] =
+                    s->cfg.accumulate == ONMF_ACC_FP32_COMP ? (float)(X[i] - (double)hi) : 0.f;
+            }
+            CK(cudaMemcpy(which ? s->B : s->A, pair.data(), FK * 8, cudaMemcpyHostToDevice));
+        }
+    }
     CK(cudaMemcpy(s->loss_sum, &loss_sum, 8, cudaMemcpyHostToDevice));
     CK(cudaMemset(s->err_d, 0, 16));
     *s->err_h = 0;

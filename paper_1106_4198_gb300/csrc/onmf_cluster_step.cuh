@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_cluster_kernel(StepArgs a,
         if (!cl_grid_sync(a.bar, G, epoch, a.err, s_vote, vp, C, rank)) break;
         // ---- phase 3: column sums, rescale, bf16 rows of W, loss
         normalize_columns<PREC_CL>(s, a.normalize, a.Wn, a.Wcm, a.Wrm, a.Wimg, a.Wrow, a.A, a.B,
-                                   a.swpart, a.err, s_red8, blockIdx.x, gridDim.x);
+                                   a.acc, a.swpart, a.err, s_red8, blockIdx.x, gridDim.x);
         if (blockIdx.x == G - 1) {
             const double l = block_sum_ordered(a.loss_part, (long long)ntiles * C, s_red);
             if (threadIdx.x == 0) *a.loss_sum += l;

@@ -57,6 +57,7 @@ struct StepArgs {
     int n_in;
     int normalize;
     int rho_on_new;
+    int acc;  // arithmetic of A and B (ACC_*)
     // frames
     const float *V;
     long long ldv;

@@ -745,10 +745,11 @@ onmf_status onmf_server_open_stream(onmf_server *sv, const onmf_config *cfg, con
                                     int64_t *stream_id) {
     if (!sv || !cfg || !W0 || !stream_id) return ONMF_EINVAL;
     const onmf_config &c = *cfg;
-    // serving runs the mma h-solve (one CTA per chunk): AUTO or MMA only
+    // serving runs the mma h-solve (AUTO or MMA) with FP64 statistics
     if (c.F != sv->cfg.F || c.K < 1 || c.K > 128 || c.n_inner < 0 || !(c.eps >= 0.0) ||
         !(c.h_exponent > 0.0) || !(c.r >= 0.0 && c.r <= 1.0) ||
-        (c.hsolve != ONMF_HSOLVE_AUTO && c.hsolve != ONMF_HSOLVE_MMA))
+        (c.hsolve != ONMF_HSOLVE_AUTO && c.hsolve != ONMF_HSOLVE_MMA) ||
+        c.accumulate != ONMF_ACC_FP64 || c.reserved)
         return ONMF_EINVAL;
     StreamRec r;
     r.cfg = c;

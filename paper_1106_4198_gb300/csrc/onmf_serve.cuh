@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kThreads, 1) serve_stats_kernel(const ServeIte
         const int FT = s.Fp16 / 16, u = base + p - off[i];
         const int mt = u % FT, ks = u / FT;
         stats_unit<PREC>(s, mt, ks, it.Pg, it.Qg, it.Hg, it.betap, 0, it.n, smem, acc);
-        epilogue_unit(s, it.Wcm, it.A, it.B, it.Wn, it.rho, it.rho_on_new, mt, ks, acc);
+        epilogue_unit(s, it.Wcm, it.A, it.B, it.Wn, it.rho, it.rho_on_new, ACC_FP64, mt, ks, acc);
         __syncthreads();
     }
 }
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kThreads) serve_rescale_kernel(const ServeItem
         const int k = base + p - off[i];
         if (k < s.K) {
             normalize_columns<PREC>(s, it.normalize, it.Wn, it.Wcm, it.Wrm, it.Wimg, nullptr,
-                                    it.A, it.B, it.swpart, it.err, s_red8, k, s.K);
+                                    it.A, it.B, ACC_FP64, it.swpart, it.err, s_red8, k, s.K);
         } else {
             const double l = block_sum_ordered(it.loss_part, ceil_div(it.n, kTile), s_red);
             if (threadIdx.x == 0) {

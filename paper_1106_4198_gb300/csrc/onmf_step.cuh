@@ -184,38 +184,116 @@ __device__ __forceinline__ void stats_unit(const Shape &s, int mt, int ks, const
                         jb, je, smem, acc);
 }
 
+// ---- arithmetic of the running statistics A and B. Every entry is 8
+// bytes: a double (ACC_FP64), a float (ACC_FP32, second half zero) or a
+// float pair (hi, lo) with hi = fl(hi + lo) (ACC_FP32C), kept by
+// error-free transformations: TwoSum (Knuth, TAOCP vol. 2, 4.2.2), the exact
+// error of a product by one FMA, and FastTwoSum (Dekker 1971) to
+// renormalize. The explicit _rn intrinsics keep the compiler from fusing
+// or reassociating these steps.
+enum { ACC_FP64 = 0, ACC_FP32 = 1, ACC_FP32C = 2 };
+
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// x * c + d
+__device__ __forceinline__ DF df_mul_add(DF x, float c, float d) {
+    const float p = __fmul_rn(x.hi, c);
+    const float pe = __fmaf_rn(x.hi, c, -p);
+    const DF t = two_sum(p, d);
+    return fast_two_sum(t.hi, __fadd_rn(__fmaf_rn(x.lo, c, pe), t.lo));
+}
+
+// x + c * d
+__device__ __forceinline__ DF df_add_mul(DF x, float c, float d) {
+    const float p = __fmul_rn(c, d);
+    const float pe = __fmaf_rn(c, d, -p);
+    const DF t = two_sum(x.hi, p);
+    return fast_two_sum(t.hi, __fadd_rn(__fadd_rn(x.lo, pe), t.lo));
+}
+
+// x / c (the remainder of the leading quotient is exact by one FMA)
+__device__ __forceinline__ DF df_div(DF x, float c) {
+    const float q = __fdiv_rn(x.hi, c);
+    const float r = __fmaf_rn(-q, c, x.hi);
+    return fast_two_sum(q, __fdiv_rn(__fadd_rn(r, x.lo), c));
+}
+
+__device__ __forceinline__ DF df_load(const double *p) {
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    return {v.x, v.y};
+}
+
+__device__ __forceinline__ void df_store(double *p, DF x) {
+    *reinterpret_cast<float2 *>(p) = make_float2(x.hi, x.lo);
+}
+
 // A <- rho A + a, B <- rho B + b, W' = sqrt(A/B) for the tile's entries
-// (Algorithm 1; the past-scaling reading of rho unless rho_on_new).
+// (Algorithm 1; the past-scaling reading of rho unless rho_on_new), in the
+// arithmetic `accm` of A and B. The increments a, b are FP32 in every mode.
 static __device__ void epilogue_unit(const Shape &s, const float *Wcm, double *A, double *B,
-                                     float *Wn, double rho, int rho_on_new, int mt, int ks,
-                                     const float *acc) {
+                                     float *Wn, double rho, int rho_on_new, int accm, int mt,
+                                     int ks, const float *acc) {
     const int F = s.F, K = s.K;
+    const float rhof = (float)rho;
     for (int e = threadIdx.x; e < 512; e += kThreads) {
         const int kk = e >> 4, ff = e & 15;
         const int f = 16 * mt + ff, k = 32 * ks + kk;
         if (f >= F || k >= K) continue;
         const long long i = f + (long long)k * F;
         const float w = Wcm[i];
-        const double av = (double)(acc[ff * 32 + kk] * w * w);
-        const double bv = (double)acc[(16 + ff) * 32 + kk];
-        const double A0 = A[i], B0 = B[i];
-        double An, Bn;
-        if (rho_on_new) {
-            An = fma(rho, av, A0);
-            Bn = fma(rho, bv, B0);
+        const float af = acc[ff * 32 + kk] * w * w;
+        const float bf = acc[(16 + ff) * 32 + kk];
+        float An, Bn;  // the new A and B rounded to FP32, for W'
+        if (accm == ACC_FP64) {
+            const double av = (double)af, bv = (double)bf;
+            const double A0 = A[i], B0 = B[i];
+            double Ad, Bd;
+            if (rho_on_new) {
+                Ad = fma(rho, av, A0);
+                Bd = fma(rho, bv, B0);
+            } else {
+                Ad = fma(rho, A0, av);
+                Bd = fma(rho, B0, bv);
+            }
+            A[i] = Ad;
+            B[i] = Bd;
+            An = (float)Ad;
+            Bn = (float)Bd;
+        } else if (accm == ACC_FP32) {
+            const float A0 = df_load(A + i).hi, B0 = df_load(B + i).hi;
+            An = rho_on_new ? __fmaf_rn(rhof, af, A0) : __fmaf_rn(rhof, A0, af);
+            Bn = rho_on_new ? __fmaf_rn(rhof, bf, B0) : __fmaf_rn(rhof, B0, bf);
+            df_store(A + i, {An, 0.f});
+            df_store(B + i, {Bn, 0.f});
         } else {
-            An = fma(rho, A0, av);
-            Bn = fma(rho, B0, bv);
+            const DF A0 = df_load(A + i), B0 = df_load(B + i);
+            const DF Ad = rho_on_new ? df_add_mul(A0, rhof, af) : df_mul_add(A0, rhof, af);
+            const DF Bd = rho_on_new ? df_add_mul(B0, rhof, bf) : df_mul_add(B0, rhof, bf);
+            df_store(A + i, Ad);
+            df_store(B + i, Bd);
+            An = Ad.hi;
+            Bn = Bd.hi;
         }
-        A[i] = An;
-        B[i] = Bn;
-        Wn[i] = (Bn > 0.0) ? sqrtf(__fdiv_rn((float)An, (float)Bn)) : w;
+        Wn[i] = (Bn > 0.f) ? sqrtf(__fdiv_rn(An, Bn)) : w;
     }
 }
 
 static __device__ __forceinline__ void online_epilogue(const StepArgs &a, int mt, int ks,
                                                        double rho, const float *acc) {
-    epilogue_unit(a.s, a.Wcm, a.A, a.B, a.Wn, rho, a.rho_on_new, mt, ks, acc);
+    epilogue_unit(a.s, a.Wcm, a.A, a.B, a.Wn, rho, a.rho_on_new, a.acc, mt, ks, acc);
 }
 
 // Fixed-order sum of one float per thread over the CTA.
@@ -238,8 +316,8 @@ static __device__ void normalize_columns(const Shape &s, int normalize, const fl
                                   float *__restrict__ Wcm, float *__restrict__ Wrm,
                                   __nv_bfloat16 *__restrict__ Wimg,
                                   __nv_bfloat16 *__restrict__ Wrow, double *__restrict__ A,
-                                  double *__restrict__ B, float *__restrict__ swpart, int *err,
-                                  float *red8, int first, int stride) {
+                                  double *__restrict__ B, int accm, float *__restrict__ swpart,
+                                  int *err, float *red8, int first, int stride) {
     const int F = s.F, K = s.K;
     const int tid = threadIdx.x;
     for (int k = first; k < K; k += stride) {
@@ -275,9 +353,25 @@ static __device__ void normalize_columns(const Shape &s, int normalize, const fl
                     const float wv = w[u] * inv;
                     bad |= !isfinite(wv);
                     Wcm[i] = wv;
-                    if (A) {
-                        A[i] = av[u] * invd;
-                        B[i] = bv[u] * sd;
+                    if (A && sc) {
+                        if (accm == ACC_FP64) {
+                            A[i] = av[u] * invd;
+                            B[i] = bv[u] * sd;
+                        } else {
+                            // the same 8 bytes as a float pair
+                            DF a2, b2;
+                            memcpy(&a2, &av[u], 8);
+                            memcpy(&b2, &bv[u], 8);
+                            if (accm == ACC_FP32) {
+                                a2 = {__fdiv_rn(a2.hi, sum), 0.f};
+                                b2 = {__fmul_rn(b2.hi, sum), 0.f};
+                            } else {
+                                a2 = df_div(a2, sum);
+                                b2 = df_mul_add(b2, sum, 0.f);
+                            }
+                            df_store(A + i, a2);
+                            df_store(B + i, b2);
+                        }
                     }
                     if (PREC == PREC_FP32) {
                         Wrm[(long long)f * K + k] = wv;
@@ -404,7 +498,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
         if (!grid_sync(a.bar, G, epoch, a.err)) break;
         // ---- phase 3: column sums, rescale, images, loss
         normalize_columns<PREC>(s, a.normalize, a.Wn, a.Wcm, a.Wrm, a.Wimg, a.Wrow, a.A, a.B,
-                                a.swpart, a.err, s_red8, blockIdx.x, gridDim.x);
+                                a.acc, a.swpart, a.err, s_red8, blockIdx.x, gridDim.x);
         if (blockIdx.x == G - 1) {
             double l = block_sum_ordered(a.loss_part, ntiles, s_red);
             if (threadIdx.x == 0) *a.loss_sum += l;

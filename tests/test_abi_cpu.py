@@ -32,13 +32,14 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_config_layout_and_defaults():
-    assert ctypes.sizeof(onmf.onmf_config) == 64
+    assert ctypes.sizeof(onmf.onmf_config) == 72
     c = onmf.onmf_config_default(513, 100)
     assert (c.F, c.K, c.beta, c.n_inner) == (513, 100, 1000, 10)
     assert c.eps == 1e-12 and c.r == 1.0 and c.n_ref == 0
     assert c.h_exponent == 0.5 and c.normalize == 1 and c.rho_on_new == 0
     assert c.precision == onmf.ONMF_FP32 and c.hsolve == onmf.ONMF_HSOLVE_AUTO
-    assert onmf.onmf_abi_version() == 3
+    assert c.accumulate == onmf.ONMF_ACC_FP64 and c.reserved == 0
+    assert onmf.onmf_abi_version() == 4
 
 
 def test_status_strings():
@@ -49,7 +50,7 @@ def test_status_strings():
 @pytest.mark.parametrize("field,value", [
     ("F", 0), ("K", 0), ("K", 257), ("beta", 0), ("n_inner", -1),
     ("eps", -1.0), ("r", 1.5), ("h_exponent", 0.0), ("precision", 7),
-    ("hsolve", 9),
+    ("hsolve", 9), ("accumulate", 3), ("accumulate", -1), ("reserved", 1),
 ])
 def test_invalid_config_rejected_on_host(field, value):
     import numpy as np

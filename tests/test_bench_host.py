@@ -98,3 +98,22 @@ def test_serving_schedule_shape():
     target = bench.SPEEDUP / bench.HOP_S
     assert len(rates) >= 10
     assert 0.8 * target <= np.median(rates) <= 1.25 * target
+
+
+def test_accumulator_choice_rule():
+    """The fastest arithmetic of A, B whose drift against the FP64 sums is
+    within the bounds; FP64 whenever nothing else qualifies."""
+    def d(fp32_w, fp32_ms, comp_w, comp_ms, fp64_ms=45.8):
+        return {"fp64": {"ms_per_1e6_frames": fp64_ms},
+                "fp32": {"ms_per_1e6_frames": fp32_ms, "W_rel": fp32_w, "A_rel": fp32_w,
+                         "B_rel": fp32_w},
+                "fp32_compensated": {"ms_per_1e6_frames": comp_ms, "W_rel": comp_w,
+                                     "A_rel": comp_w * 1e-6, "B_rel": comp_w * 1e-6}}
+    # plain FP32 is fastest but drifts; the compensated pair does not
+    assert bench.choose_accumulate(d(9e-6, 45.0, 0.0, 45.2)) == "fp32_compensated"
+    # nothing qualifying is faster than FP64
+    assert bench.choose_accumulate(d(9e-6, 45.0, 0.0, 46.0)) == "fp64"
+    # every candidate drifts
+    assert bench.choose_accumulate(d(9e-6, 45.0, 5e-6, 45.1)) == "fp64"
+    # a plain FP32 run within the bounds is taken when it is the fastest
+    assert bench.choose_accumulate(d(1e-12, 44.0, 0.0, 45.2)) == "fp32"
