@@ -929,7 +929,9 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
     a.err = err;
     a.betap = betap;
     for (int it = 0; it < n_iter && e == cudaSuccess; ++it) {
-        // H step (its first X gives the objective of the previous iterate)
+        // one pass over the frames: the H step (its first X gives the
+        // objective of the previous iterate), then X from the updated H and
+        // the P, Q, H rows of the W step
         e = launch_prepare(sh, W, Wrm, Wimg, swp, q, Wrow);
         TileArgs h = a;
         h.n_in = 1;
@@ -938,20 +940,13 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
         h.H_out = H;
         h.ldh = K;
         h.loss_first = (it > 0 && obj_out) ? 1 : 0;
-        h.final_pass = 0;
+        h.final_pass = 1;
         h.loss_part = h.loss_first ? lp : nullptr;
+        h.Pg = Pg;
+        h.Qg = Qg;
+        h.Hg = Hg;
         if (e == cudaSuccess) e = run_tiles(h);
         if (e == cudaSuccess && h.loss_first) e = launch_sum(lp, ntiles, obj_d + it - 1, 0, q);
-        // P, Q, H rows from the updated H, then the W step
-        TileArgs r = a;
-        r.n_in = 0;
-        r.H_in = H;
-        r.ldh_in = K;
-        r.final_pass = 1;
-        r.Pg = Pg;
-        r.Qg = Qg;
-        r.Hg = Hg;
-        if (e == cudaSuccess) e = run_tiles(r);
         if (e == cudaSuccess)
             e = launch_batch_stats(sh, prec, Pg, Qg, Hg, betap, N, nchunks, part,
                                    std::min(units * nchunks, 2 * nsm), q);

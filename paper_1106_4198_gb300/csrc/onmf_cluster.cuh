@@ -207,7 +207,8 @@ static __device__ void hsolve_tile_cluster(const Shape &s, const ClLayout &L, in
     for (int it = 0;; ++it) {
         const bool last = (it == t.n_in);
         if (last && !t.final_pass) break;
-        const bool want_loss = (last && t.final_pass) || (it == 0 && t.loss_first);
+        const bool want_loss =
+            t.loss_slot && ((last && t.final_pass && !t.loss_first) || (it == 0 && t.loss_first));
         // ---- step A: x = eps + W h over this CTA's rows, ratios, [P | Q]^T
         for (int ml = warp; ml < nmt; ml += kWarps) {
             float d[4][4];

@@ -28,12 +28,26 @@ struct TileJob {
     float *H_out;      // K x frames (ldh) or NULL
     long long ldh;
     int n_in;
-    int loss_first;
+    int loss_first;  // loss of the first X only (a final pass then adds none)
     int final_pass;
     double *loss_slot;  // receives the tile's loss (or NULL)
     void *Pg, *Qg, *Hg;
     long long betap;
+    // mixed path only: the tile's frames are already on their way into
+    // shared memory (issued by the previous tile of this CTA), and the
+    // frames of the CTA's next tile to issue once this one no longer needs
+    // the buffer (NULL: none)
+    int v_staged = 0;
+    const float *Vnext = nullptr;
+    int nvalid_next = 0;
 };
+
+// Whether a tile's frames go to shared memory by one bulk copy: contiguous
+// rows (ld = F), a 16-byte aligned start and a multiple of 16 bytes.
+__host__ __device__ inline bool tile_bulk(const float *Vt, long long ldv, int F, int nvalid) {
+    const size_t bytes = (size_t)nvalid * F * 4;
+    return ldv == F && (reinterpret_cast<uintptr_t>(Vt) & 15) == 0 && bytes % 16 == 0;
+}
 
 // Compile-time tags, so that a hot loop is instantiated once per value of a
 // run-time switch that is uniform over the CTA (the exponent mode, whether
@@ -140,7 +154,8 @@ static __device__ void hsolve_tile_fp32(const Shape &s, float eps, float gamma, 
     for (int it = 0;; ++it) {
         const bool last = (it == t.n_in);
         if (last && !t.final_pass) break;
-        const bool want_loss = (last && t.final_pass) || (it == 0 && t.loss_first);
+        const bool want_loss =
+            t.loss_slot && ((last && t.final_pass && !t.loss_first) || (it == 0 && t.loss_first));
         auto finish_row_t = [&](auto loss_tag, int f, const float (&acc)[kTile]) {
             constexpr bool LOSS = decltype(loss_tag)::value != 0;
             float4 ya = *reinterpret_cast<const float4 *>(y_s + f * kTile);
@@ -392,14 +407,14 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
     float *sy = misc, *lw = misc + 8;
     const int FT = Fp / 16;
 
-    // ---- frame tile -> shared memory (bulk copy when contiguous and aligned)
+    // ---- frame tile -> shared memory (bulk copy when contiguous and aligned;
+    //      possibly issued already by the previous tile)
     {
         const size_t bytes = (size_t)t.nvalid * F * 4;
-        const bool bulk = (t.ldv == F) && ((reinterpret_cast<uintptr_t>(t.Vt) & 15) == 0) &&
-                          (bytes % 16 == 0);
+        const bool bulk = tile_bulk(t.Vt, t.ldv, F, t.nvalid);
         __syncthreads();
         if (bulk) {
-            if (tid == 0) {
+            if (tid == 0 && !t.v_staged) {
                 fence_proxy_async_shared();
                 mbar_arrive_expect_tx(vbar, (unsigned)bytes);
                 bulk_g2s(y_raw, t.Vt, (unsigned)bytes, vbar);
@@ -436,6 +451,13 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
         }
     }
     __syncthreads();
+    // the raw frames are no longer needed: the next tile's go into the buffer
+    if (t.Vnext && tid == 0) {
+        const unsigned nb = (unsigned)((size_t)t.nvalid_next * F * 4);
+        fence_proxy_async_shared();
+        mbar_arrive_expect_tx(vbar, nb);
+        bulk_g2s(y_raw, t.Vnext, nb, vbar);
+    }
 
     // ---- h in registers: warp w < KS owns k = 16w + {2tq, 2tq+1, 8+2tq, 9+2tq}, frame g
     float hr[4] = {0.f, 0.f, 0.f, 0.f};
@@ -470,7 +492,8 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
     for (int it = 0;; ++it) {
         const bool last = (it == t.n_in);
         if (last && !t.final_pass) break;
-        const bool want_loss = (last && t.final_pass) || (it == 0 && t.loss_first);
+        const bool want_loss =
+            t.loss_slot && ((last && t.final_pass && !t.loss_first) || (it == 0 && t.loss_first));
         // ---- step A: x = eps + W h (groups of kMtMax m16 tiles per warp;
         //      every ldmatrix of a k-step is issued before its MMAs)
         for (int mg = warp; mg < FT; mg += kWarps * kMtMax) {

@@ -99,8 +99,8 @@ struct TileArgs {
     long long ldh_in;
     float *H_out;         // K x n (ldh) or NULL
     long long ldh;
-    int loss_first;       // loss of the first X (before any h update)
-    int final_pass;       // compute X from the final h: loss, P/Q/Hg rows
+    int loss_first;       // loss of the first X (before any h update) only
+    int final_pass;       // compute X from the final h: P/Q/Hg rows, the loss unless loss_first
     const float *Wcm;
     const float *Wrm;
     const __nv_bfloat16 *Wimg;

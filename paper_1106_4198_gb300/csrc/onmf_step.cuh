@@ -541,6 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1) tile_kernel(TileArgs a) {
         ws.pending = true;
     }
     if (PREC == PREC_TC) stage_w_tc(a.s, tc_layout(a.s), a.Wimg, a.Wrow, a.Wcm, tbase, smem);
+    bool staged = false;  // this tile's frames were issued by the previous one
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         TileJob t;
         t.Vt = a.V + tile * TILE * a.ldv;
@@ -559,6 +560,20 @@ __global__ void __launch_bounds__(kThreads, 1) tile_kernel(TileArgs a) {
         t.Qg = a.Qg;
         t.Hg = a.Hg;
         t.betap = a.betap;
+        if constexpr (PREC == PREC_MIXED) {
+            // the mma h-solve copies the next tile's frames while it computes
+            const long long next = tile + gridDim.x;
+            t.v_staged = staged;
+            if (next < ntiles) {
+                const float *vn = a.V + next * TILE * a.ldv;
+                const int nn = (int)min((long long)TILE, a.n - next * TILE);
+                if (tile_bulk(vn, a.ldv, a.s.F, nn)) {
+                    t.Vnext = vn;
+                    t.nvalid_next = nn;
+                }
+            }
+            staged = t.Vnext != nullptr;
+        }
         if constexpr (PREC == PREC_TC)
             hsolve_tile_tc<KS>(a.s, a.eps, a.gamma, sw, t, smem, tbase, &mbar[2], &mbar[3], parA,
                                parB, &mbar[1], vpar, a.err);

@@ -359,7 +359,8 @@ __device__ void hsolve_tile_tc(const Shape &s, float eps, float gamma, float sw,
     for (int it = 0;; ++it) {
         const bool last = (it == t.n_in);
         if (last && !t.final_pass) break;
-        const bool want_loss = (last && t.final_pass) || (it == 0 && t.loss_first);
+        const bool want_loss =
+            t.loss_slot && ((last && t.final_pass && !t.loss_first) || (it == 0 && t.loss_first));
         // ---- step A on the tensor core: X = W H
         if (tid == 0) {
             for (int mt = 0; mt < L.nmt; ++mt) {
