@@ -873,7 +873,21 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int units = (sh.Fp16 / 16) * (sh.Kh / 32);
-    int nchunks = std::max(1, std::min<int>((2 * nsm + units - 1) / units, (int)((N + 255) / 256)));
+    // frame ranges per output tile of the statistics: the count (<= 16, at
+    // least 256 frames a range) whose units fill whole rounds of one CTA per
+    // SM best; ties go to fewer ranges
+    int nchunks = 1;
+    {
+        double best = -1.0;
+        for (int c = 1; c <= 16 && (c == 1 || (long long)c * 256 <= N); ++c) {
+            const long long U = (long long)units * c, rounds = (U + nsm - 1) / nsm;
+            const double eff = (double)U / (double)(rounds * nsm);
+            if (eff > best + 1e-9) {
+                best = eff;
+                nchunks = c;
+            }
+        }
+    }
     // scratch
     float *Wrm = nullptr, *swp = nullptr, *part = nullptr, *scale = nullptr;
     __nv_bfloat16 *Wimg = nullptr, *Wrow = nullptr;
@@ -949,7 +963,7 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
         if (e == cudaSuccess && h.loss_first) e = launch_sum(lp, ntiles, obj_d + it - 1, 0, q);
         if (e == cudaSuccess)
             e = launch_batch_stats(sh, prec, Pg, Qg, Hg, betap, N, nchunks, part,
-                                   std::min(units * nchunks, 2 * nsm), q);
+                                   std::min(units * nchunks, prec == PREC_FP32 ? 2 * nsm : nsm), q);
         if (e == cudaSuccess) e = launch_batch_wstep(sh, part, nchunks, W, q);
         if (e == cudaSuccess) e = launch_batch_normalize(sh, normalize, W, scale, err, q);
         if (e == cudaSuccess) e = launch_batch_scale_h(K, N, H, scale, q);

@@ -169,6 +169,101 @@ static __device__ void stats_unit_fp32(const Shape &s, int mt, int ks, const flo
     __syncthreads();
 }
 
+// The same sums over a long frame range (the batch W step): chunks of
+// kChunkP frames in two shared-memory stages, the copy of chunk c+1 in
+// flight while chunk c is multiplied. Same warp roles as stats_unit_mixed.
+constexpr int kChunkP = 448;
+constexpr int kHSP = kChunkP + 8;
+constexpr size_t kStageP = (size_t)2 * kChunkP * kPS * 2 + (size_t)32 * kHSP * 2;
+static_assert(2 * kStageP <= (size_t)2 * kChunk * kPS * 2 + (size_t)32 * kHS * 2,
+              "two pipelined stages fit where one chunk of stats_unit_mixed goes");
+
+static __device__ void stats_unit_mixed_pipe(const Shape &s, int mt, int ks,
+                                             const __nv_bfloat16 *Pg, const __nv_bfloat16 *Qg,
+                                             const __nv_bfloat16 *Hg, long long betap,
+                                             long long jb, long long je, unsigned char *smem,
+                                             float *acc) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, tq = lane & 3, mi = lane >> 3, r8 = lane & 7;
+    const int quarter = warp & 3, which = warp >> 2;
+    const int Fp = s.Fp16;
+    const int f0 = 16 * mt, k0 = 32 * ks;
+    auto P_of = [&](int st) { return reinterpret_cast<__nv_bfloat16 *>(smem + st * kStageP); };
+    auto Q_of = [&](int st) { return P_of(st) + kChunkP * kPS; };
+    auto H_of = [&](int st) { return P_of(st) + 2 * kChunkP * kPS; };
+    auto issue = [&](long long cb, int st) {
+        const int nf = (int)min((long long)kChunkP, je - cb);
+        const int nfr = (nf + 15) / 16 * 16;
+        __nv_bfloat16 *P_s = P_of(st), *Q_s = Q_of(st), *H_s = H_of(st);
+        for (int i = tid; i < nfr * 2; i += kThreads) {
+            const int jj = i >> 1, half = i & 1;
+            const bool ok = jj < nf;
+            const long long o = (cb + jj) * Fp + f0 + 8 * half;
+            cp_async16(P_s + jj * kPS + 8 * half, ok ? Pg + o : Pg, ok ? 16 : 0);
+            cp_async16(Q_s + jj * kPS + 8 * half, ok ? Qg + o : Qg, ok ? 16 : 0);
+        }
+        const int nch = nfr / 8;
+        for (int kk = warp; kk < 32; kk += kWarps)
+            for (int ch = lane; ch < nch; ch += 32) {
+                const int jj = 8 * ch;
+                const bool ok = jj < nf;
+                const __nv_bfloat16 *src = ok ? Hg + (long long)(k0 + kk) * betap + cb + jj : Hg;
+                cp_async16(H_s + kk * kHSP + jj, src, ok ? 16 : 0);
+            }
+        cp_async_commit();
+    };
+    float c[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) c[u][e] = 0.f;
+    const long long nchunk = (je - jb + kChunkP - 1) / kChunkP;
+    if (nchunk > 0) issue(jb, 0);
+    for (long long ci = 0; ci < nchunk; ++ci) {
+        const long long cb = jb + ci * kChunkP;
+        const int st = (int)(ci & 1);
+        if (ci + 1 < nchunk) {
+            issue(cb + kChunkP, st ^ 1);
+            cp_async_wait_group1();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        const int nf = (int)min((long long)kChunkP, je - cb);
+        const int nks = (nf + 15) / 16;
+        const int kb = quarter * nks / 4, ke = (quarter + 1) * nks / 4;
+        const __nv_bfloat16 *X_s = which ? Q_of(st) : P_of(st);
+        const __nv_bfloat16 *xrow = X_s + (r8 + 8 * (mi >> 1)) * kPS + 8 * (mi & 1);
+        const __nv_bfloat16 *hrow = H_of(st) + (r8 + 8 * (mi >> 1)) * kHSP + 8 * (mi & 1);
+        for (int ksi = kb; ksi < ke; ++ksi) {
+            uint32_t a[4], b0[4], b1[4];
+            ldmatrix_x4_trans(a, xrow + 16 * ksi * kPS);
+            ldmatrix_x4(b0, hrow + 16 * ksi);
+            ldmatrix_x4(b1, hrow + 16 * kHSP + 16 * ksi);
+            mma_bf16_16816(c[0], a, b0[0], b0[1]);
+            mma_bf16_16816(c[1], a, b0[2], b0[3]);
+            mma_bf16_16816(c[2], a, b1[0], b1[1]);
+            mma_bf16_16816(c[3], a, b1[2], b1[3]);
+        }
+        __syncthreads();
+    }
+    float *red = reinterpret_cast<float *>(smem);  // [8 warps][16][32]
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int ff = g + 8 * (e >> 1), kk = 8 * u + 2 * tq + (e & 1);
+            red[(warp * 16 + ff) * 32 + kk] = c[u][e];
+        }
+    __syncthreads();
+    for (int e = tid; e < 2 * 512; e += kThreads) {
+        const int w4 = e >> 9, rem = e & 511;
+        const float *r = red + (w4 * 4) * 512 + rem;
+        acc[w4 * 512 + rem] = ((r[0] + r[512]) + r[1024]) + r[1536];
+    }
+    __syncthreads();
+}
+
 template <int PREC>
 __device__ __forceinline__ void stats_unit(const Shape &s, int mt, int ks, const void *Pg,
                                            const void *Qg, const void *Hg, long long betap,
@@ -605,7 +700,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int mt = r % FT, ks = r / FT;
         const long long jb = c * per, je = min(N, jb + per);
         if (jb < je) {
-            stats_unit<PREC>(s, mt, ks, Pg, Qg, Hg, betap, jb, je, smem, acc);
+            if constexpr (PREC != PREC_FP32)
+                stats_unit_mixed_pipe(s, mt, ks, reinterpret_cast<const __nv_bfloat16 *>(Pg),
+                                      reinterpret_cast<const __nv_bfloat16 *>(Qg),
+                                      reinterpret_cast<const __nv_bfloat16 *>(Hg), betap, jb, je,
+                                      smem, acc);
+            else
+                stats_unit<PREC>(s, mt, ks, Pg, Qg, Hg, betap, jb, je, smem, acc);
         } else {
             for (int e = threadIdx.x; e < 1024; e += kThreads) acc[e] = 0.f;
             __syncthreads();
