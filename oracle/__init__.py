@@ -32,17 +32,23 @@ def _lib():
         lib.or_objective.argtypes = [_i, _i, _l, _p, _l, _p, _p, _d]
         lib.or_hsolve.restype = None
         lib.or_hsolve.argtypes = [_i, _i, _p, _p, _d, _d, _i, _p, _p, _p]
+        lib.or_hsolve_pen.restype = None
+        lib.or_hsolve_pen.argtypes = [_i, _i, _p, _p, _d, _d, _i, _d, _d, _p, _p, _p]
         lib.or_stats_step.restype = None
         lib.or_stats_step.argtypes = [_i, _i, _l, _p, _l, _p, _d, _d, _i, _i,
                                       _p, _p, _p, _p]
+        lib.or_stats_step_pen.restype = None
+        lib.or_stats_step_pen.argtypes = [_i, _i, _l, _p, _l, _p, _d, _d, _i, _i, _d,
+                                          _p, _p, _p, _p]
         lib.or_rho.restype = _d
         lib.or_rho.argtypes = [_d, _l, _l]
         lib.or_online_minibatch.restype = None
         lib.or_online_pass.restype = _l
         lib.or_online_pass.argtypes = [_i, _i, _l, _p, _l, _i, _i, _d, _d, _d,
-                                       _l, _i, _i, _i, _p, _p, _p, _p, _p, _p, _p]
+                                       _l, _i, _i, _i, _d, _d, _d, _p, _p, _p, _p, _p,
+                                       _p, _p]
         lib.or_project.restype = None
-        lib.or_project.argtypes = [_i, _i, _l, _p, _l, _p, _d, _d, _i, _p, _p]
+        lib.or_project.argtypes = [_i, _i, _l, _p, _l, _p, _d, _d, _i, _d, _d, _p, _p]
         lib.or_batch_h0.restype = None
         lib.or_batch_h0.argtypes = [_i, _i, _l, _p, _l, _p, _d, _p]
         lib.or_batch.restype = None
@@ -98,23 +104,31 @@ def objective(V, W, H, eps):
     return _lib().or_objective(F, K, N, _ptr(V), F, _ptr(W), _ptr(H), eps)
 
 
-def hsolve(W, v, eps=1e-12, gamma=0.5, n_in=10, h_init=None, trace=False):
-    """h-solve of one frame. W (K,F), v (F,). Returns h (K,) [, trace]."""
+def hsolve(W, v, eps=1e-12, gamma=0.5, n_in=10, h_init=None, trace=False,
+           h_penalty=0.0, h_penalty_a=1.0):
+    """h-solve of one frame. W (K,F), v (F,). Returns h (K,) [, trace].
+    h_penalty, h_penalty_a: lambda and a of the penalty lambda*log(a + sum h)
+    (Section 2.2, "Extensions"); the trace then includes it."""
     W = _f64(W)
     v = _f32(v).ravel()
     K, F = W.shape
     h = np.zeros(K)
     hi = _f64(h_init) if h_init is not None else None
     tr = np.zeros(n_in + 1) if trace else None
-    _lib().or_hsolve(F, K, _ptr(W), _ptr(v), eps, gamma, n_in, _ptr(hi),
-                     _ptr(h), _ptr(tr))
+    if h_penalty == 0.0:
+        _lib().or_hsolve(F, K, _ptr(W), _ptr(v), eps, gamma, n_in, _ptr(hi),
+                         _ptr(h), _ptr(tr))
+    else:
+        _lib().or_hsolve_pen(F, K, _ptr(W), _ptr(v), eps, gamma, n_in, h_penalty,
+                             h_penalty_a, _ptr(hi), _ptr(h), _ptr(tr))
     return (h, tr) if trace else h
 
 
 def stats_step(V, W, A, B, H, eps=1e-12, rho=1.0, normalize=True,
-               rho_on_new=False):
-    """Dictionary step given H. V (n,F); W, A, B (K,F); H (n,K).
-    Returns (W, A, B, loss) as new arrays."""
+               rho_on_new=False, w_penalty=0.0):
+    """Dictionary step given H. V (n,F); W, A, B (K,F); H (n,K); w_penalty:
+    mu of the dictionary penalty mu*sum W. Returns (W, A, B, loss) as new
+    arrays."""
     V = _f32(V)
     W = _f64(W).copy()
     A = _f64(A).copy()
@@ -123,9 +137,9 @@ def stats_step(V, W, A, B, H, eps=1e-12, rho=1.0, normalize=True,
     n, F = V.shape
     K = W.shape[0]
     loss = ctypes.c_double(0.0)
-    _lib().or_stats_step(F, K, n, _ptr(V), F, _ptr(H), eps, rho, int(normalize),
-                         int(rho_on_new), _ptr(W), _ptr(A), _ptr(B),
-                         ctypes.byref(loss))
+    _lib().or_stats_step_pen(F, K, n, _ptr(V), F, _ptr(H), eps, rho, int(normalize),
+                             int(rho_on_new), w_penalty, _ptr(W), _ptr(A), _ptr(B),
+                             ctypes.byref(loss))
     return W, A, B, loss.value
 
 
@@ -135,11 +149,13 @@ def rho(r, nb, n_ref):
 
 def online_pass(V, W, A=None, B=None, beta=50, n_in=5, eps=1e-12, gamma=0.5,
                 r=1.0, n_ref=0, normalize=True, rho_on_new=False, flush=True,
-                want_H=True, loss_sum=0.0, H_init=None):
+                want_H=True, loss_sum=0.0, H_init=None, h_penalty=0.0,
+                h_penalty_a=1.0, w_penalty=0.0):
     """One in-order pass of Algorithm 1. V (N,F), W (K,F) [A, B (K,F)];
     H_init (N,K): warm-restart start points of the frames' h-solves (None:
-    fresh restarts). Returns dict(W, A, B, H (N,K) or None, loss_sum,
-    mb_loss, frames)."""
+    fresh restarts); h_penalty, h_penalty_a, w_penalty: the penalties of
+    Section 2.2 ("Extensions"). Returns dict(W, A, B, H (N,K) or None,
+    loss_sum, mb_loss, frames)."""
     V = _f32(V)
     N, F = V.shape
     W = _f64(W).copy()
@@ -153,23 +169,25 @@ def online_pass(V, W, A=None, B=None, beta=50, n_in=5, eps=1e-12, gamma=0.5,
     ls = ctypes.c_double(loss_sum)
     done = _lib().or_online_pass(F, K, N, _ptr(V), F, beta, n_in, eps, gamma, r,
                                  n_ref, int(normalize), int(rho_on_new),
-                                 int(flush), _ptr(W), _ptr(A), _ptr(B), _ptr(Hi),
+                                 int(flush), h_penalty, h_penalty_a, w_penalty,
+                                 _ptr(W), _ptr(A), _ptr(B), _ptr(Hi),
                                  _ptr(H), ctypes.byref(ls), _ptr(mb))
     nmb_done = (done + beta - 1) // beta if flush else done // beta
     return dict(W=W, A=A, B=B, H=H, loss_sum=ls.value, mb_loss=mb[:nmb_done],
                 frames=done)
 
 
-def project(V, W, eps=1e-12, gamma=0.5, n_in=10):
-    """h-solve of every frame with W fixed. Returns (H (N,K), obj_sum)."""
+def project(V, W, eps=1e-12, gamma=0.5, n_in=10, h_penalty=0.0, h_penalty_a=1.0):
+    """h-solve of every frame with W fixed (penalized as in online_pass).
+    Returns (H (N,K), obj_sum) with obj_sum the d_IS part."""
     V = _f32(V)
     W = _f64(W)
     N, F = V.shape
     K = W.shape[0]
     H = np.zeros((N, K))
     s = ctypes.c_double(0.0)
-    _lib().or_project(F, K, N, _ptr(V), F, _ptr(W), eps, gamma, n_in, _ptr(H),
-                      ctypes.byref(s))
+    _lib().or_project(F, K, N, _ptr(V), F, _ptr(W), eps, gamma, n_in, h_penalty,
+                      h_penalty_a, _ptr(H), ctypes.byref(s))
     return H, s.value
 
 

@@ -29,6 +29,13 @@
  *     column with s_k = 0 are left unchanged.
  *   - the statistics a, b of a minibatch use the final h of each frame and the
  *     W that the h-solve used (Algorithm 1).
+ *   - penalties (Section 2.2, "Extensions", which names the two kinds but gives
+ *     no updates): on h, lambda * psi(sum_k h_k) with psi(s) = log(a + s),
+ *     majorized by its tangent (a linear term in the h update's denominator);
+ *     on W, the linear mu * sum W, which turns the dictionary step into
+ *     sqrt(A/(B + mu)). lambda = mu = 0 is the plain algorithm. The projection
+ *     (or_project) uses the same penalized h-solve; the batch functions are
+ *     unpenalized.
  *
  * Parity status: every function here is pinned by tests against closed
  * forms, brute force and identities (d_IS properties, K = 1 closed-form
@@ -100,15 +107,23 @@ double or_objective(int F, int K, int64_t N, const float *V, int64_t ldv,
 }
 
 /* h-solve of Algorithm 1, h_t <- argmin_h d_IS(eps + v_t, eps + W h), run as
- * n_in majorization-minimization steps from the fresh-restart point.
+ * n_in majorization-minimization steps from the fresh-restart point, with the
+ * optional penalty on h of Section 2.2 ("Extensions"), lambda * psi(sum_k h_k)
+ * with the concave increasing psi(s) = log(a + s). The concave penalty is
+ * majorized by its tangent at the current h, a linear term
+ * lambda * psi'(s~) * sum_k h_k, whose gradient joins the positive part of the
+ * IS gradient in the update's denominator:
+ *   h_k <- h_k * ((W^T p)_k / ((W^T q)_k + lambda / (a + s~)))^gamma,
+ * s~ = sum_k h_k before the step (lambda = 0: the plain update).
  *   v: F frame values; W: F x K; h: K outputs.
  *   h_init: if non-NULL, start from it (warm start / batch H step) instead of
  *           the fresh-restart point.
- *   trace: if non-NULL, n_in + 1 entries: d_IS(y, eps + W h) before the first
- *          step and after each step. */
-void or_hsolve(int F, int K, const double *W, const float *v, double eps,
-               double gamma, int n_in, const double *h_init, double *h,
-               double *trace) {
+ *   trace: if non-NULL, n_in + 1 entries: the objective d_IS(y, eps + W h)
+ *          (+ lambda * log(a + sum_k h_k)) before the first step and after
+ *          each step. */
+void or_hsolve_pen(int F, int K, const double *W, const float *v, double eps,
+                   double gamma, int n_in, double lambda, double a_pen,
+                   const double *h_init, double *h, double *trace) {
     double *y = (double *)malloc(sizeof(double) * F);
     double *x = (double *)malloc(sizeof(double) * F);
     double *p = (double *)malloc(sizeof(double) * F);
@@ -131,20 +146,24 @@ void or_hsolve(int F, int K, const double *W, const float *v, double eps,
             for (int k = 0; k < K; ++k) acc += W[f + (int64_t)k * F] * h[k];
             x[f] = eps + acc;
         }
-        if (trace) trace[it] = or_dis(y, x, F);
+        double hs = 0.0; /* s~ = sum_k h_k of the current h */
+        for (int k = 0; k < K; ++k) hs += h[k];
+        if (trace) trace[it] = or_dis(y, x, F) + (lambda > 0.0 ? lambda * log(a_pen + hs) : 0.0);
         if (it == n_in) break;
         /* p = y / x^2, q = 1 / x */
         for (int f = 0; f < F; ++f) {
             q[f] = 1.0 / x[f];
             p[f] = y[f] / (x[f] * x[f]);
         }
-        /* h_k <- h_k * ((W^T p)_k / (W^T q)_k)^gamma */
+        /* h_k <- h_k * ((W^T p)_k / ((W^T q)_k + lambda psi'(s~)))^gamma */
+        const double pen = lambda > 0.0 ? lambda / (a_pen + hs) : 0.0;
         for (int k = 0; k < K; ++k) {
             double num = 0.0, den = 0.0;
             for (int f = 0; f < F; ++f) {
                 num += W[f + (int64_t)k * F] * p[f];
                 den += W[f + (int64_t)k * F] * q[f];
             }
+            den += pen;
             if (den > 0.0) h[k] = h[k] * powg(num / den, gamma);
         }
     }
@@ -154,16 +173,23 @@ void or_hsolve(int F, int K, const double *W, const float *v, double eps,
     free(q);
 }
 
+/* The unpenalized h-solve (lambda = 0). */
+void or_hsolve(int F, int K, const double *W, const float *v, double eps,
+               double gamma, int n_in, const double *h_init, double *h,
+               double *trace) {
+    or_hsolve_pen(F, K, W, v, eps, gamma, n_in, 0.0, 1.0, h_init, h, trace);
+}
+
 /* One dictionary step of Algorithm 1 given the activations of a minibatch:
  *   X = eps + W H;  a = ((Y/X^2) H^T) o W^2;  b = (1/X) H^T;
  *   A <- rho*A + a, B <- rho*B + b   (or A <- A + rho*a with rho_on_new);
  *   W = sqrt(A/B);  then for each k: s = sum_f W_fk, W_:k /= s, A_:k /= s,
  *   B_:k *= s  (when normalize).
  * loss_out (may be NULL) receives sum_n d_IS(Y_n, X_n) over the minibatch. */
-void or_stats_step(int F, int K, int64_t n, const float *V, int64_t ldv,
-                   const double *H, double eps, double rho, int normalize,
-                   int rho_on_new, double *W, double *A, double *B,
-                   double *loss_out) {
+void or_stats_step_pen(int F, int K, int64_t n, const float *V, int64_t ldv,
+                       const double *H, double eps, double rho, int normalize,
+                       int rho_on_new, double mu, double *W, double *A, double *B,
+                       double *loss_out) {
     double *X = (double *)malloc(sizeof(double) * F * (size_t)(n > 0 ? n : 1));
     double *P = (double *)malloc(sizeof(double) * F * (size_t)(n > 0 ? n : 1));
     double *Q = (double *)malloc(sizeof(double) * F * (size_t)(n > 0 ? n : 1));
@@ -203,9 +229,12 @@ void or_stats_step(int F, int K, int64_t n, const float *V, int64_t ldv,
             }
         }
     }
-    /* W = sqrt(A/B) (Section 2.1); entries with B = 0 are kept */
+    /* W = sqrt(A/B) (Section 2.1), the minimizer of A/W + B W; with the
+     * linear dictionary penalty mu * sum W of Section 2.2 ("Extensions")
+     * the auxiliary function is A/W + (B + mu) W, minimized by
+     * sqrt(A/(B + mu)). Entries with B + mu = 0 are kept. */
     for (size_t i = 0; i < (size_t)F * K; ++i)
-        if (B[i] > 0.0) W[i] = sqrt(A[i] / B[i]);
+        if (B[i] + mu > 0.0) W[i] = sqrt(A[i] / (B[i] + mu));
     if (normalize) {
         for (int k = 0; k < K; ++k) {
             double s = 0.0;
@@ -225,6 +254,15 @@ void or_stats_step(int F, int K, int64_t n, const float *V, int64_t ldv,
     free(Q);
 }
 
+/* The unpenalized dictionary step (mu = 0). */
+void or_stats_step(int F, int K, int64_t n, const float *V, int64_t ldv,
+                   const double *H, double eps, double rho, int normalize,
+                   int rho_on_new, double *W, double *A, double *B,
+                   double *loss_out) {
+    or_stats_step_pen(F, K, n, V, ldv, H, eps, rho, normalize, rho_on_new, 0.0, W, A, B,
+                      loss_out);
+}
+
 /* Forgetting factor of "Scaling past data": rho = r^(beta'/n_ref), or 1 when
  * no reference length is given. */
 double or_rho(double r, int64_t nb, int64_t n_ref) {
@@ -238,6 +276,7 @@ double or_rho(double r, int64_t nb, int64_t n_ref) {
 void or_online_minibatch(int F, int K, int64_t nb, const float *V, int64_t ldv,
                          int n_in, double eps, double gamma, double r,
                          int64_t n_ref, int normalize, int rho_on_new,
+                         double lambda, double a_pen, double mu,
                          double *W, double *A, double *B, const double *H_init,
                          double *H_out, double *loss_out) {
     double *H = (double *)malloc(sizeof(double) * K * (size_t)(nb > 0 ? nb : 1));
@@ -245,11 +284,11 @@ void or_online_minibatch(int F, int K, int64_t nb, const float *V, int64_t ldv,
      * frame (Section 2.3, "Fresh or warm restarts") */
 #pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int64_t j = 0; j < nb; ++j)
-        or_hsolve(F, K, W, V + j * ldv, eps, gamma, n_in, H_init ? H_init + j * K : NULL,
-                  H + j * K, NULL);
+        or_hsolve_pen(F, K, W, V + j * ldv, eps, gamma, n_in, lambda, a_pen,
+                      H_init ? H_init + j * K : NULL, H + j * K, NULL);
     double rho = or_rho(r, nb, n_ref);
-    or_stats_step(F, K, nb, V, ldv, H, eps, rho, normalize, rho_on_new, W, A, B,
-                  loss_out);
+    or_stats_step_pen(F, K, nb, V, ldv, H, eps, rho, normalize, rho_on_new, mu, W, A, B,
+                      loss_out);
     if (H_out) memcpy(H_out, H, sizeof(double) * K * (size_t)nb);
     free(H);
 }
@@ -263,6 +302,7 @@ void or_online_minibatch(int F, int K, int64_t nb, const float *V, int64_t ldv,
 int64_t or_online_pass(int F, int K, int64_t N, const float *V, int64_t ldv,
                        int beta, int n_in, double eps, double gamma, double r,
                        int64_t n_ref, int normalize, int rho_on_new, int flush,
+                       double lambda, double a_pen, double mu,
                        double *W, double *A, double *B, const double *H_init,
                        double *H_out, double *loss_sum, double *mb_loss) {
     int64_t done = 0;
@@ -272,7 +312,7 @@ int64_t or_online_pass(int F, int K, int64_t N, const float *V, int64_t ldv,
         if (nb < beta && !flush) break;
         double l = 0.0;
         or_online_minibatch(F, K, nb, V + done * ldv, ldv, n_in, eps, gamma, r,
-                            n_ref, normalize, rho_on_new, W, A, B,
+                            n_ref, normalize, rho_on_new, lambda, a_pen, mu, W, A, B,
                             H_init ? H_init + done * K : NULL,
                             H_out ? H_out + done * K : NULL, &l);
         if (mb_loss) mb_loss[m] = l;
@@ -288,11 +328,12 @@ int64_t or_online_pass(int F, int K, int64_t N, const float *V, int64_t ldv,
 /* Projection with W fixed (held-out evaluation): the h-solve of every frame.
  * obj_sum (may be NULL): sum_n d_IS(eps + v_n, eps + W h_n). */
 void or_project(int F, int K, int64_t N, const float *V, int64_t ldv,
-                const double *W, double eps, double gamma, int n_in, double *H,
-                double *obj_sum) {
+                const double *W, double eps, double gamma, int n_in, double lambda,
+                double a_pen, double *H, double *obj_sum) {
 #pragma omp parallel for num_threads(g_threads) schedule(static)
     for (int64_t j = 0; j < N; ++j)
-        or_hsolve(F, K, W, V + j * ldv, eps, gamma, n_in, NULL, H + j * K, NULL);
+        or_hsolve_pen(F, K, W, V + j * ldv, eps, gamma, n_in, lambda, a_pen, NULL, H + j * K,
+                      NULL);
     if (obj_sum) *obj_sum = or_objective(F, K, N, V, ldv, W, H, eps) * (double)N;
 }
 

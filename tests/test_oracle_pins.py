@@ -523,3 +523,108 @@ def test_threads_do_not_change_results():
     b = oracle.online_pass(V, W0, beta=25, n_in=3)
     oracle.set_threads(1)
     assert np.array_equal(a["W"], b["W"]) and np.array_equal(a["H"], b["H"])
+
+
+# ------------------------------- P12: penalties (Section 2.2, "Extensions")
+# h penalty lambda * log(a + sum_k h_k) (psi concave increasing), dictionary
+# penalty mu * sum W. Pinned by the K = 1 stationary point in closed form, a
+# brute-force grid minimum at F = K = 2, the objective recomputed here, and the
+# minimizer property of the penalized dictionary step.
+
+
+def _pen_obj(v, W, h, lam, a):
+    """d_IS(v, W h) + lam * log(a + sum h) at eps = 0, evaluated with numpy."""
+    y = v.astype(np.float64)
+    x = W.T @ h
+    return float(np.sum(y / x - np.log(y / x) - 1.0) + lam * np.log(a + h.sum()))
+
+
+def test_penalized_hsolve_k1_closed_form():
+    """K = 1: the objective S/h + F log h + lam log(a + h) (S = sum_f v_f/w_f,
+    up to constants) is stationary where F h + lam h^2/(a + h) = S, i.e. at the
+    positive root of (F + lam) h^2 + (F a - S) h - S a = 0."""
+    r = rng(21)
+    F = 50
+    W = r.gamma(1.0, 1.0, size=(1, F)) + 0.05
+    v = rand_V(r, 1, F)[0]
+    S = float(np.sum(v.astype(np.float64) / W[0]))
+    for lam, a in ((0.5, 1.0), (5.0, 0.2), (50.0, 3.0)):
+        qa, qb, qc = F + lam, F * a - S, -S * a
+        hstar = (-qb + math.sqrt(qb * qb - 4 * qa * qc)) / (2 * qa)
+        h = oracle.hsolve(W, v, eps=0.0, gamma=0.5, n_in=400, h_penalty=lam, h_penalty_a=a)
+        assert abs(h[0] - hstar) <= 1e-10 * hstar, (lam, a, h[0], hstar)
+    # no penalty: the plain K = 1 solution S / F
+    h = oracle.hsolve(W, v, eps=0.0, gamma=0.5, n_in=400)
+    assert abs(h[0] - S / F) <= 1e-10 * S / F
+
+
+def test_penalized_hsolve_2x2_brute_force():
+    """F = K = 2 with the h penalty: the MM iterate reaches the minimum that
+    a fine grid search of the penalized objective finds."""
+    W = np.array([[1.0, 0.3], [0.2, 0.9]])
+    v = np.array([1.2, 0.8], dtype=np.float32)
+    lam, a = 0.6, 0.5
+    best, arg = np.inf, None
+    for x0 in np.linspace(1e-3, 2.0, 400):
+        for x1 in np.linspace(1e-3, 2.0, 400):
+            o = _pen_obj(v, W, np.array([x0, x1]), lam, a)
+            if o < best:
+                best, arg = o, (x0, x1)
+    h = oracle.hsolve(W, v, eps=0.0, gamma=0.5, n_in=5000, h_penalty=lam, h_penalty_a=a)
+    o = _pen_obj(v, W, h, lam, a)
+    assert o <= best + 1e-9
+    assert abs(h[0] - arg[0]) <= 0.01 and abs(h[1] - arg[1]) <= 0.01
+    # the penalty moves the minimum: the plain solution W^{-T} v is not it
+    h0 = np.linalg.solve(W.T, v.astype(np.float64))
+    assert _pen_obj(v, W, h0, lam, a) > o + 1e-6
+
+
+def test_penalized_hsolve_descent_and_trace():
+    """The tangent majorization of the concave penalty keeps every MM step a
+    descent step of the penalized objective; the oracle's trace is that
+    objective (recomputed here at the last iterate)."""
+    r = rng(22)
+    F, K = 64, 8
+    W = rand_W(r, K, F)
+    for lam, a in ((1.0, 1.0), (20.0, 0.1)):
+        for trial in range(5):
+            v = rand_V(r, 1, F)[0]
+            h, tr = oracle.hsolve(W, v, eps=0.0, gamma=0.5, n_in=60, trace=True,
+                                  h_penalty=lam, h_penalty_a=a)
+            assert np.all(np.diff(tr) <= 1e-12 * np.abs(tr[:-1]))
+            assert tr[-1] < tr[0]
+            assert abs(tr[-1] - _pen_obj(v, W, h, lam, a)) <= 1e-10 * abs(tr[-1])
+
+
+def test_h_penalty_shrinks_the_activations():
+    """A larger lambda gives a smaller sum_k h_k at the same frame."""
+    r = rng(23)
+    F, K = 64, 8
+    W = rand_W(r, K, F)
+    v = rand_V(r, 1, F)[0]
+    sums = [oracle.hsolve(W, v, eps=0.0, n_in=300, h_penalty=lam, h_penalty_a=1.0).sum()
+            for lam in (0.0, 1.0, 10.0, 100.0)]
+    assert all(s1 > s2 for s1, s2 in zip(sums[:-1], sums[1:])), sums
+
+
+def test_w_penalty_dictionary_step_minimizes_aux():
+    """With mu * sum W the dictionary step minimizes A/W + (B + mu) W
+    entrywise; mu = 0 is the plain step, bit for bit."""
+    r = rng(24)
+    F, K, n = 40, 5, 30
+    V = rand_V(r, n, F)
+    W = rand_W(r, K, F)
+    H = r.gamma(1.0, 1.0, size=(n, K)) + 0.01
+    A = r.gamma(1.0, 1.0, size=(K, F))
+    B = r.gamma(1.0, 1.0, size=(K, F))
+    mu = 0.7
+    W2, A2, B2, _ = oracle.stats_step(V, W, A, B, H, eps=1e-12, rho=1.0, normalize=False,
+                                      w_penalty=mu)
+    g = lambda w: A2 / w + (B2 + mu) * w
+    for d in (1e-4, 1e-2, 0.3):
+        assert np.all(g(W2) <= g(W2 * (1 + d)))
+        assert np.all(g(W2) <= g(W2 * (1 - d)))
+    Wp, Ap, Bp, lp = oracle.stats_step(V, W, A, B, H, eps=1e-12, rho=1.0, normalize=False)
+    Wz, Az, Bz, lz = oracle.stats_step(V, W, A, B, H, eps=1e-12, rho=1.0, normalize=False,
+                                       w_penalty=0.0)
+    assert np.array_equal(Wp, Wz) and np.array_equal(Ap, Az) and lp == lz
