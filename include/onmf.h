@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define ONMF_ABI_VERSION 4
+#define ONMF_ABI_VERSION 5
 
 typedef struct onmf_state onmf_state;
 
@@ -106,12 +106,22 @@ typedef struct {
     int32_t hsolve;     /* onmf_hsolve: h-solve kernel of the mixed path (0 = auto) */
     int32_t accumulate; /* onmf_accumulate: arithmetic of A and B (0 = FP64)    */
     int32_t reserved;   /* must be 0                                            */
+    /* Penalties (Section 2.2, "Extensions"; FP32 path only, 0 = none):
+     * h_penalty lambda >= 0 on each frame's h, lambda * log(a + sum_k h_k)
+     * with a = h_penalty_a > 0 (a concave increasing psi of the column sum);
+     * the h update becomes h_k <- h_k ((W^T p)_k / ((W^T q)_k +
+     * lambda / (a + sum_j h_j)))^gamma (tangent majorization of psi).
+     * w_penalty mu >= 0: mu * sum W, the dictionary step W = sqrt(A/(B + mu)). */
+    double h_penalty;
+    double h_penalty_a;
+    double w_penalty;
 } onmf_config;
 
 /* Fill *cfg with the defaults for an F x K problem: beta = 1000,
  * n_inner = 10, eps = 1e-12, r = 1, n_ref = 0, h_exponent = 0.5,
  * normalize = 1, rho_on_new = 0, precision = ONMF_FP32, hsolve = AUTO,
- * accumulate = FP64. */
+ * accumulate = FP64, no penalties (h_penalty = 0, h_penalty_a = 1,
+ * w_penalty = 0). */
 void onmf_config_default(onmf_config *cfg, int32_t F, int32_t K);
 
 /* Create an online state (Algorithm 1, "Input": W^(0), A^(0) = B^(0) = 0).
@@ -322,7 +332,7 @@ typedef struct {
 onmf_status onmf_server_create(const onmf_server_config *cfg, onmf_server **out);
 
 /* Open a stream with its own parameters (cfg->F must equal the server's F;
- * K <= 128; hsolve AUTO or MMA; accumulate FP64; cfg->beta is ignored:
+ * K <= 128; hsolve AUTO or MMA; accumulate FP64; no penalties; cfg->beta is ignored:
  * chunks are the minibatches) and initial
  * dictionary W0 (F x K, host). Returns its id; the stream is admitted now if
  * its state fits the budget, else it waits in FIFO order. */

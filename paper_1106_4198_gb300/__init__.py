@@ -59,6 +59,8 @@ class onmf_config(ctypes.Structure):
         ("normalize", ctypes.c_int32), ("rho_on_new", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("hsolve", ctypes.c_int32),
         ("accumulate", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("h_penalty", ctypes.c_double), ("h_penalty_a", ctypes.c_double),
+        ("w_penalty", ctypes.c_double),
     ]
 
 

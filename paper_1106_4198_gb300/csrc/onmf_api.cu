@@ -191,6 +191,9 @@ void onmf_config_default(onmf_config *c, int32_t F, int32_t K) {
     c->normalize = 1;
     c->rho_on_new = 0;
     c->precision = ONMF_FP32;
+    c->h_penalty = 0.0;
+    c->h_penalty_a = 1.0;
+    c->w_penalty = 0.0;
 }
 
 const char *onmf_status_string(onmf_status st) {
@@ -274,8 +277,14 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
         c.n_inner < 0 || c.n_inner > 100000 || !(c.eps >= 0.0) || !std::isfinite(c.eps) ||
         !(c.r >= 0.0 && c.r <= 1.0) || !(c.h_exponent > 0.0) || c.hsolve < 0 || c.hsolve > 3 ||
         (c.precision != ONMF_FP32 && c.precision != ONMF_MIXED) || c.accumulate < 0 ||
-        c.accumulate > 2 || c.reserved)
+        c.accumulate > 2 || c.reserved || !(c.h_penalty >= 0.0) || !std::isfinite(c.h_penalty) ||
+        !(c.h_penalty_a > 0.0) || !std::isfinite(c.h_penalty_a) || !(c.w_penalty >= 0.0) ||
+        !std::isfinite(c.w_penalty))
         return ONMF_EINVAL;
+    if ((c.h_penalty > 0.0 || c.w_penalty > 0.0) && c.precision != ONMF_FP32) {
+        snprintf(g_msg, sizeof g_msg, "penalties run on the FP32 path");
+        return ONMF_EINVAL;
+    }
     if (c.precision == ONMF_MIXED && c.F > 1024) {
         snprintf(g_msg, sizeof g_msg, "mixed precision supports F <= 1024");
         return ONMF_EINVAL;
@@ -426,6 +435,9 @@ static onmf_status run_minibatches(onmf_state *s, const float *V, long long ldv,
     a.normalize = c.normalize;
     a.rho_on_new = c.rho_on_new;
     a.acc = c.accumulate;
+    a.hpen = (float)c.h_penalty;
+    a.hpen_a = (float)c.h_penalty_a;
+    a.wpen = (float)c.w_penalty;
     a.V = V;
     a.ldv = ldv;
     a.nmb = nmb;
@@ -786,6 +798,8 @@ onmf_status onmf_project(onmf_state *s, const float *V, int64_t ldv, int64_t n, 
     if (obj_sum) CK(cudaMallocAsync((void **)&lp, (size_t)ntiles * 8, q));
     TileArgs a;
     memset(&a, 0, sizeof a);
+    a.hpen = (float)c.h_penalty;  // a penalized model projects with its penalty
+    a.hpen_a = (float)c.h_penalty_a;
     a.s = s->s;
     a.eps = (float)c.eps;
     a.gamma = (float)c.h_exponent;

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_cluster_kernel(StepArgs a,
         for (int u = blockIdx.x; u < nunits; u += G) {
             const int mt = u % FT, ks = u / FT;
             stats_unit<PREC_MIXED>(s, mt, ks, a.Pg, a.Qg, a.Hg, a.betap, 0, nb, smem, acc);
-            online_epilogue(a, mt, ks, rho, acc);
+            online_epilogue<PREC_MIXED>(a, mt, ks, rho, acc);
             __syncthreads();
         }
         if (!cl_grid_sync(a.bar, G, epoch, a.err, s_vote, vp, C, rank)) break;

@@ -40,6 +40,8 @@ struct TileJob {
     int v_staged = 0;
     const float *Vnext = nullptr;
     int nvalid_next = 0;
+    // FP32 path: the h penalty lambda * log(a + sum_k h_k) (lambda = 0: none)
+    float hpen = 0.f, hpen_a = 1.f;
 };
 
 // Whether a tile's frames go to shared memory by one bulk copy: contiguous
@@ -115,7 +117,7 @@ static __device__ void hsolve_tile_fp32(const Shape &s, float eps, float gamma, 
     float *q_s = p_s + (size_t)F * kTile;          // [F][8]
     float *h_s = q_s + (size_t)F * kTile;          // [Kh][8]
     float *red = h_s + (size_t)Kh * kTile;         // [8][128][16]
-    float *misc = red + kWarps * 128 * 16;         // sy[8], lw[8]
+    float *misc = red + kWarps * 128 * 16;         // sy[8], lw[8], hsum[8]
     float *sy = misc, *lw = misc + 8;
 
     // frame tile -> y = eps + v (y = 1 in frames past the end of the data)
@@ -223,6 +225,15 @@ static __device__ void hsolve_tile_fp32(const Shape &s, float eps, float gamma, 
         __syncthreads();
         if (last) break;
 
+        // the h penalty's tangent needs each frame's sum_k h_k before this
+        // step (warp j: frame j); read after the barrier below
+        float *hsum = misc + 16;
+        if (t.hpen > 0.f && warp < kTile) {
+            float a = 0.f;
+            for (int k = lane; k < K; k += 32) a += h_s[k * kTile + warp];
+            a = warp_sum(a);
+            if (lane == 0) hsum[warp] = a;
+        }
         // W^T p and W^T q: lanes take k, warps take contiguous row ranges
         const int fper = (F + kWarps - 1) / kWarps;
         const int f_lo = warp * fper, f_hi = min(F, f_lo + fper);
@@ -274,6 +285,8 @@ static __device__ void hsolve_tile_fp32(const Shape &s, float eps, float gamma, 
                             den += red[((size_t)w * 128 + kk) * 16 + 8 + j];
                         }
                         float h = h_s[k * kTile + j];
+                        // lambda psi'(s~) joins the denominator (Section 2.2, "Extensions")
+                        if (t.hpen > 0.f) den += __fdiv_rn(t.hpen, t.hpen_a + hsum[j]);
                         if (den > 0.f) h = scale_pow<GM>(h, __fdiv_rn(num, den), gamma);
                         h_s[k * kTile + j] = h;
                     }

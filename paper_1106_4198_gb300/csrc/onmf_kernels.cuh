@@ -58,6 +58,7 @@ struct StepArgs {
     int normalize;
     int rho_on_new;
     int acc;  // arithmetic of A and B (ACC_*)
+    float hpen, hpen_a, wpen;  // penalties (FP32 path): lambda, a, mu
     // frames
     const float *V;
     long long ldv;
@@ -110,6 +111,7 @@ struct TileArgs {
     long long betap;
     double *loss_part;    // [tiles] or NULL
     int *err;
+    float hpen, hpen_a;   // h penalty lambda, a (FP32 path; lambda = 0: none)
 };
 
 }  // namespace onmf

@@ -749,7 +749,7 @@ onmf_status onmf_server_open_stream(onmf_server *sv, const onmf_config *cfg, con
     if (c.F != sv->cfg.F || c.K < 1 || c.K > 128 || c.n_inner < 0 || !(c.eps >= 0.0) ||
         !(c.h_exponent > 0.0) || !(c.r >= 0.0 && c.r <= 1.0) ||
         (c.hsolve != ONMF_HSOLVE_AUTO && c.hsolve != ONMF_HSOLVE_MMA) ||
-        c.accumulate != ONMF_ACC_FP64 || c.reserved)
+        c.accumulate != ONMF_ACC_FP64 || c.reserved || c.h_penalty != 0.0 || c.w_penalty != 0.0)
         return ONMF_EINVAL;
     StreamRec r;
     r.cfg = c;

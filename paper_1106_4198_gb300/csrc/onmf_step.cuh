@@ -338,9 +338,11 @@ __device__ __forceinline__ void df_store(double *p, DF x) {
 // A <- rho A + a, B <- rho B + b, W' = sqrt(A/B) for the tile's entries
 // (Algorithm 1; the past-scaling reading of rho unless rho_on_new), in the
 // arithmetic `accm` of A and B. The increments a, b are FP32 in every mode.
+// WPEN: the dictionary penalty mu * sum W (FP32 path), W' = sqrt(A/(B + mu)).
+template <bool WPEN = false>
 static __device__ void epilogue_unit(const Shape &s, const float *Wcm, double *A, double *B,
                                      float *Wn, double rho, int rho_on_new, int accm, int mt,
-                                     int ks, const float *acc) {
+                                     int ks, const float *acc, float wpen = 0.f) {
     const int F = s.F, K = s.K;
     const float rhof = (float)rho;
     for (int e = threadIdx.x; e < 512; e += kThreads) {
@@ -382,13 +384,19 @@ static __device__ void epilogue_unit(const Shape &s, const float *Wcm, double *A
             An = Ad.hi;
             Bn = Bd.hi;
         }
-        Wn[i] = (Bn > 0.f) ? sqrtf(__fdiv_rn(An, Bn)) : w;
+        const float Bd = WPEN ? Bn + wpen : Bn;
+        Wn[i] = (Bd > 0.f) ? sqrtf(__fdiv_rn(An, Bd)) : w;
     }
 }
 
+template <int PREC>
 static __device__ __forceinline__ void online_epilogue(const StepArgs &a, int mt, int ks,
                                                        double rho, const float *acc) {
-    epilogue_unit(a.s, a.Wcm, a.A, a.B, a.Wn, rho, a.rho_on_new, a.acc, mt, ks, acc);
+    if constexpr (PREC == PREC_FP32)
+        epilogue_unit<true>(a.s, a.Wcm, a.A, a.B, a.Wn, rho, a.rho_on_new, a.acc, mt, ks, acc,
+                            a.wpen);
+    else
+        epilogue_unit(a.s, a.Wcm, a.A, a.B, a.Wn, rho, a.rho_on_new, a.acc, mt, ks, acc);
 }
 
 // Fixed-order sum of one float per thread over the CTA.
@@ -567,6 +575,10 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                 t.H_out = Hm;
                 t.ldh = a.ldh;
                 t.n_in = a.n_in;
+                if constexpr (PREC == PREC_FP32) {
+                    t.hpen = a.hpen;
+                    t.hpen_a = a.hpen_a;
+                }
                 t.loss_first = 0;
                 t.final_pass = 1;
                 t.loss_slot = a.loss_part + tile;
@@ -587,7 +599,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
         for (int u = blockIdx.x; u < nunits; u += G) {
             const int mt = u % FT, ks = u / FT;
             stats_unit<PREC>(s, mt, ks, a.Pg, a.Qg, a.Hg, a.betap, 0, nb, smem, acc);
-            online_epilogue(a, mt, ks, rho, acc);
+            online_epilogue<PREC>(a, mt, ks, rho, acc);
             __syncthreads();
         }
         if (!grid_sync(a.bar, G, epoch, a.err)) break;
@@ -651,6 +663,10 @@ __global__ void __launch_bounds__(kThreads, 1) tile_kernel(TileArgs a) {
         t.loss_first = a.loss_first;
         t.final_pass = a.final_pass;
         t.loss_slot = a.loss_part ? a.loss_part + tile : nullptr;
+        if constexpr (PREC == PREC_FP32) {
+            t.hpen = a.hpen;
+            t.hpen_a = a.hpen_a;
+        }
         t.Pg = a.Pg;
         t.Qg = a.Qg;
         t.Hg = a.Hg;

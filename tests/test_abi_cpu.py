@@ -32,14 +32,15 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_config_layout_and_defaults():
-    assert ctypes.sizeof(onmf.onmf_config) == 72
+    assert ctypes.sizeof(onmf.onmf_config) == 96
     c = onmf.onmf_config_default(513, 100)
     assert (c.F, c.K, c.beta, c.n_inner) == (513, 100, 1000, 10)
     assert c.eps == 1e-12 and c.r == 1.0 and c.n_ref == 0
     assert c.h_exponent == 0.5 and c.normalize == 1 and c.rho_on_new == 0
     assert c.precision == onmf.ONMF_FP32 and c.hsolve == onmf.ONMF_HSOLVE_AUTO
     assert c.accumulate == onmf.ONMF_ACC_FP64 and c.reserved == 0
-    assert onmf.onmf_abi_version() == 4
+    assert c.h_penalty == 0.0 and c.h_penalty_a == 1.0 and c.w_penalty == 0.0
+    assert onmf.onmf_abi_version() == 5
 
 
 def test_status_strings():
@@ -51,6 +52,8 @@ def test_status_strings():
     ("F", 0), ("K", 0), ("K", 257), ("beta", 0), ("n_inner", -1),
     ("eps", -1.0), ("r", 1.5), ("h_exponent", 0.0), ("precision", 7),
     ("hsolve", 9), ("accumulate", 3), ("accumulate", -1), ("reserved", 1),
+    ("h_penalty", -0.1), ("h_penalty_a", 0.0), ("w_penalty", -1.0),
+    ("h_penalty", float("nan")), ("w_penalty", float("inf")),
 ])
 def test_invalid_config_rejected_on_host(field, value):
     import numpy as np
@@ -62,6 +65,16 @@ def test_invalid_config_rejected_on_host(field, value):
                               ctypes.byref(h))
     assert st == 1  # ONMF_EINVAL
     assert not h.value
+
+
+def test_penalties_run_on_the_fp32_path_only():
+    import numpy as np
+    W0 = np.ones((4, 16), dtype=np.float32) / 16
+    for kw in (dict(h_penalty=0.5), dict(w_penalty=0.5)):
+        c = onmf.onmf_config_default(16, 4, precision=onmf.ONMF_MIXED, **kw)
+        h = ctypes.c_void_p()
+        st = onmf.lib().onmf_init(ctypes.byref(c), W0.ctypes.data, 0, None, ctypes.byref(h))
+        assert st == 1  # ONMF_EINVAL
 
 
 def test_mixed_precision_shape_limits():

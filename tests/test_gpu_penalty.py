@@ -1,0 +1,69 @@
+"""Penalized online IS-NMF (Section 2.2, "Extensions") on the FP32 path,
+through the C ABI, against the FP64 oracle: the h penalty
+lambda * log(a + sum_k h_k) (tangent majorization in the h update) and the
+dictionary penalty mu * sum W (W = sqrt(A/(B + mu))). FP32 bound 1e-5 on W,
+A, B, H and the loss, as for the plain FP32 path."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1106_4198_gb300 as onmf
+from helpers import cuda, problem, relerr
+from test_gpu_online import run_gpu
+
+pytestmark = pytest.mark.gpu
+FP32 = onmf.ONMF_FP32
+
+
+def oracle_pass(V, W0, beta, n_in, **kw):
+    oracle.set_threads(16)
+    o = oracle.online_pass(V, W0, beta=beta, n_in=n_in, **kw)
+    oracle.set_threads(1)
+    return o
+
+
+def errors(g, o):
+    return dict(W=relerr(g["W"], o["W"]), A=relerr(g["A"], o["A"]), B=relerr(g["B"], o["B"]),
+                H=relerr(g["H"], o["H"]),
+                loss=abs(g["loss_sum"] - o["loss_sum"]) / abs(o["loss_sum"]))
+
+
+@pytest.mark.parametrize("F,K,N,beta,n_in", [(129, 8, 2000, 50, 5), (513, 100, 1000, 1000, 10),
+                                             (65, 200, 96, 32, 3)])
+@pytest.mark.parametrize("lam,a,mu", [(0.5, 1.0, 0.0), (0.0, 1.0, 0.2), (4.0, 0.3, 0.05)])
+def test_penalized_pass_matches_oracle(F, K, N, beta, n_in, lam, a, mu):
+    """Includes K = 200 (two 128-wide k blocks of the FP32 h update, whose
+    penalty uses the frame sums taken before either block is updated)."""
+    V, W0 = problem(F, K, N, seed=41 + K)
+    pen = dict(h_penalty=lam, h_penalty_a=a, w_penalty=mu)
+    g = run_gpu(V, W0, beta=beta, n_inner=n_in, precision=FP32, **pen)
+    o = oracle_pass(V, W0, beta, n_in, **pen)
+    e = errors(g, o)
+    print("F=%d K=%d lam=%g a=%g mu=%g:" % (F, K, lam, a, mu), {k: "%.1e" % v for k, v in e.items()})
+    for k, v in e.items():
+        assert v <= 1e-5, (k, e)
+
+
+def test_penalized_projection_matches_oracle():
+    F, K, N = 257, 24, 300
+    V, W0 = problem(F, K, N, seed=45)
+    lam, a = 2.0, 0.5
+    m = onmf.OnlineISNMF(F, K, W0, precision=FP32, h_penalty=lam, h_penalty_a=a)
+    import torch
+    H = torch.empty((N, K), device="cuda")
+    m.project(cuda(V), H, n_inner=8)
+    m.close()
+    Ho, _ = oracle.project(V, W0, n_in=8, h_penalty=lam, h_penalty_a=a)
+    e = relerr(H.cpu().numpy(), Ho)
+    print("penalized projection H: %.1e" % e)
+    assert e <= 1e-5
+
+
+def test_h_penalty_shrinks_activations_on_gpu():
+    F, K, N = 129, 8, 400
+    V, W0 = problem(F, K, N, seed=46)
+    sums = []
+    for lam in (0.0, 2.0, 20.0):
+        g = run_gpu(V, W0, beta=50, n_inner=5, precision=FP32, h_penalty=lam)
+        sums.append(float(g["H"].sum()))
+    assert sums[0] > sums[1] > sums[2], sums
