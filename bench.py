@@ -50,6 +50,8 @@ def parse():
                    help="arithmetic of A, B on the mixed path; auto: measure the drift of "
                         "each over one pass and take the fastest within bounds")
     p.add_argument("--skip-e2e", action="store_true")
+    p.add_argument("--skip-batch-long", action="store_true",
+                   help="skip the batch cycles over the whole long stream")
     p.add_argument("--skip-cpu", action="store_true")
     p.add_argument("--cpu-sample-minibatches", type=int, default=120)
     p.add_argument("--skip-c2", action="store_true",
@@ -85,6 +87,7 @@ def init_dist(world, backend):
 
 
 DRIFT_W, DRIFT_AB = 1e-6, 1e-9
+BATCH_LONG_CYCLES = 3
 
 
 def choose_accumulate(drift):
@@ -305,9 +308,10 @@ def run_ours(args):
         per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
         total_ms = evs[0].elapsed_time(evs[-1])
         _, _, t, ls = m.stats()
+        W_end = m.W()
         m.close()
         return dict(ms=total_ms, per_step_ms=per, launches=launches,
-                    frames=t, loss=ls / max(t, 1), clocks=clk.summary())
+                    frames=t, loss=ls / max(t, 1), clocks=clk.summary(), W=W_end)
 
     mixed = timed_pass(onmf.ONMF_MIXED)
 
@@ -342,6 +346,46 @@ def run_ours(args):
         del host
 
     fp32 = None if args.skip_fp32 else timed_pass(onmf.ONMF_FP32)
+
+    # batch IS-NMF on the same long stream, which fits in HBM here: a few
+    # cycles over every frame, and both dictionaries scored alike (h of every
+    # frame re-solved with W fixed, mean d_IS per frame)
+    batch_long = None
+    if rank == 0 and not args.skip_batch_long:
+        Vall = torch.cat(chunks)
+        N_all = Vall.shape[0]
+        Wb = torch.as_tensor(W0, device=dev).contiguous()
+        Hb = torch.empty((N_all, K), device=dev)
+
+        def score_long(W):
+            sc = onmf.OnlineISNMF(F, K, W, stream=stream, beta=BETA, n_inner=N_IN,
+                                  precision=onmf.ONMF_MIXED)
+            o = sc.project(Vall, Hb, n_inner=N_IN, want_obj=True)
+            sc.close()
+            return o / N_all
+
+        s_init = score_long(W0)
+        s_online = score_long(mixed["W"])
+        onmf.nmf_batch_init_H(Vall, Wb, Hb, stream=stream)
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        obj = onmf.nmf_batch_step(Vall, Wb, Hb, n_iter=BATCH_LONG_CYCLES,
+                                  precision=onmf.ONMF_MIXED, stream=stream)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        batch_ms = b0.elapsed_time(b1)
+        s_batch = score_long(Wb.cpu().numpy())
+        batch_long = {
+            "frames": int(N_all), "cycles": BATCH_LONG_CYCLES,
+            "ms_per_cycle": batch_ms / BATCH_LONG_CYCLES,
+            "batch_own_objective_per_cycle": [float(x) for x in obj],
+            "score": "mean d_IS per frame, every frame's h re-solved with W fixed "
+                     "(%d iterations)" % N_IN,
+            "score_initial_W": s_init, "score_online_pass_W": s_online,
+            "score_batch_W": s_batch, "online_pass_ms": mixed["ms"]}
+        del Vall, Hb, Wb
+        torch.cuda.empty_cache()
 
     ms = max_over_ranks(dist, mixed["ms"], dev)
     total_frames = sum_over_ranks(dist, fps * args.steps, dev)
@@ -387,6 +431,7 @@ def run_ours(args):
             "gpu_launches": mixed["launches"],
             "clocks": mixed["clocks"],
             "accumulator_drift": drift,
+            "batch_long_stream": batch_long,
         }
     return out, dist
 
