@@ -329,6 +329,17 @@ def run_ours(args):
         for w in range(args.warmup):
             m.push(host[w % 2].numpy())
         m.sync()
+        # the host link's own rate on this machine: one step of frames copied from
+        # the same pinned buffer by the copy engine (e2e cannot beat it)
+        scratch = torch.empty_like(chunks[0])
+        l0e, l1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for rep in range(2):
+            l0e.record(stream)
+            scratch.copy_(host[0], non_blocking=True)
+            l1e.record(stream)
+            torch.cuda.synchronize()
+        link_gbs = fps * F * 4 / (l0e.elapsed_time(l1e) * 1e6)
+        del scratch
         res = np.zeros(1)
         barrier(dist, local)
         torch.cuda.synchronize()
@@ -342,7 +353,9 @@ def run_ours(args):
         m.close()
         e2e = {"value": sum_over_ranks(dist, fps * args.steps, dev) / e2e_s,
                "unit": "frames/s", "h2d_bytes_per_step": fps * F * 4,
-               "d2h_bytes_per_step": 8, "clocks": clk.summary()}
+               "d2h_bytes_per_step": 8, "clocks": clk.summary(),
+               "h2d_link_gbs": link_gbs,
+               "h2d_link_bound_frames_per_s": link_gbs * 1e9 / (F * 4)}
         del host
 
     fp32 = None if args.skip_fp32 else timed_pass(onmf.ONMF_FP32)

@@ -590,10 +590,14 @@ onmf_status onmf_push_frames(onmf_state *s, const float *V, int64_t ldv, int64_t
             CK(cudaEventRecord(s->ring_ev[b], s->stream));
         }
     }
-    long long i = 0;
+    // slot sizes ramp up within a push (8 minibatches, then x4 up to a full
+    // slot): the first copy, the one nothing hides, stays short, and each
+    // later copy is shorter than the step kernels of the slot before it
+    long long i = 0, cap = std::min(s->ring_frames, 8LL * c.beta);
     int b = 0;
     while (i < n) {
-        long long m = std::min(s->ring_frames, n - i);
+        long long m = std::min(cap, n - i);
+        cap = std::min(s->ring_frames, 4 * cap);
         CK(cudaStreamWaitEvent(s->copy_stream, s->ring_ev[b], 0));  // slot consumed
         if (ldv == c.F)
             CK(cudaMemcpyAsync(s->vring[b], V + i * ldv, (size_t)m * c.F * 4,
