@@ -106,7 +106,8 @@ typedef struct {
     int32_t hsolve;     /* onmf_hsolve: h-solve kernel of the mixed path (0 = auto) */
     int32_t accumulate; /* onmf_accumulate: arithmetic of A and B (0 = FP64)    */
     int32_t reserved;   /* must be 0                                            */
-    /* Penalties (Section 2.2, "Extensions"; FP32 path only, 0 = none):
+    /* Penalties (Section 2.2, "Extensions"; FP32 path and the mma h-solve of
+     * the mixed path, EINVAL with the others; 0 = none):
      * h_penalty lambda >= 0 on each frame's h, lambda * log(a + sum_k h_k)
      * with a = h_penalty_a > 0 (a concave increasing psi of the column sum);
      * the h update becomes h_k <- h_k ((W^T p)_k / ((W^T q)_k +

@@ -281,12 +281,19 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
         !(c.h_penalty_a > 0.0) || !std::isfinite(c.h_penalty_a) || !(c.w_penalty >= 0.0) ||
         !std::isfinite(c.w_penalty))
         return ONMF_EINVAL;
-    if ((c.h_penalty > 0.0 || c.w_penalty > 0.0) && c.precision != ONMF_FP32) {
-        snprintf(g_msg, sizeof g_msg, "penalties run on the FP32 path");
-        return ONMF_EINVAL;
-    }
+
     if (c.precision == ONMF_MIXED && c.F > 1024) {
         snprintf(g_msg, sizeof g_msg, "mixed precision supports F <= 1024");
+        return ONMF_EINVAL;
+    }
+    // the kernel choice and what it takes are host checks, before any device work
+    const int prec = pick_prec(c.precision, make_shape(c.F, c.K), c.hsolve);
+    if (prec < 0) {
+        snprintf(g_msg, sizeof g_msg, "h-solve %d does not support F=%d K=%d", c.hsolve, c.F, c.K);
+        return ONMF_EINVAL;
+    }
+    if ((c.h_penalty > 0.0 || c.w_penalty > 0.0) && prec != PREC_FP32 && prec != PREC_MIXED) {
+        snprintf(g_msg, sizeof g_msg, "penalties run on the FP32 and mma paths");
         return ONMF_EINVAL;
     }
     onmf_status st = ensure_configured();
@@ -295,12 +302,7 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
     s->cfg = c;
     s->s = make_shape(c.F, c.K);
     s->stream = reinterpret_cast<cudaStream_t>(stream);
-    s->prec = pick_prec(c.precision, s->s, c.hsolve);
-    if (s->prec < 0) {
-        snprintf(g_msg, sizeof g_msg, "h-solve %d does not support F=%d K=%d", c.hsolve, c.F, c.K);
-        delete s;
-        return ONMF_EINVAL;
-    }
+    s->prec = prec;
     const Shape &sh = s->s;
     const size_t FK = (size_t)c.F * c.K;
     s->betap = (c.beta + 15) / 16 * 16;

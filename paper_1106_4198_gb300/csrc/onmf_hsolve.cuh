@@ -364,7 +364,7 @@ __host__ __device__ inline MixedLayout mixed_layout(const Shape &s) {
     o += (size_t)s.Fp16 * kTile * 4;
     o = (o + 127) / 128 * 128;
     L.misc = o;
-    o += 256;
+    o += 768;  // frame sums, loss per warp, the penalty's per-warp h sums [2][8][8]
     L.total = o;
     return L;
 }
@@ -401,7 +401,7 @@ struct WStage {
 //           F (4 interleaved chains per n-tile); the accumulator fragment
 //           holds (W^T p)_k and (W^T q)_k of the same (frame, k), so the h
 //           update happens in registers (FP32 master h).
-template <int KS>
+template <int KS, bool PEN = false>
 static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma, float sw,
                                   const TileJob &t, unsigned char *smem, WStage &ws,
                                   uint64_t *vbar, unsigned &vparity, int *err) {
@@ -418,7 +418,12 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
     float *yT = reinterpret_cast<float *>(smem + L.yt);       // [Fp][8] y = eps + v
     float *misc = reinterpret_cast<float *>(smem + L.misc);
     float *sy = misc, *lw = misc + 8;
+    // PEN: per-warp sums over the warp's k of each frame's h, double-buffered
+    // by iteration parity ([2][kWarps][kTile]); the h penalty's tangent needs
+    // sum_k h_k of the h before each update (Section 2.2, "Extensions")
+    float *hpart = misc + 32;
     const int FT = Fp / 16;
+
 
     // ---- frame tile -> shared memory (bulk copy when contiguous and aligned;
     //      possibly issued already by the previous tile)
@@ -475,6 +480,14 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
     // ---- h in registers: warp w < KS owns k = 16w + {2tq, 2tq+1, 8+2tq, 9+2tq}, frame g
     float hr[4] = {0.f, 0.f, 0.f, 0.f};
     const bool hown = warp < KS;
+    // PEN: this warp's share of frame g's sum_k h_k (the four lanes of frame
+    // g add their entries; the tq = 0 lane writes)
+    auto put_hsum = [&](int buf) {
+        float v = (hr[0] + hr[1]) + (hr[2] + hr[3]);
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        if (tq == 0) hpart[(buf * kWarps + warp) * kTile + g] = v;
+    };
     if (hown) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -491,6 +504,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
         *reinterpret_cast<uint32_t *>(H_s + g * HLD + 16 * warp + 2 * tq) = pack_bf16(hr[0], hr[1]);
         *reinterpret_cast<uint32_t *>(H_s + g * HLD + 16 * warp + 8 + 2 * tq) =
             pack_bf16(hr[2], hr[3]);
+        if constexpr (PEN) put_hsum(0);
     }
     // W^T is first read by step A: its bulk copy (issued before the frame
     // tile) overlaps the frame sums and the start point above
@@ -605,7 +619,15 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
             }
             // n[0..1] = (W^T p)[k, k+1] of frame g, n[2..3] = (W^T q)[k, k+1]
             const float num[4] = {n0[0], n0[1], n1[0], n1[1]};
-            const float den[4] = {n0[2], n0[3], n1[2], n1[3]};
+            float den[4] = {n0[2], n0[3], n1[2], n1[3]};
+            if constexpr (PEN) {
+                // lambda psi'(s~) joins the denominator, s~ = sum_k h_k of frame g
+                float hs = 0.f;
+                for (int w = 0; w < KS; ++w) hs += hpart[((it & 1) * kWarps + w) * kTile + g];
+                const float pen = t.hpen > 0.f ? __fdiv_rn(t.hpen, t.hpen_a + hs) : 0.f;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) den[e] += pen;
+            }
             with_gamma_mode(gamma, [&](auto gm) {
                 constexpr int GM = decltype(gm)::value;
 #pragma unroll
@@ -616,6 +638,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
                 pack_bf16(hr[0], hr[1]);
             *reinterpret_cast<uint32_t *>(H_s + g * HLD + 16 * warp + 8 + 2 * tq) =
                 pack_bf16(hr[2], hr[3]);
+            if constexpr (PEN) put_hsum((it + 1) & 1);
         }
         __syncthreads();
     }

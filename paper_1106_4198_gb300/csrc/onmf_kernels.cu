@@ -153,6 +153,9 @@ const void *mixed_tile_lo(int prec, int ks);
 const void *mixed_tile_hi(int prec, int ks);
 const void *mixed_serve_lo(int ks);
 const void *mixed_serve_hi(int ks);
+// The penalized mma variants (1..8), in onmf_mixed_pen.cu.
+const void *mixed_online_pen(int ks);
+const void *mixed_tile_pen(int ks);
 
 // Cluster h-solve kernels, instantiated per k16-slab count in
 // onmf_cluster_lo.cu (1..8) and onmf_cluster_hi.cu (9..16).
@@ -273,12 +276,16 @@ const void *serve_rescale_fn(int prec) {
                              : (const void *)serve_rescale_kernel<PREC_MIXED>;
 }
 
-static const void *online_fn(int prec, int ks) {
+// pen: the penalized variant (the mma path only; FP32 takes penalties in its
+// one instantiation)
+static const void *online_fn(int prec, int ks, bool pen = false) {
     if (prec == PREC_FP32) return (const void *)online_kernel<PREC_FP32, 0>;
+    if (pen && prec == PREC_MIXED) return mixed_online_pen(ks);
     return ks <= 4 ? mixed_online_lo(prec, ks) : mixed_online_hi(prec, ks);
 }
-static const void *tile_fn(int prec, int ks) {
+static const void *tile_fn(int prec, int ks, bool pen = false) {
     if (prec == PREC_FP32) return (const void *)tile_kernel<PREC_FP32, 0>;
+    if (pen && prec == PREC_MIXED) return mixed_tile_pen(ks);
     return ks <= 4 ? mixed_tile_lo(prec, ks) : mixed_tile_hi(prec, ks);
 }
 static const void *bstats_fn(int prec) {
@@ -302,7 +309,11 @@ cudaError_t configure_kernels() {
             fns.push_back(online_fn(p, ks));
             fns.push_back(tile_fn(p, ks));
         }
-    for (int ks = 1; ks <= 8; ++ks) fns.push_back(serve_fn(PREC_MIXED, ks));
+    for (int ks = 1; ks <= 8; ++ks) {
+        fns.push_back(serve_fn(PREC_MIXED, ks));
+        fns.push_back(online_fn(PREC_MIXED, ks, true));
+        fns.push_back(tile_fn(PREC_MIXED, ks, true));
+    }
     for (int p = PREC_FP32; p <= PREC_MIXED; ++p) fns.push_back(serve_stats_fn(p));
     for (int ks = 1; ks <= 16; ++ks) {
         fns.push_back(cluster_online_fn(ks));
@@ -331,6 +342,10 @@ size_t max_dynamic_smem() {
             fns.push_back(online_fn(p, ks));
             fns.push_back(tile_fn(p, ks));
         }
+    for (int ks = 1; ks <= 8; ++ks) {
+        fns.push_back(online_fn(PREC_MIXED, ks, true));
+        fns.push_back(tile_fn(PREC_MIXED, ks, true));
+    }
     for (int ks = 1; ks <= 16; ++ks) {
         fns.push_back(cluster_online_fn(ks));
         fns.push_back(cluster_tile_fn(ks));
@@ -352,8 +367,9 @@ cudaError_t launch_online(const StepArgs &a, int prec, int grid, size_t smem,
     if (e != cudaSuccess) return e;
     StepArgs copy = a;
     void *args[] = {&copy};
-    e = cudaLaunchCooperativeKernel(online_fn(prec, a.s.Kp / 16), dim3(grid), dim3(kThreads),
-                                    args, smem, stream);
+    const bool pen = a.hpen > 0.f || a.wpen > 0.f;
+    e = cudaLaunchCooperativeKernel(online_fn(prec, a.s.Kp / 16, pen), dim3(grid),
+                                    dim3(kThreads), args, smem, stream);
     if (e == cudaSuccess) count_launch();
     return e;
 }
@@ -405,8 +421,8 @@ cudaError_t launch_tiles_cluster(const TileArgs &a, int C, int grid, size_t smem
 cudaError_t launch_tiles(const TileArgs &a, int prec, int grid, size_t smem, cudaStream_t stream) {
     TileArgs copy = a;
     void *args[] = {&copy};
-    cudaError_t e =
-        cudaLaunchKernel(tile_fn(prec, a.s.Kp / 16), dim3(grid), dim3(kThreads), args, smem, stream);
+    cudaError_t e = cudaLaunchKernel(tile_fn(prec, a.s.Kp / 16, a.hpen > 0.f), dim3(grid),
+                                     dim3(kThreads), args, smem, stream);
     if (e == cudaSuccess) count_launch();
     return e;
 }

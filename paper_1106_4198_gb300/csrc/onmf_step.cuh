@@ -389,10 +389,10 @@ static __device__ void epilogue_unit(const Shape &s, const float *Wcm, double *A
     }
 }
 
-template <int PREC>
+template <int PREC, bool PEN = false>
 static __device__ __forceinline__ void online_epilogue(const StepArgs &a, int mt, int ks,
                                                        double rho, const float *acc) {
-    if constexpr (PREC == PREC_FP32)
+    if constexpr (PREC == PREC_FP32 || PEN)
         epilogue_unit<true>(a.s, a.Wcm, a.A, a.B, a.Wn, rho, a.rho_on_new, a.acc, mt, ks, acc,
                             a.wpen);
     else
@@ -510,20 +510,22 @@ static __device__ double block_sum_ordered(const double *x, long long n, double 
     return r;
 }
 
-template <int PREC, int KS>
+template <int PREC, int KS, bool PEN = false>
 __device__ __forceinline__ void hsolve_tile(const Shape &s, float eps, float gamma,
                                             const float *Wcm, const float *Wrm, float sw,
                                             const TileJob &t, unsigned char *smem, WStage &ws,
                                             uint64_t *vbar, unsigned &vpar, int *err) {
     if constexpr (PREC == PREC_MIXED)
-        hsolve_tile_mixed<KS>(s, eps, gamma, sw, t, smem, ws, vbar, vpar, err);
+        hsolve_tile_mixed<KS, PEN>(s, eps, gamma, sw, t, smem, ws, vbar, vpar, err);
     else
         hsolve_tile_fp32(s, eps, gamma, Wcm, Wrm, sw, t, smem, err);
 }
 
 // ----------------------------------------------------- persistent online step
 
-template <int PREC, int KS>
+// PEN: the penalized variant of the mma path (Section 2.2, "Extensions");
+// the FP32 path takes the penalties in its one instantiation.
+template <int PREC, int KS, bool PEN = false>
 __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar[4];
@@ -575,7 +577,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                 t.H_out = Hm;
                 t.ldh = a.ldh;
                 t.n_in = a.n_in;
-                if constexpr (PREC == PREC_FP32) {
+                if constexpr (PREC == PREC_FP32 || PEN) {
                     t.hpen = a.hpen;
                     t.hpen_a = a.hpen_a;
                 }
@@ -590,7 +592,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                     hsolve_tile_tc<KS>(s, a.eps, a.gamma, sw, t, smem, tbase, &mbar[2], &mbar[3],
                                        parA, parB, &mbar[1], vpar, a.err);
                 else
-                    hsolve_tile<PREC, KS>(s, a.eps, a.gamma, a.Wcm, a.Wrm, sw, t, smem, ws,
+                    hsolve_tile<PREC, KS, PEN>(s, a.eps, a.gamma, a.Wcm, a.Wrm, sw, t, smem, ws,
                                           &mbar[1], vpar, a.err);
             }
         }
@@ -599,7 +601,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
         for (int u = blockIdx.x; u < nunits; u += G) {
             const int mt = u % FT, ks = u / FT;
             stats_unit<PREC>(s, mt, ks, a.Pg, a.Qg, a.Hg, a.betap, 0, nb, smem, acc);
-            online_epilogue<PREC>(a, mt, ks, rho, acc);
+            online_epilogue<PREC, PEN>(a, mt, ks, rho, acc);
             __syncthreads();
         }
         if (!grid_sync(a.bar, G, epoch, a.err)) break;
@@ -622,7 +624,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
 
 // ----------------------------------------------- projection / batch tiles
 
-template <int PREC, int KS>
+template <int PREC, int KS, bool PEN = false>
 __global__ void __launch_bounds__(kThreads, 1) tile_kernel(TileArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar[4];
@@ -663,7 +665,7 @@ __global__ void __launch_bounds__(kThreads, 1) tile_kernel(TileArgs a) {
         t.loss_first = a.loss_first;
         t.final_pass = a.final_pass;
         t.loss_slot = a.loss_part ? a.loss_part + tile : nullptr;
-        if constexpr (PREC == PREC_FP32) {
+        if constexpr (PREC == PREC_FP32 || PEN) {
             t.hpen = a.hpen;
             t.hpen_a = a.hpen_a;
         }
@@ -689,7 +691,7 @@ __global__ void __launch_bounds__(kThreads, 1) tile_kernel(TileArgs a) {
             hsolve_tile_tc<KS>(a.s, a.eps, a.gamma, sw, t, smem, tbase, &mbar[2], &mbar[3], parA,
                                parB, &mbar[1], vpar, a.err);
         else
-            hsolve_tile<PREC, KS>(a.s, a.eps, a.gamma, a.Wcm, a.Wrm, sw, t, smem, ws, &mbar[1],
+            hsolve_tile<PREC, KS, PEN>(a.s, a.eps, a.gamma, a.Wcm, a.Wrm, sw, t, smem, ws, &mbar[1],
                                   vpar, a.err);
     }
     if (PREC == PREC_TC) {

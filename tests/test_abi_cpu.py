@@ -67,14 +67,18 @@ def test_invalid_config_rejected_on_host(field, value):
     assert not h.value
 
 
-def test_penalties_run_on_the_fp32_path_only():
+def test_penalties_rejected_off_the_fp32_and_mma_paths():
+    """The tcgen05 and cluster h-solves take no penalties; the host refuses
+    the combination before any device work."""
     import numpy as np
-    W0 = np.ones((4, 16), dtype=np.float32) / 16
-    for kw in (dict(h_penalty=0.5), dict(w_penalty=0.5)):
-        c = onmf.onmf_config_default(16, 4, precision=onmf.ONMF_MIXED, **kw)
-        h = ctypes.c_void_p()
-        st = onmf.lib().onmf_init(ctypes.byref(c), W0.ctypes.data, 0, None, ctypes.byref(h))
-        assert st == 1  # ONMF_EINVAL
+    W0 = np.ones((8, 256), dtype=np.float32) / 256
+    for hs in (onmf.ONMF_HSOLVE_TC, onmf.ONMF_HSOLVE_CLUSTER):
+        for kw in (dict(h_penalty=0.5), dict(w_penalty=0.5)):
+            c = onmf.onmf_config_default(256, 8, precision=onmf.ONMF_MIXED, hsolve=hs, **kw)
+            h = ctypes.c_void_p()
+            st = onmf.lib().onmf_init(ctypes.byref(c), W0.ctypes.data, 0, None,
+                                      ctypes.byref(h))
+            assert st == 1  # ONMF_EINVAL
 
 
 def test_mixed_precision_shape_limits():

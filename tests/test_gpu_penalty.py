@@ -1,8 +1,9 @@
-"""Penalized online IS-NMF (Section 2.2, "Extensions") on the FP32 path,
-through the C ABI, against the FP64 oracle: the h penalty
-lambda * log(a + sum_k h_k) (tangent majorization in the h update) and the
-dictionary penalty mu * sum W (W = sqrt(A/(B + mu))). FP32 bound 1e-5 on W,
-A, B, H and the loss, as for the plain FP32 path."""
+"""Penalized online IS-NMF (Section 2.2, "Extensions") through the C ABI,
+against the FP64 oracle: the h penalty lambda * log(a + sum_k h_k) (tangent
+majorization in the h update) and the dictionary penalty mu * sum W
+(W = sqrt(A/(B + mu))). FP32 path: 1e-5 on W, A, B, H and the loss; the
+mma h-solve of the mixed path: the mixed bounds 1e-2 (W, A, B, H) and 1e-3
+(loss). The unpenalized kernels are separate instantiations."""
 import numpy as np
 import pytest
 
@@ -67,3 +68,40 @@ def test_h_penalty_shrinks_activations_on_gpu():
         g = run_gpu(V, W0, beta=50, n_inner=5, precision=FP32, h_penalty=lam)
         sums.append(float(g["H"].sum()))
     assert sums[0] > sums[1] > sums[2], sums
+
+
+@pytest.mark.parametrize("F,K,N,beta,n_in", [(129, 8, 2000, 50, 5), (513, 100, 1000, 1000, 10),
+                                             (65, 128, 96, 32, 3)])
+@pytest.mark.parametrize("lam,a,mu", [(0.5, 1.0, 0.0), (4.0, 0.3, 0.05)])
+def test_penalized_pass_mixed_mma(F, K, N, beta, n_in, lam, a, mu):
+    V, W0 = problem(F, K, N, seed=51 + K)
+    pen = dict(h_penalty=lam, h_penalty_a=a, w_penalty=mu)
+    g = run_gpu(V, W0, beta=beta, n_inner=n_in, precision=onmf.ONMF_MIXED,
+                hsolve=onmf.ONMF_HSOLVE_MMA, **pen)
+    o = oracle_pass(V, W0, beta, n_in, **pen)
+    e = errors(g, o)
+    print("mixed F=%d K=%d lam=%g a=%g mu=%g:" % (F, K, lam, a, mu),
+          {k: "%.1e" % v for k, v in e.items()})
+    assert e["loss"] <= 1e-3
+    for k in ("W", "A", "B", "H"):
+        assert e[k] <= 1e-2, (k, e)
+    # the activations follow the penalized oracle, not the unpenalized one
+    # (W moves by less than the bf16 error here, H by more)
+    ou = oracle_pass(V, W0, beta, n_in)
+    assert e["H"] < relerr(g["H"], ou["H"])
+
+
+def test_penalized_projection_mixed_mma():
+    import torch
+    F, K, N = 257, 24, 300
+    V, W0 = problem(F, K, N, seed=55)
+    lam, a = 2.0, 0.5
+    m = onmf.OnlineISNMF(F, K, W0, precision=onmf.ONMF_MIXED, hsolve=onmf.ONMF_HSOLVE_MMA,
+                         h_penalty=lam, h_penalty_a=a)
+    H = torch.empty((N, K), device="cuda")
+    m.project(cuda(V), H, n_inner=8)
+    m.close()
+    Ho, _ = oracle.project(V, W0, n_in=8, h_penalty=lam, h_penalty_a=a)
+    e = relerr(H.cpu().numpy(), Ho)
+    print("mixed penalized projection H: %.1e" % e)
+    assert e <= 1e-2
