@@ -9,11 +9,14 @@ L2 flush is needed between steps.
 
 Reported: frames/s of the mixed-precision path (value), the plain FP32 GPU
 path on the same workload, their objective agreement, the roofline of the
-step kernel, an end-to-end number through the C ABI with host buffers, the
-FP64 oracle on the host cores (cpu_baseline), SM clocks during the timed
-region, and our kernel launch count.
+step kernel, an end-to-end number through the C ABI with host buffers (and
+the host link's own rate), the FP64 oracle on the host cores
+(cpu_baseline), SM clocks during the timed region, the library's kernel
+launch count, the drift of each arithmetic of A and B, batch IS-NMF on the
+same stream, the objective-vs-time comparison, the parameter study and the
+serving replay.
 
---impl reference times the FP64 CPU oracle (the reference arm of this build).
+--impl reference times the FP64 CPU oracle as the reference arm.
 """
 import argparse
 import json
