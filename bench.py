@@ -362,6 +362,7 @@ def run_ours(args):
         del host
 
     fp32 = None if args.skip_fp32 else timed_pass(onmf.ONMF_FP32)
+    unfused = None if (args.skip_fp32 or rank != 0) else run_unfused_fp32(chunks, W0)
 
     # batch IS-NMF on the same long stream, which fits in HBM here: a few
     # cycles over every frame, and both dictionaries scored alike (h of every
@@ -437,6 +438,7 @@ def run_ours(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "fp32_value": (total_frames / (fp32["ms"] / 1e3)) if fp32 else None,
             "fp32_clocks": fp32["clocks"] if fp32 else None,
+            "fp32_unfused_torch": unfused,
             "speedup_vs_fp32": (fp32["ms"] / mixed["ms"]) if fp32 else None,
             "objective": mixed["loss"],
             "objective_fp32": fp32["loss"] if fp32 else None,
@@ -450,6 +452,58 @@ def run_ours(args):
             "batch_long_stream": batch_long,
         }
     return out, dist
+
+
+# ------------------------------------- unfused FP32 (cuBLAS + elementwise)
+
+
+def run_unfused_fp32(chunks, W0, n_mb=20, warm=3):
+    """The plain FP32 GPU form written out with PyTorch CUDA ops (cuBLAS SGEMM
+    with TF32 off, one elementwise kernel per step, FP32 everywhere): the
+    same Algorithm 1 step per minibatch, on the first n_mb minibatches of the
+    stream after `warm` untimed ones. A comparison leg of the benchmark, not
+    part of the library."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        V = chunks[0]
+        eps = 1e-12
+        W = torch.as_tensor(W0, device=V.device).t().contiguous()  # F x K
+        A = torch.zeros_like(W)
+        B = torch.zeros_like(W)
+
+        def minibatch(j, W, A, B):
+            Y = V[j * BETA:(j + 1) * BETA].t() + eps  # F x beta
+            H = (Y.sum(0) / W.sum()).expand(K, BETA).contiguous()
+            for _ in range(N_IN):
+                X = W @ H + eps
+                H = H * torch.sqrt((W.t() @ (Y / (X * X))) / (W.t() @ (1.0 / X)))
+            X = W @ H + eps
+            P, Q = Y / (X * X), 1.0 / X
+            A = A + (P @ H.t()) * W * W
+            B = B + Q @ H.t()
+            W = torch.sqrt(A / B)
+            s = W.sum(0)
+            return W / s, A / s, B * s
+
+        for j in range(warm):
+            W, A, B = minibatch(j, W, A, B)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for j in range(warm, warm + n_mb):
+            W, A, B = minibatch(j, W, A, B)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    return {"value": n_mb * BETA / (ms / 1e3), "unit": "frames/s",
+            "us_per_minibatch": 1e3 * ms / n_mb,
+            "sample": "%d minibatches after %d untimed ones" % (n_mb, warm),
+            "what": "Algorithm 1 in PyTorch FP32 ops: cuBLAS SGEMM (TF32 off) and "
+                    "elementwise kernels, about 8 launches per inner iteration"}
 
 
 # ----------------------------------------------------------------- serving
