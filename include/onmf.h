@@ -52,10 +52,12 @@ typedef enum {
 } onmf_status;
 
 typedef enum {
-    ONMF_FP32 = 0,  /* FP32 everywhere on the GPU (A, B accumulate in FP64)   */
+    ONMF_FP32 = 0,  /* FP32 everywhere on the GPU; A and B in the
+                       onmf_accumulate arithmetic (FP64 by default)          */
     ONMF_MIXED = 1  /* BF16 tensor-core products with FP32 accumulation, FP32
-                       ratios y/x^2 and 1/x, FP64 A and B; K <= 256, F <= 1024
-                       (K > 128: the cluster h-solve; serving: K <= 128) */
+                       ratios y/x^2 and 1/x, A and B as above; K <= 256,
+                       F <= 1024 (K > 128: the cluster h-solve; serving:
+                       K <= 128, FP64 A and B) */
 } onmf_precision;
 
 /* Kernel of the mixed-precision h-solve (no counterpart in the paper; the
