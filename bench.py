@@ -457,6 +457,27 @@ def run_ours(args):
 # ------------------------------------- unfused FP32 (cuBLAS + elementwise)
 
 
+def unfused_minibatch(Vmb, W, A, B, eps=1e-12, n_in=10):
+    """One step of Algorithm 1 written out with PyTorch ops on any device and
+    dtype: Vmb (n, F) frames, W, A, B (F, K). Fresh-restart start point
+    h0 = sum_f y_f / sum W for every k, n_in multiplicative h updates with
+    exponent 1/2, X from the final h, A += (P H^T) o W^2, B += Q H^T,
+    W = sqrt(A/B), then the L1 column rescale of W, A, B."""
+    import torch
+    Y = Vmb.t() + eps  # F x n
+    H = (Y.sum(0) / W.sum()).expand(W.shape[1], Y.shape[1]).contiguous()
+    for _ in range(n_in):
+        X = W @ H + eps
+        H = H * torch.sqrt((W.t() @ (Y / (X * X))) / (W.t() @ (1.0 / X)))
+    X = W @ H + eps
+    P, Q = Y / (X * X), 1.0 / X
+    A = A + (P @ H.t()) * W * W
+    B = B + Q @ H.t()
+    W = torch.sqrt(A / B)
+    s = W.sum(0)
+    return W / s, A / s, B * s
+
+
 def run_unfused_fp32(chunks, W0, n_mb=20, warm=3):
     """The plain FP32 GPU form written out with PyTorch CUDA ops (cuBLAS SGEMM
     with TF32 off, one elementwise kernel per step, FP32 everywhere): the
@@ -474,18 +495,7 @@ def run_unfused_fp32(chunks, W0, n_mb=20, warm=3):
         B = torch.zeros_like(W)
 
         def minibatch(j, W, A, B):
-            Y = V[j * BETA:(j + 1) * BETA].t() + eps  # F x beta
-            H = (Y.sum(0) / W.sum()).expand(K, BETA).contiguous()
-            for _ in range(N_IN):
-                X = W @ H + eps
-                H = H * torch.sqrt((W.t() @ (Y / (X * X))) / (W.t() @ (1.0 / X)))
-            X = W @ H + eps
-            P, Q = Y / (X * X), 1.0 / X
-            A = A + (P @ H.t()) * W * W
-            B = B + Q @ H.t()
-            W = torch.sqrt(A / B)
-            s = W.sum(0)
-            return W / s, A / s, B * s
+            return unfused_minibatch(V[j * BETA:(j + 1) * BETA], W, A, B, eps, N_IN)
 
         for j in range(warm):
             W, A, B = minibatch(j, W, A, B)

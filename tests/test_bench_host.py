@@ -117,3 +117,22 @@ def test_accumulator_choice_rule():
     assert bench.choose_accumulate(d(9e-6, 45.0, 5e-6, 45.1)) == "fp64"
     # a plain FP32 run within the bounds is taken when it is the fastest
     assert bench.choose_accumulate(d(1e-12, 44.0, 0.0, 45.2)) == "fp32"
+
+
+def test_unfused_comparison_leg_computes_algorithm_1():
+    """The benchmark's unfused FP32 leg (PyTorch ops) run in FP64 on the CPU
+    gives the oracle's W, A, B over a few minibatches (to rounding)."""
+    import torch
+    import oracle
+    import synth
+    F, K, beta, n_in = 33, 4, 8, 3
+    V = synth.spectrogram(F, K, 3 * beta, seed=3)
+    W0 = synth.init_dictionary(F, K)
+    Vt = torch.as_tensor(V, dtype=torch.float64)
+    W = torch.as_tensor(W0, dtype=torch.float64).t().contiguous()
+    A, B = torch.zeros_like(W), torch.zeros_like(W)
+    for j in range(3):
+        W, A, B = bench.unfused_minibatch(Vt[j * beta:(j + 1) * beta], W, A, B, 1e-12, n_in)
+    o = oracle.online_pass(V, W0, beta=beta, n_in=n_in)
+    for x, ref in ((W, o["W"]), (A, o["A"]), (B, o["B"])):
+        assert np.allclose(x.t().numpy(), ref, rtol=1e-12, atol=0)
