@@ -150,10 +150,12 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0,
  *       H_out must stay valid until then.
  * Asynchronous on the state's stream; V (if on the device) must stay valid
  * until the stream reaches this call. Host V goes through a two-slot device
- * ring filled on a private copy stream, so the copy of one slot overlaps the
- * steps on the other: pageable host V may be reused as soon as the call
- * returns, page-locked host V must stay unchanged until the state's stream
- * reaches this call (onmf_synchronize). n = 0 is a no-op.
+ * ring filled on a private copy stream, so the transfer of one slot overlaps
+ * the steps on the other (page-locked V is read by a small copy kernel
+ * through its mapped address, pageable V goes through the copy engine):
+ * pageable host V may be reused as soon as the call returns, page-locked
+ * host V must stay unchanged until the state's stream reaches this call
+ * (onmf_synchronize). n = 0 is a no-op.
  * Errors: EINVAL, ESTATE (sticky error), ECUDA; kernel-detected input errors
  * surface later as ENUMERIC. */
 onmf_status onmf_push_frames(onmf_state *s, const float *V, int64_t ldv,

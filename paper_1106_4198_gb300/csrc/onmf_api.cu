@@ -595,13 +595,27 @@ onmf_status onmf_push_frames(onmf_state *s, const float *V, int64_t ldv, int64_t
     // slot sizes ramp up within a push (8 minibatches, then x4 up to a full
     // slot): the first copy, the one nothing hides, stays short, and each
     // later copy is shorter than the step kernels of the slot before it
+    // pinned host memory mapped into the device's address space is pulled by
+    // a few CTAs on the SMs the step kernel leaves free; other host memory
+    // goes through the copy engine
+    const float *Vmap = nullptr;
+    {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, V) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            pa.devicePointer)
+            Vmap = reinterpret_cast<const float *>(pa.devicePointer);
+        else
+            cudaGetLastError();
+    }
     long long i = 0, cap = std::min(s->ring_frames, 8LL * c.beta);
     int b = 0;
     while (i < n) {
         long long m = std::min(cap, n - i);
         cap = std::min(s->ring_frames, 4 * cap);
         CK(cudaStreamWaitEvent(s->copy_stream, s->ring_ev[b], 0));  // slot consumed
-        if (ldv == c.F)
+        if (Vmap)
+            CK(launch_pull_rows(s->vring[b], c.F, Vmap + i * ldv, ldv, m, s->copy_stream));
+        else if (ldv == c.F)
             CK(cudaMemcpyAsync(s->vring[b], V + i * ldv, (size_t)m * c.F * 4,
                                cudaMemcpyHostToDevice, s->copy_stream));
         else

@@ -534,6 +534,46 @@ __global__ void __launch_bounds__(kThreads) index_rows_kernel(long long *dst, co
         dst[r] = idx ? idx[first + r] : first + r;
 }
 
+// Frames from mapped pinned host memory into a device ring slot, pulled by
+// the SMs (the step kernel leaves some free) instead of a copy engine: rows
+// of F floats, source leading dimension lds, destination dense. float4 with
+// four loads in flight per thread when both ends allow it.
+__global__ void __launch_bounds__(kThreads) pull_rows_kernel(float *__restrict__ dst, int F,
+                                                            const float *__restrict__ src,
+                                                            long long lds, long long n,
+                                                            int vec) {
+    const long long T = (long long)gridDim.x * kThreads;
+    const long long t0 = blockIdx.x * (long long)kThreads + threadIdx.x;
+    if (vec) {
+        const long long nv = n * F / 4;
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        for (long long i = t0; i < nv; i += 4 * T) {
+            float4 r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i + u * T < nv) r[u] = s4[i + u * T];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (i + u * T < nv) d4[i + u * T] = r[u];
+        }
+    } else {
+        const int lane = threadIdx.x & 31;
+        for (long long r = t0 >> 5; r < n; r += T >> 5)
+            for (int c = lane; c < F; c += 32) dst[r * F + c] = src[r * lds + c];
+    }
+}
+
+cudaError_t launch_pull_rows(float *dst, int F, const float *src, long long lds, long long n,
+                             cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    const int vec = lds == F && ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0 &&
+                    ((long long)n * F) % 4 == 0;
+    pull_rows_kernel<<<kPullCtas, kThreads, 0, stream>>>(dst, F, src, lds, n, vec);
+    count_launch();
+    return cudaGetLastError();
+}
+
 static int rows_grid(long long n) {
     const long long g = (n + kWarps - 1) / kWarps;
     return (int)(g < 4096 ? (g > 0 ? g : 1) : 4096);

@@ -69,6 +69,11 @@ cudaError_t launch_scatter_rows(float *dst, long long ld_dst, const float *src, 
                                 cudaStream_t stream);
 cudaError_t launch_index_rows(long long *dst, const long long *idx, long long first, long long n,
                               cudaStream_t stream);
+// Rows of F floats from mapped host memory (src, leading dimension lds) to a
+// dense device buffer, by kPullCtas CTAs.
+constexpr int kPullCtas = 16;
+cudaError_t launch_pull_rows(float *dst, int F, const float *src, long long lds, long long n,
+                             cudaStream_t stream);
 
 cudaError_t launch_wait_selftest(int which, unsigned *counter, int *err,
                                  unsigned long long *elapsed, cudaStream_t stream);

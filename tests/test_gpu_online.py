@@ -134,7 +134,8 @@ def test_host_input_ring_crosses_slots():
     """Host frames run through a two-slot device ring filled on a copy stream.
     beta = 2**18 makes one slot hold exactly one minibatch, so 2.5 minibatches
     reuse both slots and leave a ragged tail in staging. Pageable, page-locked
-    and strided host buffers (with host H_out) all equal the device path."""
+    (pulled by a copy kernel) and strided host buffers (with host H_out) all
+    equal the device path."""
     import torch
     F, K, beta = 33, 4, 1 << 18
     N = 5 * beta // 2
@@ -143,7 +144,8 @@ def test_host_input_ring_crosses_slots():
     pinned = torch.from_numpy(V).pin_memory()
     wide = np.zeros((N, F + 3), dtype=np.float32)
     wide[:, :F] = V
-    for Vh in (np.ascontiguousarray(V), pinned, wide[:, :F]):
+    wide_pinned = torch.from_numpy(wide).pin_memory()[:, :F]  # strided, page-locked
+    for Vh in (np.ascontiguousarray(V), pinned, wide[:, :F], wide_pinned):
         m = onmf.OnlineISNMF(F, K, W0, beta=beta, n_inner=3, precision=MIXED)
         H = np.zeros((N, K), dtype=np.float32)
         m.push(Vh, H)
