@@ -10,17 +10,19 @@
 // persistent single-stream kernel in the same order, so a chunk's result
 // does not depend on the batch it runs in.
 //
-// Host side: a worker thread forms batches from the queued chunks of
-// admitted streams that have nothing in flight (oldest chunk first), packs
-// their frames into a pinned staging buffer, copies them and a header of
-// the batch's layout to the device and launches the three phases on one of
-// `slots` CUDA streams, by default as one CUDA graph captured once per slot
-// and set of dictionary sizes (the kernels read the layout from the header,
-// so the graph serves every such batch unchanged); it records an event, and
-// completed batches are turned into
-// completion records with submit/done timestamps. Stream states live in a
-// device pool of budget_bytes reserved at creation (first-fit free list);
-// a stream that does not fit waits in FIFO order until others close.
+// Host side: onmf_server_submit copies a chunk's frames once, into a buffer
+// of a pinned host arena mapped into the device's address space. A worker
+// thread forms batches from the queued chunks of admitted streams that have
+// nothing in flight (oldest chunk first), copies the batch's item table and
+// a header of its layout to the device and launches, on one of `slots` CUDA
+// streams, the gather of the frames from the arena and the three phases, by
+// default as one CUDA graph captured once per slot and set of dictionary
+// sizes (the kernels read the layout from the header, so the graph serves
+// every such batch unchanged); it records an event, and completed batches
+// give their arena buffers back and are turned into completion records with
+// submit/done timestamps. Stream states live in a device pool of
+// budget_bytes reserved at creation (first-fit free list); a stream that
+// does not fit waits in FIFO order until others close.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
