@@ -41,7 +41,10 @@
  * forms, brute force and identities (d_IS properties, K = 1 closed-form
  * trajectory, block-diagonal W, F = K = 2 brute force, monotone descent,
  * the sqrt(A/B) minimizer, the online-equals-batch identity, power-of-two
- * scale equivariance, the noiseless fixed point, order invariance).
+ * scale equivariance, the noiseless fixed point, order invariance; for the
+ * penalties the K = 1 stationary point in closed form, an F = K = 2 grid
+ * minimum, descent of the penalized objective and the penalized dictionary
+ * step's minimizer).
  */
 #include <math.h>
 #include <stdint.h>
