@@ -132,3 +132,40 @@ def test_c_client_compiles_against_the_header():
                         os.path.join(root, "tests", "c", "onmf_c_smoke.c")],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_struct_layouts_match_the_header():
+    """Every field of the C ABI's structs sits at the same offset in the
+    ctypes binding as gcc places it from include/onmf.h."""
+    import shutil
+    import subprocess
+    import tempfile
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    structs = [onmf.onmf_config, onmf.onmf_server_config, onmf.onmf_completion,
+               onmf.onmf_server_stats]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "onmf.h"',
+             'int main(void) {']
+    for st in structs:
+        name = st.__name__
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in st._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines.append("return 0; }")
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "layout.c"), os.path.join(d, "layout")
+        open(src, "w").write("\n".join(lines))
+        subprocess.run(["gcc", "-std=c99", "-I" + os.path.join(root, "include"), src, "-o", exe],
+                       check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line.strip():
+            parts = line.split()
+            got[(parts[0], parts[1])] = int(parts[2])
+    for st in structs:
+        name = st.__name__
+        assert got[(name, "sizeof")] == ctypes.sizeof(st), name
+        for f, _ in st._fields_:
+            assert got[(name, f)] == getattr(st, f).offset, (name, f)
