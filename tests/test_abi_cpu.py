@@ -169,3 +169,26 @@ def test_struct_layouts_match_the_header():
         assert got[(name, "sizeof")] == ctypes.sizeof(st), name
         for f, _ in st._fields_:
             assert got[(name, f)] == getattr(st, f).offset, (name, f)
+
+
+def declared_arity():
+    """Parameter count of every function the header declares."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    arity = {}
+    for m in re.finditer(r"\b((?:onmf|nmf)_[A-Za-z0-9_]*)\s*\(([^;{]*?)\)\s*;", text):
+        params = m.group(2).strip()
+        arity[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    return arity
+
+
+def test_binding_argument_counts_match_the_header():
+    arity = declared_arity()
+    assert set(arity) == set(declared_functions())
+    L = onmf.lib()
+    checked = 0
+    for name, n in arity.items():
+        at = getattr(L, name).argtypes
+        if at is not None:
+            assert len(at) == n, (name, len(at), n)
+            checked += 1
+    assert checked >= 20
