@@ -35,7 +35,7 @@
 extern "C" {
 #endif
 
-#define ONMF_ABI_VERSION 5
+#define ONMF_ABI_VERSION 6
 
 typedef struct onmf_state onmf_state;
 
@@ -228,11 +228,35 @@ onmf_status onmf_project(onmf_state *s, const float *V, int64_t ldv, int64_t n,
  *   receive the objective (1/N) sum_n d_IS(eps+v_n, eps+W h_n) after each
  *   cycle (synchronizes when non-NULL).
  *   stream: cudaStream_t (NULL = legacy default stream).
- * Allocates its scratch for the call and frees it before returning. */
+ * Takes its scratch from the stream's memory pool for the call and returns
+ * it in stream order (cudaMallocAsync / cudaFreeAsync); to run cycles with
+ * no allocation at all, make a plan once (nmf_batch_plan_create) and call
+ * nmf_batch_plan_step. */
 onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H,
                            int32_t F, int32_t K, int64_t N, double eps,
                            double h_exponent, int32_t n_iter, int32_t normalize,
                            int32_t precision, double *obj_out, void *stream);
+
+/* Scratch of batch IS-NMF cycles (Section 2.1) for one shape, allocated once
+ * on the current device: the derived images of W, the P, Q, H operands of
+ * the W step for up to N_max frames, the split statistics, the loss slots.
+ * About (2 or 4 bytes) x N_max x (2 F + K) plus O(F K). Synchronizes.
+ * Destroy with nmf_batch_plan_destroy (synchronizes the device first). */
+typedef struct nmf_batch_plan nmf_batch_plan;
+onmf_status nmf_batch_plan_create(int32_t F, int32_t K, int64_t N_max,
+                                  int32_t precision, nmf_batch_plan **out);
+
+/* nmf_batch_step on a plan: the same cycles, kernels and results, for N <=
+ * N_max frames on the plan's device, with no allocation or free (the per-call
+ * objective buffer of nmf_batch_step lives in the plan). Asynchronous unless
+ * obj_out is given. Calls on one plan must not overlap on the GPU. */
+onmf_status nmf_batch_plan_step(nmf_batch_plan *plan, const float *V,
+                                int64_t ldv, float *W, float *H, int64_t N,
+                                double eps, double h_exponent, int32_t n_iter,
+                                int32_t normalize, double *obj_out,
+                                void *stream);
+
+void nmf_batch_plan_destroy(nmf_batch_plan *plan);
 
 /* Batch start point for H: every column gets the fresh-restart value
  * sum_f (eps + V_fn) / sum_{f,k} W_fk. V, W, H on the device. */
@@ -243,6 +267,19 @@ onmf_status nmf_batch_init_H(const float *V, int64_t ldv, const float *W,
 /* Size of the fixed device scratch array used by onmf_project_static. */
 #define ONMF_STATIC_SCRATCH_BYTES (4u << 20)
 
+/* Bits a kernel ORs into a device error word (onmf_project_static's err_out):
+ * INPUT    a frame value was negative, NaN or Inf (the h of that tile is
+ *          meaningless);
+ * NUMERIC  a result was not finite;
+ * TIMEOUT  a bounded device-side wait ran out (2 s) and the kernel left early,
+ *          so outputs may be unwritten;
+ * CONFIG   a kernel was launched with a shape it cannot run (cluster size) and
+ *          returned at entry without writing its outputs. */
+#define ONMF_DEVERR_INPUT 1
+#define ONMF_DEVERR_NUMERIC 2
+#define ONMF_DEVERR_TIMEOUT 4
+#define ONMF_DEVERR_CONFIG 8
+
 /* Projection (the h-solve of onmf_project, same kernels and results) for
  * callers that cannot allocate device memory: code running in a real-time
  * audio callback, where cudaMalloc may stall on a device-wide
@@ -251,26 +288,34 @@ onmf_status nmf_batch_init_H(const float *V, int64_t ldv, const float *W,
  *   W: F x K dictionary (device, ld F). V: F x n frames (device, ldv >= F).
  *   H_out: K x n (device, ldh >= K) or NULL. obj_sum: NULL or a device double
  *   that receives sum_n d_IS(eps + v_n, eps + W h_n). precision: onmf_precision.
+ *   err_out: NULL or a device int32 that the call clears and the kernels OR
+ *   their ONMF_DEVERR_* bits into; read it after the stream reaches the end
+ *   of the call (0: every output was written from valid input). With NULL
+ *   the bits go to the scratch array and are lost.
  *   stream: cudaStream_t (NULL = legacy default stream).
- * Allocates nothing: its scratch (the derived images of W, K column sums and
- * one double per 8 frames) lives in one static device array of
+ * Allocates nothing: its scratch lives in one static device array of
  * ONMF_STATIC_SCRATCH_BYTES (4 MiB) that every GPU loading the library keeps
  * until the process exits. A call whose scratch would not fit returns
- * ONMF_EINVAL: the need is about 4*F*K bytes (FP32) or 4*K*F bytes (mixed:
- * two bf16 images of W) for W, plus 4*K, plus n bytes for the loss slots, and it
- * must stay under 4 MiB - 256 B (F = 513, K = 100 leaves room for about
- * 3.9 million frames per call in FP32). All calls share the array: calls that run at the same
- * time on the GPU (different streams or threads) race and must be serialized
- * by the caller. The first call on each device looks up the array's device
- * address (and sets kernel attributes); make that first call before any
- * stream capture. Asynchronous; V is not checked for negative or non-finite
- * values here (the caller validates its input). */
+ * ONMF_EINVAL. With a(x) = x rounded up to a multiple of 256, Kp = K rounded
+ * up to 16 and Fp = F rounded up to 16, the need in bytes is
+ *   FP32 (any K):         a(4 F K) + a(4 K) + 8 ceil(n / 8);
+ *   mixed, K <= 128:      a(2 Kp (Fp + 8)) + a(4 K) + 8 ceil(n / 8)
+ *                         (with ONMF_HSOLVE=tc in the environment:
+ *                         a(2 Kp (Fp + 8)) + a(2 F Kp) + a(4 K) + 8 ceil(n / 16));
+ *   mixed, K > 128:       a(2 F Kp) + a(4 K) + 8 C ceil(n / 32), C the
+ *                         cluster size (1, 2, 4 or 8; at most 8);
+ * and it must not exceed ONMF_STATIC_SCRATCH_BYTES - 256 (F = 513, K = 100
+ * leaves room for about 4 million frames per call in FP32). All calls share
+ * the array: calls that run at the same time on the GPU (different streams or
+ * threads) race and must be serialized by the caller. The first call on each
+ * device looks up the array's device address (and sets kernel attributes);
+ * make that first call before any stream capture. Asynchronous. */
 onmf_status onmf_project_static(const float *W, int32_t F, int32_t K,
                                 const float *V, int64_t ldv, int64_t n,
                                 float *H_out, int64_t ldh, double eps,
                                 double h_exponent, int32_t n_inner,
                                 int32_t precision, double *obj_sum,
-                                void *stream);
+                                int32_t *err_out, void *stream);
 
 /* Release the state and everything the library allocated for it. */
 void onmf_destroy(onmf_state *s);

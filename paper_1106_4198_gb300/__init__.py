@@ -24,6 +24,7 @@ __all__ = [
     "onmf_project", "nmf_batch_step", "nmf_batch_init_H", "onmf_destroy",
     "onmf_status_string", "onmf_kernel_launches", "onmf_abi_version",
     "onmf_project_static", "onmf_push_frames_warm", "onmf_autotune", "OnlineISNMF", "EXPORTED",
+    "BatchPlan",
 ]
 
 ONMF_FP32 = 0
@@ -33,6 +34,7 @@ ONMF_HSOLVE_AUTO, ONMF_HSOLVE_MMA, ONMF_HSOLVE_TC, ONMF_HSOLVE_CLUSTER = 0, 1, 2
 HSOLVE_NAMES = {0: "auto", 1: "mma", 2: "tc", 3: "cluster"}
 ONMF_SERVE_GRAPH, ONMF_SERVE_DIRECT = 0, 1
 ONMF_ACC_FP64, ONMF_ACC_FP32, ONMF_ACC_FP32_COMP = 0, 1, 2
+ONMF_DEVERR_INPUT, ONMF_DEVERR_NUMERIC, ONMF_DEVERR_TIMEOUT, ONMF_DEVERR_CONFIG = 1, 2, 4, 8
 ACC_NAMES = {0: "fp64", 1: "fp32", 2: "fp32_compensated"}
 ONMF_ETIMEOUT = 6
 
@@ -47,6 +49,7 @@ EXPORTED = [
     "onmf_server_poll", "onmf_server_get_W", "onmf_server_close_stream",
     "onmf_server_get_stats", "onmf_server_destroy", "onmf_selftest_wait",
     "onmf_push_frames_warm", "onmf_autotune", "onmf_server_submit_many",
+    "nmf_batch_plan_create", "nmf_batch_plan_step", "nmf_batch_plan_destroy",
 ]
 
 
@@ -138,8 +141,13 @@ def lib():
                                  _i32, _i32, _i32, _vp, _vp]
     L.nmf_batch_init_H.argtypes = [_vp, _i64, _vp, _vp, _i32, _i32, _i64, _d,
                                    _vp]
+    L.nmf_batch_plan_create.argtypes = [_i32, _i32, _i64, _i32, ctypes.POINTER(_vp)]
+    L.nmf_batch_plan_step.argtypes = [_vp, _vp, _i64, _vp, _vp, _i64, _d, _d, _i32,
+                                      _i32, _vp, _vp]
+    L.nmf_batch_plan_destroy.argtypes = [_vp]
+    L.nmf_batch_plan_destroy.restype = None
     L.onmf_project_static.argtypes = [_vp, _i32, _i32, _vp, _i64, _i64, _vp,
-                                      _i64, _d, _d, _i32, _i32, _vp, _vp]
+                                      _i64, _d, _d, _i32, _i32, _vp, _vp, _vp]
     L.onmf_destroy.argtypes = [_vp]
     L.onmf_destroy.restype = None
     L.onmf_server_create.argtypes = [ctypes.POINTER(onmf_server_config),
@@ -169,7 +177,8 @@ def lib():
                  "onmf_server_open_stream", "onmf_server_submit", "onmf_server_poll",
                  "onmf_server_get_W", "onmf_server_close_stream",
                  "onmf_server_get_stats", "onmf_selftest_wait", "onmf_push_frames_warm",
-                 "onmf_autotune", "onmf_server_submit_many"):
+                 "onmf_autotune", "onmf_server_submit_many", "nmf_batch_plan_create",
+                 "nmf_batch_plan_step"):
         getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -375,18 +384,55 @@ def nmf_batch_step(V, W, H, eps=1e-12, h_exponent=0.5, n_iter=1, normalize=1,
     return np.array(obj[:n_iter]) if want_obj else None
 
 
+class BatchPlan:
+    """Owner of an nmf_batch_plan: batch cycles of one shape (F, K, at most
+    N_max frames, precision) with the scratch allocated once."""
+
+    def __init__(self, F, K, N_max, precision=ONMF_FP32):
+        self.F, self.K, self.N_max, self.precision = F, K, N_max, precision
+        h = _vp()
+        _check(lib().nmf_batch_plan_create(F, K, N_max, precision, ctypes.byref(h)),
+               "nmf_batch_plan_create")
+        self._h = h
+
+    def step(self, V, W, H, eps=1e-12, h_exponent=0.5, n_iter=1, normalize=1,
+             want_obj=True, stream=None):
+        """nmf_batch_step on device tensors V (N, F), W (K, F), H (N, K)."""
+        pv, ldv = _ptr_ld(V, V.shape[1])
+        obj = (ctypes.c_double * max(1, n_iter))() if want_obj else None
+        _check(lib().nmf_batch_plan_step(self._h, pv, ldv, W.data_ptr(), H.data_ptr(),
+                                         V.shape[0], eps, h_exponent, n_iter, normalize,
+                                         obj, _stream_handle(stream)),
+               "nmf_batch_plan_step")
+        return np.array(obj[:n_iter]) if want_obj else None
+
+    def close(self):
+        if self._h:
+            lib().nmf_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def onmf_project_static(W, V, H_out=None, obj_sum=None, eps=1e-12,
                         h_exponent=0.5, n_inner=10, precision=ONMF_FP32,
-                        stream=None):
+                        err_out=None, stream=None):
     """Allocation-free projection: device tensors W (K, F), V (n, F), H_out
-    (n, K) or None, obj_sum a 1-element float64 device tensor or None."""
+    (n, K) or None, obj_sum a 1-element float64 device tensor or None,
+    err_out a 1-element int32 device tensor (receives the ONMF_DEVERR_* bits
+    the kernels raise) or None."""
     K, F = W.shape
     pv, ldv = _ptr_ld(V, F)
     ph, ldh = _ptr_ld(H_out, K) if H_out is not None else (None, K)
     po = obj_sum.data_ptr() if obj_sum is not None else None
+    pe = err_out.data_ptr() if err_out is not None else None
     _check(lib().onmf_project_static(W.data_ptr(), F, K, pv, ldv, V.shape[0], ph,
                                      ldh, eps, h_exponent, n_inner, precision,
-                                     po, _stream_handle(stream)),
+                                     po, pe, _stream_handle(stream)),
            "onmf_project_static")
 
 

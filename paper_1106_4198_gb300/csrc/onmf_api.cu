@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -878,23 +879,148 @@ onmf_status nmf_batch_init_H(const float *V, int64_t ldv, const float *W, float 
     return ONMF_OK;
 }
 
-onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int32_t F, int32_t K,
-                           int64_t N, double eps, double h_exponent, int32_t n_iter,
-                           int32_t normalize, int32_t precision, double *obj_out, void *stream) {
-    Range range_("nmf_batch_step");
-    if (!V || !W || !H || F < 1 || F > 8192 || K < 1 || K > 256 || N < 1 || ldv < F ||
-        n_iter < 0 || !(eps >= 0.0) || !(h_exponent > 0.0) ||
+}  // extern "C"
+
+// Device scratch of batch IS-NMF cycles for one shape, sized for at most
+// N_max frames and allocated once (nmf_batch_plan_create), so that the
+// cycles themselves (nmf_batch_plan_step) allocate nothing.
+struct nmf_batch_plan {
+    int F = 0, K = 0, precision = 0, prec = 0, dev = 0, nsm = 1;
+    long long Nmax = 0;
+    Shape sh{};
+    size_t elem = 4;
+    long long betap_max = 0, slots_max = 0;
+    static constexpr int kMaxChunks = 16;  // frame ranges of the statistics
+    static constexpr int kObjCap = 256;    // objectives held on the device at once
+    float *Wrm = nullptr, *swp = nullptr, *part = nullptr, *scale = nullptr;
+    __nv_bfloat16 *Wimg = nullptr, *Wrow = nullptr;
+    void *Pg = nullptr, *Qg = nullptr, *Hg = nullptr;
+    double *lp = nullptr, *obj_d = nullptr;
+    int *err = nullptr;
+    std::vector<void *> owned;
+    // stream-ordered plan (the one-shot nmf_batch_step): buffers come from
+    // and go back to the stream's memory pool, in stream order
+    bool ordered = false;
+    cudaStream_t q = nullptr;
+};
+
+static void batch_plan_free(nmf_batch_plan *p) {
+    if (!p) return;
+    if (p->ordered) {
+        for (void *x : p->owned) cudaFreeAsync(x, p->q);
+    } else {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(p->dev);
+        cudaDeviceSynchronize();  // no kernel of the plan may still run
+        for (void *x : p->owned) cudaFree(x);
+        cudaSetDevice(cur);
+    }
+    delete p;
+}
+
+static onmf_status batch_plan_make(int32_t F, int32_t K, int64_t N_max, int32_t precision,
+                                   bool ordered, cudaStream_t q, nmf_batch_plan **out);
+
+extern "C" {
+
+onmf_status nmf_batch_plan_create(int32_t F, int32_t K, int64_t N_max, int32_t precision,
+                                  nmf_batch_plan **out) {
+    return batch_plan_make(F, K, N_max, precision, false, nullptr, out);
+}
+
+}  // extern "C"
+
+static onmf_status batch_plan_make(int32_t F, int32_t K, int64_t N_max, int32_t precision,
+                                   bool ordered, cudaStream_t q, nmf_batch_plan **out) {
+    if (!out) return ONMF_EINVAL;
+    *out = nullptr;
+    if (F < 1 || F > 8192 || K < 1 || K > 256 || N_max < 1 ||
         (precision != ONMF_FP32 && precision != ONMF_MIXED))
         return ONMF_EINVAL;
     if (precision == ONMF_MIXED && F > 1024) return ONMF_EINVAL;
     onmf_status st = ensure_configured();
     if (st != ONMF_OK) return st;
+    nmf_batch_plan *p = new (std::nothrow) nmf_batch_plan;
+    if (!p) return ONMF_ENOMEM;
+    p->F = F;
+    p->K = K;
+    p->Nmax = N_max;
+    p->ordered = ordered;
+    p->q = q;
+    p->precision = precision;
+    p->sh = make_shape(F, K);
+    p->prec = pick_prec(precision, p->sh);
+    cudaGetDevice(&p->dev);
+    cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->dev);
+    p->elem = p->prec == PREC_FP32 ? 4 : 2;
+    p->betap_max = (N_max + 15) / 16 * 16;
+    // loss slots of every h-solve at any N <= N_max: one per 8 frames (mma,
+    // FP32), per 16 (tcgen05), or C <= 8 per 32 (cluster), plus a margin for
+    // the cluster size chosen at small N
+    p->slots_max = (N_max + 3) / 4 + 8LL * kClMaxC + 64;
+    const Shape &sh = p->sh;
+    auto al = [&](void **x, size_t bytes) -> bool {
+        if ((ordered ? cudaMallocAsync(x, bytes, q) : cudaMalloc(x, bytes)) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        p->owned.push_back(*x);
+        return true;
+    };
+    bool ok = al((void **)&p->swp, (size_t)K * 4) && al((void **)&p->scale, (size_t)K * 4) &&
+              al((void **)&p->part, (size_t)nmf_batch_plan::kMaxChunks * 2 * sh.Fp16 * sh.Kh * 4) &&
+              al(&p->Pg, (size_t)p->betap_max * sh.Fp16 * p->elem) &&
+              al(&p->Qg, (size_t)p->betap_max * sh.Fp16 * p->elem) &&
+              al(&p->Hg, (size_t)p->betap_max * sh.Kh * p->elem) &&
+              al((void **)&p->lp, (size_t)p->slots_max * 8) &&
+              al((void **)&p->obj_d, (size_t)nmf_batch_plan::kObjCap * 8) &&
+              al((void **)&p->err, 16);
+    if (ok && p->prec == PREC_FP32) ok = al((void **)&p->Wrm, (size_t)F * K * 4);
+    if (ok && p->prec != PREC_FP32 && p->prec != PREC_CL)
+        ok = al((void **)&p->Wimg, (size_t)sh.Kp * sh.WLD * 2);
+    if (ok && (p->prec == PREC_TC || p->prec == PREC_CL))
+        ok = al((void **)&p->Wrow, (size_t)F * sh.Kp * 2);
+    if (!ok) {
+        batch_plan_free(p);
+        snprintf(g_msg, sizeof g_msg, "batch plan allocation failed");
+        return ONMF_ENOMEM;
+    }
+    // padding of the images and of H stays zero for the plan's life (the
+    // kernels write only the live rows)
+    cudaError_t e = cudaSuccess;
+    if (p->Wimg) e = cudaMemsetAsync(p->Wimg, 0, (size_t)sh.Kp * sh.WLD * 2, q);
+    if (p->Wrow && e == cudaSuccess) e = cudaMemsetAsync(p->Wrow, 0, (size_t)F * sh.Kp * 2, q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->Hg, 0, (size_t)p->betap_max * sh.Kh * p->elem, q);
+    if (e == cudaSuccess && !ordered) e = cudaStreamSynchronize(q);
+    if (e != cudaSuccess) {
+        set_msg("batch plan init", e);
+        batch_plan_free(p);
+        return ONMF_ECUDA;
+    }
+    *out = p;
+    return ONMF_OK;
+}
+
+extern "C" {
+
+void nmf_batch_plan_destroy(nmf_batch_plan *p) { batch_plan_free(p); }
+
+onmf_status nmf_batch_plan_step(nmf_batch_plan *p, const float *V, int64_t ldv, float *W, float *H,
+                                int64_t N, double eps, double h_exponent, int32_t n_iter,
+                                int32_t normalize, double *obj_out, void *stream) {
+    Range range_("nmf_batch_plan_step");
+    if (!p || !V || !W || !H || N < 1 || N > p->Nmax || ldv < p->F || n_iter < 0 ||
+        !(eps >= 0.0) || !(h_exponent > 0.0))
+        return ONMF_EINVAL;
     if (n_iter == 0) return ONMF_OK;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->dev) return ONMF_EINVAL;
     cudaStream_t q = reinterpret_cast<cudaStream_t>(stream);
-    const Shape sh = make_shape(F, K);
-    const int prec = pick_prec(precision, sh);
+    const Shape &sh = p->sh;
+    const int prec = p->prec, K = p->K, nsm = p->nsm;
     const long long betap = (N + 15) / 16 * 16;
-    const size_t elem = prec == PREC_FP32 ? 4 : 2;
     const int tile = prec == PREC_TC ? kTcTile : kTile;
     long long ntiles = (N + tile - 1) / tile;  // loss slots
     ClusterTiles ct;
@@ -903,9 +1029,7 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
         if (ct.C == 0) return ONMF_EINVAL;
         ntiles = ct.slots;
     }
-    int dev = 0, nsm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (ntiles > p->slots_max) return ONMF_EINVAL;
     const int units = (sh.Fp16 / 16) * (sh.Kh / 32);
     // frame ranges per output tile of the statistics: the count (<= 16, at
     // least 256 frames a range) whose units fill whole rounds of one CTA per
@@ -913,7 +1037,8 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
     int nchunks = 1;
     {
         double best = -1.0;
-        for (int c = 1; c <= 16 && (c == 1 || (long long)c * 256 <= N); ++c) {
+        for (int c = 1; c <= nmf_batch_plan::kMaxChunks && (c == 1 || (long long)c * 256 <= N);
+             ++c) {
             const long long U = (long long)units * c, rounds = (U + nsm - 1) / nsm;
             const double eff = (double)U / (double)(rounds * nsm);
             if (eff > best + 1e-9) {
@@ -922,39 +1047,7 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
             }
         }
     }
-    // scratch
-    float *Wrm = nullptr, *swp = nullptr, *part = nullptr, *scale = nullptr;
-    __nv_bfloat16 *Wimg = nullptr, *Wrow = nullptr;
-    void *Pg = nullptr, *Qg = nullptr, *Hg = nullptr;
-    double *lp = nullptr, *obj_d = nullptr;
-    int *err = nullptr;
-    std::vector<void *> owned;
-    auto al = [&](void **p, size_t bytes) -> bool {
-        if (cudaMallocAsync(p, bytes, q) != cudaSuccess) return false;
-        owned.push_back(*p);
-        return true;
-    };
-    bool ok = al((void **)&swp, (size_t)K * 4) && al((void **)&scale, (size_t)K * 4) &&
-              al((void **)&part, (size_t)nchunks * 2 * sh.Fp16 * sh.Kh * 4) &&
-              al(&Pg, (size_t)betap * sh.Fp16 * elem) && al(&Qg, (size_t)betap * sh.Fp16 * elem) &&
-              al(&Hg, (size_t)betap * sh.Kh * elem) && al((void **)&lp, (size_t)ntiles * 8) &&
-              al((void **)&obj_d, (size_t)std::max(1, n_iter) * 8) && al((void **)&err, 16);
-    if (ok && prec == PREC_FP32) ok = al((void **)&Wrm, (size_t)F * K * 4);
-    if (ok && prec != PREC_FP32 && prec != PREC_CL) ok = al((void **)&Wimg, (size_t)sh.Kp * sh.WLD * 2);
-    if (ok && (prec == PREC_TC || prec == PREC_CL)) ok = al((void **)&Wrow, (size_t)F * sh.Kp * 2);
-    auto cleanup = [&]() {
-        for (void *p : owned) cudaFreeAsync(p, q);
-    };
-    if (!ok) {
-        cleanup();
-        snprintf(g_msg, sizeof g_msg, "batch scratch allocation failed");
-        return ONMF_ENOMEM;
-    }
-    cudaError_t e = cudaSuccess;
-    if (Wimg) e = cudaMemsetAsync(Wimg, 0, (size_t)sh.Kp * sh.WLD * 2, q);
-    if (Wrow && e == cudaSuccess) e = cudaMemsetAsync(Wrow, 0, (size_t)F * sh.Kp * 2, q);
-    if (e == cudaSuccess) e = cudaMemsetAsync(Hg, 0, (size_t)betap * sh.Kh * elem, q);
-    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, 16, q);
+    cudaError_t e = cudaMemsetAsync(p->err, 0, 16, q);
     const size_t tsm = tc_min_smem(prec, tile_smem_bytes(sh, prec));
     const int tgrid = (int)std::min<long long>(ntiles, 2LL * nsm);
     auto run_tiles = [&](const TileArgs &x) {
@@ -970,17 +1063,28 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
     a.ldv = ldv;
     a.n = N;
     a.Wcm = W;
-    a.Wrm = Wrm;
-    a.Wimg = Wimg;
-    a.Wrow = Wrow;
-    a.swpart = swp;
-    a.err = err;
+    a.Wrm = p->Wrm;
+    a.Wimg = p->Wimg;
+    a.Wrow = p->Wrow;
+    a.swpart = p->swp;
+    a.err = p->err;
     a.betap = betap;
+    constexpr int cap = nmf_batch_plan::kObjCap;
+    std::vector<double> objs;
+    if (obj_out) objs.resize((size_t)n_iter);
+    // objective slot of the iterate after cycle i, and the copy-out of full
+    // blocks of kObjCap objectives (the device holds one block at a time)
+    auto obj_slot = [&](int i) { return p->obj_d + (i % cap); };
+    auto flush_block = [&](int last) -> cudaError_t {
+        const int first = last / cap * cap;
+        return cudaMemcpyAsync(objs.data() + first, p->obj_d, (size_t)(last - first + 1) * 8,
+                               cudaMemcpyDeviceToHost, q);
+    };
     for (int it = 0; it < n_iter && e == cudaSuccess; ++it) {
         // one pass over the frames: the H step (its first X gives the
         // objective of the previous iterate), then X from the updated H and
         // the P, Q, H rows of the W step
-        e = launch_prepare(sh, W, Wrm, Wimg, swp, q, Wrow);
+        e = launch_prepare(sh, W, p->Wrm, p->Wimg, p->swp, q, p->Wrow);
         TileArgs h = a;
         h.n_in = 1;
         h.H_in = H;
@@ -989,45 +1093,72 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
         h.ldh = K;
         h.loss_first = (it > 0 && obj_out) ? 1 : 0;
         h.final_pass = 1;
-        h.loss_part = h.loss_first ? lp : nullptr;
-        h.Pg = Pg;
-        h.Qg = Qg;
-        h.Hg = Hg;
+        h.loss_part = h.loss_first ? p->lp : nullptr;
+        h.Pg = p->Pg;
+        h.Qg = p->Qg;
+        h.Hg = p->Hg;
         if (e == cudaSuccess) e = run_tiles(h);
-        if (e == cudaSuccess && h.loss_first) e = launch_sum(lp, ntiles, obj_d + it - 1, 0, q);
+        if (e == cudaSuccess && h.loss_first) {
+            e = launch_sum(p->lp, ntiles, obj_slot(it - 1), 0, q);
+            if (e == cudaSuccess && (it - 1) % cap == cap - 1) e = flush_block(it - 1);
+        }
         if (e == cudaSuccess)
-            e = launch_batch_stats(sh, prec, Pg, Qg, Hg, betap, N, nchunks, part,
-                                   std::min(units * nchunks, prec == PREC_FP32 ? 2 * nsm : nsm), q);
-        if (e == cudaSuccess) e = launch_batch_wstep(sh, part, nchunks, W, q);
-        if (e == cudaSuccess) e = launch_batch_normalize(sh, normalize, W, scale, err, q);
-        if (e == cudaSuccess) e = launch_batch_scale_h(K, N, H, scale, q);
+            e = launch_batch_stats(sh, prec, p->Pg, p->Qg, p->Hg, betap, N, nchunks, p->part,
+                                   std::min(units * nchunks, prec == PREC_FP32 ? 2 * nsm : nsm),
+                                   q);
+        if (e == cudaSuccess) e = launch_batch_wstep(sh, p->part, nchunks, W, q);
+        if (e == cudaSuccess) e = launch_batch_normalize(sh, normalize, W, p->scale, p->err, q);
+        if (e == cudaSuccess) e = launch_batch_scale_h(K, N, H, p->scale, q);
     }
     if (e == cudaSuccess && obj_out) {
         // objective of the final iterate
-        e = launch_prepare(sh, W, Wrm, Wimg, swp, q, Wrow);
+        e = launch_prepare(sh, W, p->Wrm, p->Wimg, p->swp, q, p->Wrow);
         TileArgs o = a;
         o.n_in = 0;
         o.H_in = H;
         o.ldh_in = K;
         o.final_pass = 1;
-        o.loss_part = lp;
+        o.loss_part = p->lp;
         if (e == cudaSuccess) e = run_tiles(o);
-        if (e == cudaSuccess) e = launch_sum(lp, ntiles, obj_d + n_iter - 1, 0, q);
+        if (e == cudaSuccess) e = launch_sum(p->lp, ntiles, obj_slot(n_iter - 1), 0, q);
+        if (e == cudaSuccess) e = flush_block(n_iter - 1);
     }
     int errh = 0;
     if (e == cudaSuccess && obj_out) {
-        std::vector<double> o(n_iter);
-        e = cudaMemcpyAsync(o.data(), obj_d, (size_t)n_iter * 8, cudaMemcpyDeviceToHost, q);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(&errh, err, 4, cudaMemcpyDeviceToHost, q);
+        e = cudaMemcpyAsync(&errh, p->err, 4, cudaMemcpyDeviceToHost, q);
         if (e == cudaSuccess) e = cudaStreamSynchronize(q);
-        for (int i = 0; i < n_iter; ++i) obj_out[i] = o[i] / (double)N;
+        for (int i = 0; i < n_iter; ++i) obj_out[i] = objs[(size_t)i] / (double)N;
     }
-    cleanup();
     if (e != cudaSuccess) {
-        set_msg("nmf_batch_step", e);
+        set_msg("nmf_batch_plan_step", e);
         return ONMF_ECUDA;
     }
     return errh ? status_from_err(errh) : ONMF_OK;
+}
+
+onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int32_t F, int32_t K,
+                           int64_t N, double eps, double h_exponent, int32_t n_iter,
+                           int32_t normalize, int32_t precision, double *obj_out, void *stream) {
+    Range range_("nmf_batch_step");
+    if (!V || !W || !H || F < 1 || F > 8192 || K < 1 || K > 256 || N < 1 || ldv < F ||
+        n_iter < 0 || !(eps >= 0.0) || !(h_exponent > 0.0) ||
+        (precision != ONMF_FP32 && precision != ONMF_MIXED))
+        return ONMF_EINVAL;
+    if (precision == ONMF_MIXED && F > 1024) return ONMF_EINVAL;
+    if (n_iter == 0) {
+        onmf_status st = ensure_configured();
+        return st;
+    }
+    // a plan whose buffers come from the stream's pool and return to it in
+    // stream order: the call stays asynchronous unless obj_out is given
+    cudaStream_t q = reinterpret_cast<cudaStream_t>(stream);
+    nmf_batch_plan *p = nullptr;
+    onmf_status st = batch_plan_make(F, K, N, precision, true, q, &p);
+    if (st != ONMF_OK) return st;
+    st = nmf_batch_plan_step(p, V, ldv, W, H, N, eps, h_exponent, n_iter, normalize, obj_out,
+                             stream);
+    batch_plan_free(p);
+    return st;
 }
 
 }  // extern "C"

@@ -5,6 +5,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "onmf.h"
@@ -16,6 +19,9 @@
 #include "onmf_step.cuh"
 
 namespace onmf {
+
+// Guards the per-device caches of launch queries below.
+static std::mutex g_cache_mu;
 
 // Derived images of a dictionary W (column-major F x K): the row-major copy,
 // the bf16 W^T image and the column sums. One warp per column.
@@ -196,15 +202,28 @@ static cudaLaunchConfig_t cluster_config(int C, int grid, size_t smem, cudaStrea
 }
 
 int cluster_max_active(const Shape &s, int C, bool online) {
+    // cached per (device, k16 slabs, C, online, shared memory): the answer is
+    // an occupancy query that depends on nothing else
+    static std::map<std::tuple<int, int, int, int, size_t>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const size_t smem = cluster_smem_bytes(s, C, online);
+    const auto key = std::make_tuple(dev, s.Kp / 16, C, online ? 1 : 0, smem);
+    {
+        std::lock_guard<std::mutex> lock(g_cache_mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
     const void *fn = online ? cluster_online_fn(s.Kp / 16) : cluster_tile_fn(s.Kp / 16);
     cudaLaunchAttribute at[2];
-    cudaLaunchConfig_t cfg =
-        cluster_config(C, C * 1024, cluster_smem_bytes(s, C, online), 0, at, false);
+    cudaLaunchConfig_t cfg = cluster_config(C, C * 1024, smem, 0, at, false);
     int n = 0;
     if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    cache[key] = n;
     return n;
 }
 
@@ -330,7 +349,10 @@ cudaError_t configure_kernels() {
     return cudaSuccess;
 }
 
-size_t max_dynamic_smem() {
+// The kernels' static shared memory does not change once the library is
+// loaded, so the answer is computed once per device (about 80 attribute
+// queries) and cached.
+static size_t max_dynamic_smem_uncached() {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -356,6 +378,21 @@ size_t max_dynamic_smem() {
     return (size_t)optin > worst ? optin - worst : 0;
 }
 
+size_t max_dynamic_smem() {
+    constexpr int kDevs = 64;
+    static size_t cached[kDevs];
+    static bool have[kDevs];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevs)
+        return max_dynamic_smem_uncached();
+    std::lock_guard<std::mutex> lock(g_cache_mu);
+    if (!have[dev]) {
+        cached[dev] = max_dynamic_smem_uncached();
+        have[dev] = true;
+    }
+    return cached[dev];
+}
+
 cudaError_t max_coresident_blocks(int prec, int ks, size_t smem, int *blocks_per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, online_fn(prec, ks),
                                                          kThreads, smem);
@@ -374,13 +411,15 @@ cudaError_t launch_online(const StepArgs &a, int prec, int grid, size_t smem,
     return e;
 }
 
-// The online step on clusters of C CTAs. Cooperative where the runtime
-// accepts it together with a cluster dimension; otherwise a plain cluster
-// launch whose grid is sized to the co-resident clusters (the bounded grid
-// barrier turns a CTA that never became resident into ERR_TIMEOUT).
+// The online step on clusters of C CTAs, always as a cooperative launch: its
+// grid barriers need every CTA resident at once, which only a cooperative
+// launch guarantees (a plain launch sized by the occupancy query can still
+// find SMs taken, e.g. by the frame-pull kernel that runs beside it, and
+// its barrier would then run out after 2 s instead of failing at launch).
+// A runtime that refuses the cooperative attribute together with a cluster
+// dimension gets an error here, not a weaker launch.
 cudaError_t launch_online_cluster(const StepArgs &a, int C, int grid, size_t smem,
                                   cudaStream_t stream) {
-    static int coop_ok = -1;
     cudaError_t e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
     StepArgs copy = a;
@@ -388,19 +427,7 @@ cudaError_t launch_online_cluster(const StepArgs &a, int C, int grid, size_t sme
     void *args[] = {&copy, &c};
     const void *fn = cluster_online_fn(a.s.Kp / 16);
     cudaLaunchAttribute at[2];
-    if (coop_ok != 0) {
-        cudaLaunchConfig_t cfg = cluster_config(C, grid, smem, stream, at, true);
-        e = cudaLaunchKernelExC(&cfg, fn, args);
-        if (e == cudaSuccess) {
-            coop_ok = 1;
-            count_launch();
-            return e;
-        }
-        if (coop_ok == 1) return e;
-        cudaGetLastError();
-        coop_ok = 0;
-    }
-    cudaLaunchConfig_t cfg = cluster_config(C, grid, smem, stream, at, false);
+    cudaLaunchConfig_t cfg = cluster_config(C, grid, smem, stream, at, true);
     e = cudaLaunchKernelExC(&cfg, fn, args);
     if (e == cudaSuccess) count_launch();
     return e;

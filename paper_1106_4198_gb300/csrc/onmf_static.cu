@@ -52,10 +52,16 @@ onmf_status scratch_address(void **out) {
 
 }  // namespace
 
+// The kernels' error bits are the ones the header promises to err_out.
+static_assert(onmf::ERR_INPUT == ONMF_DEVERR_INPUT && onmf::ERR_NUMERIC == ONMF_DEVERR_NUMERIC &&
+                  onmf::ERR_TIMEOUT == ONMF_DEVERR_TIMEOUT && onmf::ERR_CONFIG == ONMF_DEVERR_CONFIG,
+              "device error bits");
+
 extern "C" onmf_status onmf_project_static(const float *W, int32_t F, int32_t K, const float *V,
                                            int64_t ldv, int64_t n, float *H_out, int64_t ldh,
                                            double eps, double h_exponent, int32_t n_inner,
-                                           int32_t precision, double *obj_sum, void *stream) {
+                                           int32_t precision, double *obj_sum, int32_t *err_out,
+                                           void *stream) {
     using namespace onmf;
     if (!W || F < 1 || K < 1 || n < 0 || (n > 0 && !V) || ldv < F || (H_out && ldh < K) ||
         n_inner < 0 || !(eps >= 0.0) || !(h_exponent > 0.0) ||
@@ -100,6 +106,11 @@ extern "C" onmf_status onmf_project_static(const float *W, int32_t F, int32_t K,
     // call of another shape left there
     if (Wimg && cudaMemsetAsync(Wimg, 0, img, q) != cudaSuccess) return ONMF_ECUDA;
     if (Wrow && cudaMemsetAsync(Wrow, 0, rows, q) != cudaSuccess) return ONMF_ECUDA;
+    // the kernels OR their error bits into the caller's word when there is
+    // one, else into the last 256 bytes of the scratch (then nobody reads them)
+    int *err = err_out ? reinterpret_cast<int *>(err_out)
+                       : reinterpret_cast<int *>(b + ONMF_STATIC_SCRATCH_BYTES - 256);
+    if (cudaMemsetAsync(err, 0, sizeof(int), q) != cudaSuccess) return ONMF_ECUDA;
     if (launch_prepare(sh, W, Wrm, Wimg, swpart, q, Wrow) != cudaSuccess) return ONMF_ECUDA;
     if (n == 0) {
         if (obj_sum && cudaMemsetAsync(obj_sum, 0, sizeof(double), q) != cudaSuccess)
@@ -124,10 +135,6 @@ extern "C" onmf_status onmf_project_static(const float *W, int32_t F, int32_t K,
     a.Wrow = Wrow;
     a.swpart = swpart;
     a.loss_part = obj_sum ? loss : nullptr;
-    // the kernel's input-check flag goes to the last 256 bytes of the scratch;
-    // this entry point does not read it back (it never synchronizes)
-    int *err = reinterpret_cast<int *>(b + ONMF_STATIC_SCRATCH_BYTES - 256);
-    if (cudaMemsetAsync(err, 0, sizeof(int), q) != cudaSuccess) return ONMF_ECUDA;
     a.err = err;
     if (prec == PREC_CL) {
         if (launch_tiles_cluster(a, ct.C, ct.grid, smem, q) != cudaSuccess) return ONMF_ECUDA;

@@ -40,7 +40,7 @@ def test_config_layout_and_defaults():
     assert c.precision == onmf.ONMF_FP32 and c.hsolve == onmf.ONMF_HSOLVE_AUTO
     assert c.accumulate == onmf.ONMF_ACC_FP64 and c.reserved == 0
     assert c.h_penalty == 0.0 and c.h_penalty_a == 1.0 and c.w_penalty == 0.0
-    assert onmf.onmf_abi_version() == 5
+    assert onmf.onmf_abi_version() == 6
 
 
 def test_status_strings():
@@ -114,6 +114,14 @@ def test_null_arguments_rejected():
     assert L.onmf_get_W(None, None, 0) == 1
     assert L.nmf_batch_step(None, 0, None, None, 1, 1, 1, 0.0, 0.5, 1, 1, 0,
                             None, None) == 1
+    assert L.nmf_batch_plan_step(None, None, 0, None, None, 1, 0.0, 0.5, 1, 1,
+                                 None, None) == 1
+    h = ctypes.c_void_p()
+    assert L.nmf_batch_plan_create(0, 4, 16, 0, ctypes.byref(h)) == 1  # F < 1
+    assert L.nmf_batch_plan_create(16, 4, 0, 0, ctypes.byref(h)) == 1  # N_max < 1
+    assert L.nmf_batch_plan_create(16, 4, 16, 7, ctypes.byref(h)) == 1  # precision
+    assert not h.value
+    L.nmf_batch_plan_destroy(None)  # a NULL plan is ignored
     # an unknown wait kind is refused before any device work
     assert L.onmf_selftest_wait(7, None, None) == 1
     assert L.onmf_selftest_wait(-1, None, None) == 1

@@ -16,7 +16,7 @@ import pytest
 
 import paper_1106_4198_gb300 as onmf
 from helpers import cuda, problem, relerr
-from test_gpu_online import run_gpu, run_oracle
+from test_gpu_online import MIXED_TOL, compare, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 MODES = [onmf.ONMF_ACC_FP64, onmf.ONMF_ACC_FP32, onmf.ONMF_ACC_FP32_COMP]
@@ -29,13 +29,8 @@ def test_modes_match_oracle(acc, precision):
     V, W0 = problem(F, K, N, seed=3)
     g = run_gpu(V, W0, beta=beta, n_inner=n_in, precision=precision, accumulate=acc)
     o = run_oracle(V, W0, beta, n_in)
-    e = dict(W=relerr(g["W"], o["W"]), A=relerr(g["A"], o["A"]), B=relerr(g["B"], o["B"]),
-             H=relerr(g["H"], o["H"]), loss=abs(g["loss_sum"] - o["loss_sum"]) / o["loss_sum"])
-    print(onmf.ACC_NAMES[acc], "precision", precision, {k: "%.2e" % v for k, v in e.items()})
-    tol, tol_l = (1e-5, 1e-5) if precision == onmf.ONMF_FP32 else (1e-2, 1e-3)
-    assert e["loss"] <= tol_l
-    for k in ("W", "A", "B", "H"):
-        assert e[k] <= tol, (k, e)
+    tol = 1e-5 if precision == onmf.ONMF_FP32 else MIXED_TOL
+    compare(g, o, tol, label="%s precision %d" % (onmf.ACC_NAMES[acc], precision))
 
 
 def long_run(V, W0, acc, beta):
@@ -105,5 +100,5 @@ def test_forgetting_factor_in_every_mode(acc, rho_on_new):
     kw = dict(r=0.7, n_ref=N, rho_on_new=rho_on_new)
     g = run_gpu(V, W0, beta=beta, n_inner=3, accumulate=acc, **kw)
     o = run_oracle(V, W0, beta, 3, **kw)
-    for k in ("W", "A", "B", "H"):
-        assert relerr(g[k], o[k]) <= 1e-5, k
+    compare(g, o, 1e-5, label="forgetting factor %s rho_on_new=%d" % (onmf.ACC_NAMES[acc],
+                                                                    rho_on_new))

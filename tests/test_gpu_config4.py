@@ -3,18 +3,20 @@ objective-vs-time workload: F = 513, N = 112,500 frames of the gamma model
 (drawn with a 50-atom W*), dictionaries of K in {64, 100, 256} atoms,
 minibatches beta in {512, 2048}, 10 inner iterations, the h-solve kernel the
 autotuner picks. Every setting against the FP64 oracle over the same pass:
-the error of W, A, B and of the running objective is printed and held to the
-mixed-path bounds (1e-2 on W, A, B; 1e-3 on the objective)."""
+the errors of W, A, B (every entry, every frequency row, the last row on its
+own) and of the running objective are printed and held to PASS_TOL (about
+three times the largest measured) and 1e-3 on the objective."""
 import numpy as np
 import pytest
 
 import paper_1106_4198_gb300 as onmf
 import synth
-from helpers import relerr
+from helpers import parity
 from test_gpu_online import run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 F, N, N_IN = 513, 112_500, 10
+PASS_TOL = dict(W=3e-2, A=3e-2, B=3e-2, objective=1e-3)
 
 
 @pytest.fixture(scope="module")
@@ -31,12 +33,10 @@ def test_setting_full_pass(K, beta, frames, tmp_path):
     g = run_gpu(frames, W0, beta=beta, n_inner=N_IN, precision=onmf.ONMF_MIXED, hsolve=h,
                 want_H=False)
     o = run_oracle(frames, W0, beta, N_IN)
-    e = dict(W=relerr(g["W"], o["W"]), A=relerr(g["A"], o["A"]), B=relerr(g["B"], o["B"]),
-             objective=abs(g["loss_sum"] - o["loss_sum"]) / o["loss_sum"])
     print("K=%d beta=%d h-solve %s (%s): objective %.6f" % (
         K, beta, onmf.HSOLVE_NAMES[h], {k: round(v, 1) for k, v in times.items()},
-        o["loss_sum"] / N), {k: "%.2e" % v for k, v in e.items()})
+        o["loss_sum"] / N))
     assert g["t"] == N
-    assert e["objective"] <= 1e-3
-    for k in ("W", "A", "B"):
-        assert e[k] <= 1e-2, (k, e)
+    parity("config-4 pass K=%d beta=%d" % (K, beta),
+           dict(W=(g["W"], o["W"]), A=(g["A"], o["A"]), B=(g["B"], o["B"]),
+                objective=(g["loss_sum"], o["loss_sum"])), PASS_TOL)

@@ -1,17 +1,20 @@
 """Parity of the online IS-NMF step (Algorithm 1) on the GPU, called through
 the C ABI, against the FP64 oracle on the same seeded inputs.
 
-Tolerances (norm-wise relative, ||x - x_ref|| / ||x_ref||):
-  FP32, one minibatch:          W, H, A, B <= 1e-5
+Every comparison is element-wise (helpers.parity): each entry within
+tol * (|x_ref| + 1e-3 mean|x_ref|), and for W, A, B each frequency row within
+tol in norm, the last row f = F - 1 asserted on its own.
+  FP32, one minibatch:          W, H, A, B and the loss <= 1e-5
   FP32, objective trajectory:   every minibatch loss <= 1e-3 (up to 100 steps)
-  mixed (BF16 products):        stated per test, measured against the oracle
+  mixed (BF16 products):        MIXED_TOL, about three times the largest
+                                error measured on a GB300 (printed by the test)
 """
 import numpy as np
 import pytest
 
 import oracle
 import paper_1106_4198_gb300 as onmf
-from helpers import cuda, problem, relerr
+from helpers import cuda, parity, problem
 
 pytestmark = pytest.mark.gpu
 
@@ -52,17 +55,23 @@ def run_oracle(V, W0, beta, n_inner, eps=1e-12, r=1.0, n_ref=0, h_exponent=0.5,
     return o
 
 
-def compare(g, o, tol, nframes=None):
-    errs = dict(W=relerr(g["W"], o["W"]), A=relerr(g["A"], o["A"]),
-                B=relerr(g["B"], o["B"]),
-                loss=abs(g["loss_sum"] - o["loss_sum"]) / abs(o["loss_sum"]))
+# Element-wise bounds of the mixed path (BF16 operands of the products,
+# FP32 ratios, FP64 or compensated A and B) for one minibatch.
+MIXED_TOL = dict(W=3e-2, A=3e-2, B=3e-2, H=1e-1, loss=1e-3)
+
+
+def pairs_of(g, o, nframes=None):
+    """(GPU, oracle) pairs of one run's outputs."""
+    p = dict(W=(g["W"], o["W"]), A=(g["A"], o["A"]), B=(g["B"], o["B"]))
     if g["H"] is not None:
         n = nframes if nframes is not None else o["frames"]
-        errs["H"] = relerr(g["H"][:n], o["H"][:n])
-    print("errors:", {k: "%.2e" % v for k, v in errs.items()})
-    for k, v in errs.items():
-        assert v <= tol, (k, v, errs)
-    return errs
+        p["H"] = (g["H"][:n], o["H"][:n])
+    p["loss"] = (g["loss_sum"], o["loss_sum"])
+    return p
+
+
+def compare(g, o, tol, nframes=None, label="online"):
+    return parity(label, pairs_of(g, o, nframes), tol)
 
 
 @pytest.mark.parametrize("F,K,beta,n_in", [(129, 8, 50, 5), (513, 100, 1000, 10),
@@ -93,11 +102,11 @@ def test_fp32_c1_pass_objective_trajectory():
         prev = ls
         worst = max(worst, abs(lg - o["mb_loss"][i]) / abs(o["mb_loss"][i]))
     W = m.W()
+    A, B, _, _ = m.stats()
     m.close()
-    print("worst minibatch loss rel err %.2e, final W rel err %.2e"
-          % (worst, relerr(W, o["W"])))
+    print("worst minibatch loss rel err %.2e" % worst)
     assert worst <= 1e-3
-    assert relerr(W, o["W"]) <= 1e-3
+    parity("C1 pass FP32", dict(W=(W, o["W"]), A=(A, o["A"]), B=(B, o["B"])), 1e-4)
 
 
 def test_ragged_pushes_and_flush():
@@ -227,10 +236,7 @@ def test_projection_fp32():
     oracle.set_threads(16)
     Ho, so = oracle.project(V, W0, n_in=10)
     oracle.set_threads(1)
-    e = relerr(H.cpu().numpy(), Ho)
-    print("projection H rel err %.2e, obj rel err %.2e" % (e, abs(obj - so) / so))
-    assert e <= 1e-5
-    assert abs(obj - so) / so <= 1e-5
+    parity("projection FP32", dict(H=(H.cpu().numpy(), Ho), objective=(obj, so)), 1e-5)
 
 
 def test_projection_block_diagonal_closed_form():
@@ -275,15 +281,9 @@ def hsolve(request, monkeypatch):
                                            (513, 128, 512, 10), (256, 40, 37, 4)])
 def test_mixed_single_minibatch_error_stated(F, K, beta, n_in, hsolve):
     """Mixed precision (BF16 tensor-core products, FP32 ratios, FP64 A/B):
-    one minibatch against the FP64 oracle. Stated bounds: W, A, B, H within
-    1e-2 and the minibatch loss within 1e-3."""
+    one minibatch against the FP64 oracle, element-wise within MIXED_TOL
+    (rows of W, A, B including the last one), the minibatch loss within 1e-3."""
     V, W0 = problem(F, K, beta)
     g = run_gpu(V, W0, beta=beta, n_inner=n_in, precision=MIXED)
     o = run_oracle(V, W0, beta, n_in)
-    errs = dict(W=relerr(g["W"], o["W"]), A=relerr(g["A"], o["A"]),
-                B=relerr(g["B"], o["B"]), H=relerr(g["H"], o["H"]),
-                loss=abs(g["loss_sum"] - o["loss_sum"]) / abs(o["loss_sum"]))
-    print("mixed (%s) errors:" % hsolve, {k: "%.2e" % v for k, v in errs.items()})
-    assert errs["loss"] <= 1e-3
-    for k in ("W", "A", "B", "H"):
-        assert errs[k] <= 1e-2, (k, errs)
+    compare(g, o, MIXED_TOL, label="mixed %s F=%d K=%d beta=%d" % (hsolve, F, K, beta))
