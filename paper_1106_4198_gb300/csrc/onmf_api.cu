@@ -117,6 +117,7 @@ struct onmf_state {
     double *A = nullptr, *B = nullptr, *loss_sum = nullptr;
     // scratch
     void *Pg = nullptr, *Qg = nullptr, *Hg = nullptr;
+    float *part = nullptr;  // frame-range partial sums of the tcgen05 statistics
     int betap = 0;
     double *loss_part = nullptr, *tmp_sum = nullptr;
     unsigned *bar = nullptr;
@@ -253,7 +254,7 @@ void onmf_destroy(onmf_state *s) {
     cudaStreamSynchronize(s->stream);
     if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
     void *dev[] = {s->Wcm, s->Wrm, s->Wn, s->swpart, s->Wimg, s->Wrow, s->A, s->B, s->loss_sum, s->Pg,
-                   s->Qg, s->Hg, s->loss_part, s->tmp_sum, s->bar, s->err_d, s->staging,
+                   s->Qg, s->Hg, s->part, s->loss_part, s->tmp_sum, s->bar, s->err_d, s->staging,
                    s->Hstage, s->vring[0], s->vring[1], s->hring[0], s->hring[1],
                    s->gV,     s->gH,       s->Hin_stage, s->stage_idx};
     for (void *p : dev)
@@ -335,10 +336,13 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
         AL(s->Hg, (size_t)s->betap * sh.Kh * 4);
     } else {
         if (s->prec != PREC_CL) AL(s->Wimg, (size_t)sh.Kp * sh.WLD * 2);
-        AL(s->Hg, (size_t)sh.Kh * s->betap * 2);
+        // the mma h-solve writes H in 128-row core blocks (the tcgen05
+        // statistics' A operand), the others k rows of betap frames
+        AL(s->Hg, (size_t)(s->prec == PREC_MIXED ? 128 : sh.Kh) * s->betap * 2);
         if (s->prec == PREC_TC || s->prec == PREC_CL) AL(s->Wrow, (size_t)sh.F * sh.Kp * 2);
     }
-    AL(s->Pg, (size_t)s->betap * sh.Fp16 * elem);
+    // P and Q: on the mma path one interleaved core-matrix buffer in Pg
+    AL(s->Pg, (size_t)s->betap * sh.Fp16 * elem * (s->prec == PREC_MIXED ? 2 : 1));
     AL(s->Qg, (size_t)s->betap * sh.Fp16 * elem);
     AL(s->loss_part, (size_t)nslots * 8);
     AL(s->bar, 16);
@@ -354,8 +358,12 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
     cudaError_t e = cudaSuccess;
     if (s->Wimg && e == cudaSuccess) e = cudaMemsetAsync(s->Wimg, 0, (size_t)sh.Kp * sh.WLD * 2, q);
     if (s->Wrow && e == cudaSuccess) e = cudaMemsetAsync(s->Wrow, 0, (size_t)sh.F * sh.Kp * 2, q);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->Hg, 0, (size_t)s->betap * sh.Kh * elem, q);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->Pg, 0, (size_t)s->betap * sh.Fp16 * elem, q);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(s->Hg, 0,
+                            (size_t)(s->prec == PREC_MIXED ? 128 : sh.Kh) * s->betap * elem, q);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(s->Pg, 0,
+                            (size_t)s->betap * sh.Fp16 * elem * (s->prec == PREC_MIXED ? 2 : 1), q);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->Qg, 0, (size_t)s->betap * sh.Fp16 * elem, q);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->A, 0, FK * 8, q);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->B, 0, FK * 8, q);
@@ -409,6 +417,16 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
         s->grid = std::min(want, per_sm * s->num_sms);
     }
     s->tile_grid = s->num_sms;
+    if (s->prec == PREC_MIXED) {
+        // partial sums of the frame ranges of a full minibatch (a partial
+        // one has no more ranges)
+        const StatsSplit sp = stats_split(c.beta, s->grid, sh.Fp16 / 16);
+        if ((e = cudaMalloc((void **)&s->part, (size_t)sp.S * 2 * c.K * sh.Fp16 * 4)) !=
+            cudaSuccess) {
+            set_msg("cudaMalloc", e);
+            return fail(ONMF_ENOMEM);
+        }
+    }
     // sanity: all of W0 finite and >= 0 (checked on the host copy)
     std::vector<float> w(FK);
     if (cudaMemcpyAsync(w.data(), s->Wcm, FK * 4, cudaMemcpyDeviceToHost, q) != cudaSuccess ||
@@ -464,6 +482,7 @@ static onmf_status run_minibatches(onmf_state *s, const float *V, long long ldv,
     a.Pg = s->Pg;
     a.Qg = s->Qg;
     a.Hg = s->Hg;
+    a.part = s->part;
     a.betap = s->betap;
     a.loss_part = s->loss_part;
     a.bar = s->bar;

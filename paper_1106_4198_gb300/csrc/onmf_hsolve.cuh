@@ -42,6 +42,9 @@ struct TileJob {
     int nvalid_next = 0;
     // FP32 path: the h penalty lambda * log(a + sum_k h_k) (lambda = 0: none)
     float hpen = 0.f, hpen_a = 1.f;
+    // mixed path: write P, Q and H in the core-matrix layout of the tcgen05
+    // statistics (stats_tc.cuh) instead of frame rows
+    int pq_core = 0;
 };
 
 // Whether a tile's frames go to shared memory by one bulk copy: contiguous
@@ -644,7 +647,37 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
     }
 
     // ---- outputs
-    if (t.final_pass && t.Pg) {
+    if (t.final_pass && t.Pg && t.pq_core) {
+        // core-matrix layout (8 frames x 16 bytes per core): the frames of
+        // this tile are frame group gi; f-tile ft of P and Q is one 512-byte
+        // block [P f 0-7 | P f 8-15 | Q f 0-7 | Q f 8-15], row j = frame; H
+        // is one 2 KB block per group, row k = 8 frames of h_k
+        unsigned char *PQc = reinterpret_cast<unsigned char *>(t.Pg);
+        unsigned char *Hc = reinterpret_cast<unsigned char *>(t.Hg);
+        const long long G = t.betap / 8, gi = t.j0 / 8;
+        const int cpr = Fp / 8;  // 16-byte chunks per row
+        for (int row = warp; row < 2 * kTile; row += kWarps) {
+            const int which = row >> 3, j = row & 7;
+            for (int c = lane; c < cpr; c += 32) {
+                uint4 v = make_uint4(0, 0, 0, 0);
+                if (j < t.nvalid) v = *reinterpret_cast<const uint4 *>(PQ_s + row * WLD + 8 * c);
+                *reinterpret_cast<uint4 *>(PQc + ((long long)(c >> 1) * G + gi) * 512 +
+                                           (which * 2 + (c & 1)) * 128 + j * 16) = v;
+            }
+        }
+        for (int k = tid; k < KS * 16; k += kThreads) {
+            uint32_t w[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = 2 * e;
+                const float a = (j < t.nvalid) ? __bfloat162float(H_s[j * HLD + k]) : 0.f;
+                const float b = (j + 1 < t.nvalid) ? __bfloat162float(H_s[(j + 1) * HLD + k]) : 0.f;
+                w[e] = pack_bf16(a, b);
+            }
+            *reinterpret_cast<uint4 *>(Hc + gi * 2048 + (long long)k * 16) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    } else if (t.final_pass && t.Pg) {
         __nv_bfloat16 *Pg = reinterpret_cast<__nv_bfloat16 *>(t.Pg);
         __nv_bfloat16 *Qg = reinterpret_cast<__nv_bfloat16 *>(t.Qg);
         __nv_bfloat16 *Hg = reinterpret_cast<__nv_bfloat16 *>(t.Hg);

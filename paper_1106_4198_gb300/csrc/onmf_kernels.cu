@@ -144,6 +144,7 @@ bool tc_shape_supported(const Shape &s) { return tc_supported(s); }
 size_t online_smem_bytes(const Shape &s, int prec) {
     size_t p1 = hsolve_smem(s, prec);
     size_t p2 = stats_smem_bytes(prec);
+    if (prec == PREC_MIXED && p2 < kStatsSmemBytes) p2 = kStatsSmemBytes;  // tcgen05 statistics
     return p1 > p2 ? p1 : p2;
 }
 

@@ -49,6 +49,29 @@ __host__ __device__ inline Shape make_shape(int F, int K) {
     return s;
 }
 
+// Frame ranges of the tcgen05 statistics of the mma path (onmf_stats_tc.cuh).
+struct StatsSplit {
+    int S;    // frame ranges
+    int gps;  // 8-frame groups per range (even: whole 16-frame MMA steps)
+};
+
+// Frame ranges of a minibatch of nb frames for a grid of G CTAs and FT
+// 16-frequency tiles: enough ranges that the FT * S units fill the grid,
+// with at least one 16-frame step per range.
+__host__ __device__ inline StatsSplit stats_split(int nb, int G, int FT) {
+    const int ng = (nb + 7) / 8;
+    int S = G / FT > 1 ? G / FT : 1;
+    const int steps = (ng + 1) / 2;
+    if (S > steps) S = steps;
+    if (S < 1) S = 1;
+    int gps = (ng + S - 1) / S;
+    gps = (gps + 1) / 2 * 2;
+    StatsSplit r;
+    r.gps = gps;
+    r.S = (ng + gps - 1) / gps;
+    return r;
+}
+
 // Arguments of the online step kernel (one launch = nmb minibatches).
 struct StepArgs {
     Shape s;
@@ -82,6 +105,7 @@ struct StepArgs {
     // scratch
     void *Pg, *Qg, *Hg;
     int betap;  // rows of Pg/Qg (and columns of the bf16 Hg)
+    float *part;  // mma path: frame-range partial sums of P H^T, Q H^T
     double *loss_part;
     unsigned *bar;
     int *err;

@@ -1,0 +1,246 @@
+// Statistics and dictionary step of Algorithm 1 (arXiv:1106.4198, Section
+// 2.3, Eq. aux_fun) for the mixed-precision online step, on the tcgen05
+// tensor cores:
+//
+//   phase 2   a_fk = W_fk^2 sum_j P_jf H_kj,  b_fk = sum_j Q_jf H_kj  as one
+//             contraction per work unit (16 frequencies x one range of frames):
+//             D[k, n] = sum_j H[k, j] [P | Q][j, n], M = 128 dictionary rows
+//             (K <= 128, rows past K are zero), N = 32 (16 frequencies of P,
+//             16 of Q), 16 frames per instruction; operands bulk-copied into
+//             shared memory in core-matrix form (two stages, the copy of one
+//             chunk overlapping the MMAs of the other), the FP32 accumulator
+//             in tensor memory, read back with tcgen05.ld and written as one
+//             partial sum per frame range;
+//   phase 3   one CTA per dictionary column: the partial sums of the frame
+//             ranges added in a fixed order, A <- rho A + a, B <- rho B + b,
+//             W' = sqrt(A/B), the column sum s_k, W = W'/s_k, A /= s_k,
+//             B *= s_k and the bf16 image row of W, all on values held in
+//             registers (one pass over the column).
+//
+// Global layouts (written by hsolve_tile_mixed with TileJob::pq_core):
+//   PQc  per (16-frequency tile t, 8-frame group g) a 512-byte block at
+//        (t * G + g) * 512: four core matrices [P f0-7 | P f8-15 | Q f0-7 |
+//        Q f8-15] of 8 rows (frames) x 16 bytes (8 bf16 frequencies);
+//   Hc   per group g a 2 KB block at g * 2048: 128 rows (k) x 16 bytes
+//        (8 bf16 frames); rows k >= K stay zero;
+//   part [split s][P or Q][k][Fp16] float partial sums (k < K).
+// In shared memory a chunk's groups sit back to back in the same form, so the
+// descriptors are: A (H, K-major) leading byte offset 2048 between 8-frame
+// cores, stride byte offset 128 between 8-row cores; B ([P|Q], MN-major)
+// leading byte offset 512 between 8-frame cores, stride byte offset 128
+// between 8-frequency cores.
+//
+// Included by onmf_step.cuh after the arithmetic of A and B (DF, ACC_*) and
+// before the persistent online kernel that calls these functions.
+#pragma once
+
+#include "onmf_device.cuh"
+#include "onmf_kernels.cuh"
+#include "onmf_tc.cuh"
+
+namespace onmf {
+
+constexpr int kStatsStageGroups = 24;                  // 8-frame groups per stage
+constexpr size_t kStatsStageBytes = (size_t)kStatsStageGroups * (2048 + 512);
+constexpr size_t kStatsSmemBytes = 2 * kStatsStageBytes;  // two stages
+constexpr uint32_t kStatsTmemCols = 32;
+
+// mbarriers of the statistics and their phase parities: two stages, each
+// with a bulk-copy barrier (ld) and an MMA-commit barrier (mma), tracked by
+// the issuing thread 0, and one barrier per unit that every thread waits on
+// (done).
+struct StatsBars {
+    uint64_t *ld[2], *mma[2], *done;
+    unsigned pl[2], pm[2], pd;
+};
+
+// One work unit of phase 2: f-tile t, frame range s (groups [s*gps, ...)),
+// in chunks of at most kStatsStageGroups groups through two shared-memory
+// stages: the bulk copy of chunk c+1 runs while the MMAs of chunk c do.
+// tcol: the CTA's tensor-memory columns (32).
+static __device__ void stats_unit_tc(int t, int s, int gps, int ng, long long G,
+                                     const unsigned char *PQc, const unsigned char *Hc,
+                                     float *part, int K, int Fp, unsigned char *smem,
+                                     uint32_t tcol, StatsBars &sb, int *err) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int g0 = s * gps, g1 = min(ng, g0 + gps);
+    const int nch = (g1 - g0 + kStatsStageGroups - 1) / kStatsStageGroups;
+    auto H_of = [&](int st) { return smem + st * kStatsStageBytes; };
+    auto PQ_of = [&](int st) { return smem + st * kStatsStageBytes + kStatsStageGroups * 2048; };
+    __syncthreads();  // the previous user of this shared memory is done
+    if (tid == 0) {
+        auto issue = [&](int c) {
+            const int st = c & 1;
+            const int a = g0 + c * kStatsStageGroups, n = min(kStatsStageGroups, g1 - a);
+            fence_proxy_async_shared();
+            mbar_arrive_expect_tx(sb.ld[st], (unsigned)n * 2560u);
+            bulk_g2s(H_of(st), Hc + (long long)a * 2048, (unsigned)n * 2048u, sb.ld[st]);
+            bulk_g2s(PQ_of(st), PQc + ((long long)t * G + a) * 512, (unsigned)n * 512u, sb.ld[st]);
+        };
+        bool ok = true;
+        issue(0);
+        if (nch > 1) issue(1);
+        const uint32_t id = tc_idesc(128, 32);
+        for (int c = 0; c < nch && ok; ++c) {
+            const int st = c & 1;
+            const int a = g0 + c * kStatsStageGroups, n = min(kStatsStageGroups, g1 - a);
+            if (n & 1) {  // the last 16-frame step has one group: the other reads zero
+                uint4 *hz = reinterpret_cast<uint4 *>(H_of(st) + (size_t)n * 2048);
+                uint4 *pz = reinterpret_cast<uint4 *>(PQ_of(st) + (size_t)n * 512);
+                for (int i = 0; i < 2048 / 16; ++i) hz[i] = make_uint4(0, 0, 0, 0);
+                for (int i = 0; i < 512 / 16; ++i) pz[i] = make_uint4(0, 0, 0, 0);
+                fence_proxy_async_shared();
+            }
+            ok = mbar_wait_bounded(sb.ld[st], sb.pl[st], err);
+            sb.pl[st] ^= 1u;
+            if (!ok) break;
+            tc_fence_after();
+            for (int ks = 0; ks < (n + 1) / 2; ++ks)
+                tc_mma_smem_a(tcol, tc_desc(H_of(st) + (size_t)ks * 4096, 2048, 128),
+                              tc_desc(PQ_of(st) + (size_t)ks * 1024, 512, 128), id,
+                              (c > 0 || ks > 0) ? 1u : 0u);
+            if (c + 2 < nch) {
+                // the stage is refilled once its MMAs have read it
+                tc_commit(sb.mma[st]);
+                ok = mbar_wait_bounded(sb.mma[st], sb.pm[st], err);
+                sb.pm[st] ^= 1u;
+                if (ok) issue(c + 2);
+            }
+        }
+        tc_commit(sb.done);  // arrives once every MMA above is done
+    }
+    const bool ok = mbar_wait_bounded(sb.done, sb.pd, err);
+    sb.pd ^= 1u;
+    tc_fence_after();
+    // accumulators: warp w reads lanes 32 (w % 4) .. (k) and the 16 columns of
+    // P (w < 4) or Q (w >= 4)
+    const int q = warp & 3, which = warp >> 2;
+    const int k = 32 * q + lane;
+    uint32_t r0[8], r1[8];
+    const uint32_t ta = tcol + ((uint32_t)(32 * q) << 16) + 16u * which;
+    tmem_ld8_async(ta, r0);
+    tmem_ld8_async(ta + 8, r1);
+    tmem_wait_ld(r0);
+    tmem_wait_ld(r1);
+    if (ok && k < K) {
+        float4 *dst = reinterpret_cast<float4 *>(
+            part + (((long long)s * 2 + which) * K + k) * Fp + 16 * t);
+        dst[0] = make_float4(__uint_as_float(r0[0]), __uint_as_float(r0[1]),
+                             __uint_as_float(r0[2]), __uint_as_float(r0[3]));
+        dst[1] = make_float4(__uint_as_float(r0[4]), __uint_as_float(r0[5]),
+                             __uint_as_float(r0[6]), __uint_as_float(r0[7]));
+        dst[2] = make_float4(__uint_as_float(r1[0]), __uint_as_float(r1[1]),
+                             __uint_as_float(r1[2]), __uint_as_float(r1[3]));
+        dst[3] = make_float4(__uint_as_float(r1[4]), __uint_as_float(r1[5]),
+                             __uint_as_float(r1[6]), __uint_as_float(r1[7]));
+    }
+    tc_fence_before();
+    __syncthreads();  // every read of the accumulator precedes the next MMA
+}
+
+// ---- phase 3: one dictionary column per CTA (strided), every value of the
+// column in registers (F <= kColRows).
+constexpr int kColPer = 4;                    // frequencies per thread
+constexpr int kColRows = kColPer * kThreads;  // 1024 >= F on the mixed path
+
+// A <- rho A + a (or A + rho a with rho_on_new) for one entry in the state's
+// arithmetic; `raw` is the stored 8 bytes (a double, a float, or a float
+// pair) and is replaced by the new stored form; returns the new value as a
+// float, the operand of W' = sqrt(A/B).
+__device__ __forceinline__ float ab_accumulate(int accm, double rho, int rho_on_new, float inc,
+                                               double &raw) {
+    const float rhof = (float)rho;
+    if (accm == ACC_FP64) {
+        const double v = rho_on_new ? fma(rho, (double)inc, raw) : fma(rho, raw, (double)inc);
+        raw = v;
+        return (float)v;
+    }
+    DF x;
+    memcpy(&x, &raw, 8);
+    if (accm == ACC_FP32) {
+        const float v = rho_on_new ? __fmaf_rn(rhof, inc, x.hi) : __fmaf_rn(rhof, x.hi, inc);
+        x = {v, 0.f};
+    } else {
+        x = rho_on_new ? df_add_mul(x, rhof, inc) : df_mul_add(x, rhof, inc);
+    }
+    memcpy(&raw, &x, 8);
+    return x.hi;
+}
+
+// The rescale of one stored entry: A / s (div) or B * s; FP64 sums use the
+// double reciprocal invd = 1/s and the double sd = s.
+__device__ __forceinline__ double ab_rescale(int accm, double raw, float sum, double invd,
+                                             double sd, bool div) {
+    if (accm == ACC_FP64) return div ? raw * invd : raw * sd;
+    DF x;
+    memcpy(&x, &raw, 8);
+    if (accm == ACC_FP32)
+        x = {div ? __fdiv_rn(x.hi, sum) : __fmul_rn(x.hi, sum), 0.f};
+    else
+        x = div ? df_div(x, sum) : df_mul_add(x, sum, 0.f);
+    double r;
+    memcpy(&r, &x, 8);
+    return r;
+}
+
+// WPEN: the dictionary penalty mu * sum W, W' = sqrt(A/(B + mu)).
+template <bool WPEN>
+static __device__ void column_step(const StepArgs &a, int S, double rho, float *red8, int first,
+                                   int stride) {
+    const Shape &s = a.s;
+    const int F = s.F, K = s.K, Fp = s.Fp16;
+    const int tid = threadIdx.x;
+    const int accm = a.acc;
+    for (int k = first; k < K; k += stride) {
+        float wn[kColPer];
+        double Ar[kColPer], Br[kColPer];
+        float part_sum = 0.f;
+#pragma unroll
+        for (int u = 0; u < kColPer; ++u) {
+            const int f = tid + u * kThreads;
+            wn[u] = 0.f;
+            if (f < F) {
+                const long long i = f + (long long)k * F;
+                // the frame ranges' partial sums, added in range order
+                float ph = 0.f, qh = 0.f;
+                const float *pp = a.part + (long long)k * Fp + f;
+                const long long step = (long long)K * Fp;
+                for (int r = 0; r < S; ++r) {
+                    ph += __ldcg(pp + (2LL * r) * step);
+                    qh += __ldcg(pp + (2LL * r + 1) * step);
+                }
+                const float w = a.Wcm[i];
+                Ar[u] = a.A[i];
+                Br[u] = a.B[i];
+                const float An = ab_accumulate(accm, rho, a.rho_on_new, ph * w * w, Ar[u]);
+                const float Bn = ab_accumulate(accm, rho, a.rho_on_new, qh, Br[u]);
+                const float Bd = WPEN ? Bn + a.wpen : Bn;
+                wn[u] = (Bd > 0.f) ? sqrtf(__fdiv_rn(An, Bd)) : w;
+                part_sum += wn[u];
+            }
+        }
+        const float sum = block_sum_f(part_sum, red8);
+        const bool sc = a.normalize && sum > 0.f;
+        const float inv = sc ? __frcp_rn(sum) : 1.f;
+        const double invd = sc ? 1.0 / (double)sum : 1.0;
+        const double sd = sc ? (double)sum : 1.0;
+        bool bad = false;
+#pragma unroll
+        for (int u = 0; u < kColPer; ++u) {
+            const int f = tid + u * kThreads;
+            if (f < F) {
+                const long long i = f + (long long)k * F;
+                const float wv = wn[u] * inv;
+                bad |= !isfinite(wv);
+                a.Wcm[i] = wv;
+                a.A[i] = sc ? ab_rescale(accm, Ar[u], sum, invd, sd, true) : Ar[u];
+                a.B[i] = sc ? ab_rescale(accm, Br[u], sum, invd, sd, false) : Br[u];
+                a.Wimg[(long long)k * s.WLD + f] = __float2bfloat16_rn(wv);
+            }
+        }
+        if (bad) flag_error(a.err, ERR_NUMERIC);
+        if (tid == 0) a.swpart[k] = sc ? sum * inv : sum;
+    }
+}
+
+}  // namespace onmf

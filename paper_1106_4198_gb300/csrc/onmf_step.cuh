@@ -521,6 +521,12 @@ __device__ __forceinline__ void hsolve_tile(const Shape &s, float eps, float gam
         hsolve_tile_fp32(s, eps, gamma, Wcm, Wrm, sw, t, smem, err);
 }
 
+}  // namespace onmf
+
+#include "onmf_stats_tc.cuh"
+
+namespace onmf {
+
 // ----------------------------------------------------- persistent online step
 
 // PEN: the penalized variant of the mma path (Section 2.2, "Extensions");
@@ -528,21 +534,25 @@ __device__ __forceinline__ void hsolve_tile(const Shape &s, float eps, float gam
 template <int PREC, int KS, bool PEN = false>
 __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t mbar[4];
+    __shared__ __align__(8) uint64_t mbar[9];
     __shared__ float s_tmp;
     __shared__ float s_red8[kWarps];
     __shared__ double s_red[kThreads];
     __shared__ uint32_t s_tslot;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 4; ++i) mbar_init(&mbar[i], 1);
+        for (int i = 0; i < 9; ++i) mbar_init(&mbar[i], 1);
         fence_mbar_init();
     }
+    // tensor memory: the tcgen05 h-solve's W and accumulators, or the
+    // accumulator of the tcgen05 statistics (mma h-solve)
     if (PREC == PREC_TC && threadIdx.x < 32) tmem_alloc(&s_tslot, kTmemCols);
+    if (PREC == PREC_MIXED && threadIdx.x < 32) tmem_alloc(&s_tslot, kStatsTmemCols);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tbase = PREC == PREC_TC ? s_tslot : 0u;
+    const uint32_t tbase = (PREC == PREC_TC || PREC == PREC_MIXED) ? s_tslot : 0u;
     unsigned wpar = 0, vpar = 0, epoch = 0, parA = 0, parB = 0;
+    StatsBars sb{{&mbar[4], &mbar[5]}, {&mbar[6], &mbar[7]}, &mbar[8], {0u, 0u}, {0u, 0u}, 0u};
     constexpr int TILE = PREC == PREC_TC ? kTcTile : kTile;
     const unsigned G = gridDim.x;
     const Shape &s = a.s;
@@ -583,6 +593,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                 }
                 t.loss_first = 0;
                 t.final_pass = 1;
+                t.pq_core = PREC == PREC_MIXED ? 1 : 0;
                 t.loss_slot = a.loss_part + tile;
                 t.Pg = a.Pg;
                 t.Qg = a.Qg;
@@ -597,17 +608,31 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
             }
         }
         if (!grid_sync(a.bar, G, epoch, a.err)) break;
-        // ---- phase 2: statistics and W' = sqrt(A/B)
-        for (int u = blockIdx.x; u < nunits; u += G) {
-            const int mt = u % FT, ks = u / FT;
-            stats_unit<PREC>(s, mt, ks, a.Pg, a.Qg, a.Hg, a.betap, 0, nb, smem, acc);
-            online_epilogue<PREC, PEN>(a, mt, ks, rho, acc);
-            __syncthreads();
+        if constexpr (PREC == PREC_MIXED) {
+            // ---- phase 2: [P H^T | Q H^T] partial sums on the tensor cores
+            const StatsSplit sp = stats_split(nb, (int)G, FT);
+            const int ng = (nb + 7) / 8;
+            for (int u = blockIdx.x; u < FT * sp.S; u += G)
+                stats_unit_tc(u % FT, u / FT, sp.gps, ng, a.betap / 8,
+                              reinterpret_cast<const unsigned char *>(a.Pg),
+                              reinterpret_cast<const unsigned char *>(a.Hg), a.part, s.K, s.Fp16,
+                              smem, tbase, sb, a.err);
+            if (!grid_sync(a.bar, G, epoch, a.err)) break;
+            // ---- phase 3: partial sums, A, B, W' = sqrt(A/B), rescale, image
+            column_step<PEN>(a, sp.S, rho, s_red8, blockIdx.x, gridDim.x);
+        } else {
+            // ---- phase 2: statistics and W' = sqrt(A/B)
+            for (int u = blockIdx.x; u < nunits; u += G) {
+                const int mt = u % FT, ks = u / FT;
+                stats_unit<PREC>(s, mt, ks, a.Pg, a.Qg, a.Hg, a.betap, 0, nb, smem, acc);
+                online_epilogue<PREC, PEN>(a, mt, ks, rho, acc);
+                __syncthreads();
+            }
+            if (!grid_sync(a.bar, G, epoch, a.err)) break;
+            // ---- phase 3: column sums, rescale, images, loss
+            normalize_columns<PREC>(s, a.normalize, a.Wn, a.Wcm, a.Wrm, a.Wimg, a.Wrow, a.A,
+                                    a.B, a.acc, a.swpart, a.err, s_red8, blockIdx.x, gridDim.x);
         }
-        if (!grid_sync(a.bar, G, epoch, a.err)) break;
-        // ---- phase 3: column sums, rescale, images, loss
-        normalize_columns<PREC>(s, a.normalize, a.Wn, a.Wcm, a.Wrm, a.Wimg, a.Wrow, a.A, a.B,
-                                a.acc, a.swpart, a.err, s_red8, blockIdx.x, gridDim.x);
         if (blockIdx.x == G - 1) {
             double l = block_sum_ordered(a.loss_part, ntiles, s_red);
             if (threadIdx.x == 0) *a.loss_sum += l;
@@ -615,10 +640,10 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
         if (PREC != PREC_FP32) asm volatile("fence.proxy.async.global;\n" ::: "memory");
         if (!lastmb && !grid_sync(a.bar, G, epoch, a.err)) break;
     }
-    if (PREC == PREC_TC) {
+    if (PREC == PREC_TC || PREC == PREC_MIXED) {
         tc_fence_before();
         __syncthreads();
-        if (threadIdx.x < 32) tmem_dealloc(tbase, kTmemCols);
+        if (threadIdx.x < 32) tmem_dealloc(tbase, PREC == PREC_TC ? kTmemCols : kStatsTmemCols);
     }
 }
 

@@ -3,9 +3,9 @@ through the C ABI: FP64 (default), FP32, and compensated FP32 (a float pair
 per entry).
 
   - every mode against the FP64 oracle on the small online workload
-    (F=129, K=8, beta=50, 5 inner iterations, 40 minibatches): FP32 path
-    within the stated 1e-5 on W, A, B, H and the loss, mixed path within
-    1e-2 (W, A, B, H) and 1e-3 (loss);
+    (F=129, K=8, beta=50, 5 inner iterations, 40 minibatches), element-wise
+    (helpers.parity): FP32 path within 1e-5 on W, A, B, H and the loss,
+    mixed path within test_gpu_online.MIXED_TOL;
   - on a long stream (4,000 minibatches) the compensated pair stays with
     FP64 to float rounding of W, while plain FP32 sums drift further;
   - onmf_get_stats / onmf_set_state convert the float pairs to doubles and

@@ -16,7 +16,9 @@ from test_gpu_online import run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 F, N, N_IN = 513, 112_500, 10
-PASS_TOL = dict(W=3e-2, A=3e-2, B=3e-2, objective=1e-3)
+# about three times the largest measured (W 4.3e-4, A 9.9e-4, B 3.0e-4 per
+# entry; objective 2.5e-7)
+PASS_TOL = dict(W=1.3e-3, A=3e-3, B=1e-3, objective=1e-4)
 
 
 @pytest.fixture(scope="module")

@@ -12,8 +12,7 @@ The oracle cannot redo 10^6 frames in a test, so:
   - sampled minibatches recomputed by the FP64 oracle from the GPU's own
     state before them (minibatch 500 and the last one): W, A, B after the
     step, the h of every frame of the minibatch and the loss increment,
-    element-wise within the one-minibatch bounds (test_gpu_online.MIXED_TOL;
-    rows of W, A, B including the last; 1e-3 for the loss).
+    element-wise within FULL_TOL (rows of W, A, B including the last).
 """
 import numpy as np
 import pytest
@@ -23,6 +22,11 @@ import paper_1106_4198_gb300 as onmf
 import synth
 from helpers import parity
 from test_gpu_online import MIXED_TOL
+
+# W, A, B after one step from a state of 500+ minibatches move little, so
+# their bounds are about three times the measured (W 1.0e-6, A 3.5e-6,
+# B 2.0e-6 per entry); H as for one minibatch.
+FULL_TOL = dict(W=3e-6, A=1.1e-5, B=6e-6, H=MIXED_TOL["H"], loss=MIXED_TOL["loss"])
 
 pytestmark = pytest.mark.gpu
 F, K, BETA, N_IN, N = 513, 100, 1000, 10, 1_000_000
@@ -105,4 +109,4 @@ def test_sampled_minibatch_against_oracle(runs, frames, piece):
     parity("minibatch %d of 1000 at full size" % (b // BETA),
            dict(W=(after["W"], o["W"]), A=(after["A"], o["A"]), B=(after["B"], o["B"]),
                 H=(H1[a:b].cpu().numpy(), o["H"]),
-                loss=(after["loss"] - before["loss"], o["loss_sum"])), MIXED_TOL)
+                loss=(after["loss"] - before["loss"], o["loss_sum"])), FULL_TOL)

@@ -56,8 +56,11 @@ def run_oracle(V, W0, beta, n_inner, eps=1e-12, r=1.0, n_ref=0, h_exponent=0.5,
 
 
 # Element-wise bounds of the mixed path (BF16 operands of the products,
-# FP32 ratios, FP64 or compensated A and B) for one minibatch.
-MIXED_TOL = dict(W=3e-2, A=3e-2, B=3e-2, H=1e-1, loss=1e-3)
+# FP32 ratios, FP64 or compensated A and B) for one minibatch: about three
+# times the largest error measured on a GB300 over the one-minibatch, warm,
+# penalty, accumulator and cluster tests (W 1.4e-3, A 5.5e-3, B 2.8e-3,
+# H 3.0e-3 per entry; loss 2.2e-5).
+MIXED_TOL = dict(W=4e-3, A=1.6e-2, B=9e-3, H=9e-3, loss=1e-4)
 
 
 def pairs_of(g, o, nframes=None):
@@ -106,7 +109,7 @@ def test_fp32_c1_pass_objective_trajectory():
     m.close()
     print("worst minibatch loss rel err %.2e" % worst)
     assert worst <= 1e-3
-    parity("C1 pass FP32", dict(W=(W, o["W"]), A=(A, o["A"]), B=(B, o["B"])), 1e-4)
+    parity("C1 pass FP32", dict(W=(W, o["W"]), A=(A, o["A"]), B=(B, o["B"])), 1e-5)
 
 
 def test_ragged_pushes_and_flush():

@@ -6,8 +6,9 @@ Checked here:
     (onmf_push_frames + onmf_flush per chunk), bit for bit;
   - a stream's results alone equal its results in a mix of streams with
     other dictionary sizes and chunk lengths, bit for bit;
-  - parity with the FP64 oracle run chunk by chunk (FP32 <= 1e-5; mixed
-    within the stated 1e-2 on W, 1e-3 on the losses);
+  - parity with the FP64 oracle run chunk by chunk, W element-wise and by
+    frequency row (FP32 <= 1e-5; mixed <= 4e-3, three times the measured
+    1.2e-3), every chunk's loss within 1e-5 / 1e-3;
   - admission by the memory budget: streams that do not fit wait and run
     once others close;
   - batches launched as captured CUDA graphs (the default) and as direct
@@ -130,7 +131,7 @@ def test_result_alone_equals_result_in_the_mix(precision):
 
 
 @pytest.mark.parametrize("precision,tol_w,tol_l", [(onmf.ONMF_FP32, 1e-5, 1e-5),
-                                                   (onmf.ONMF_MIXED, 3e-2, 1e-3)])
+                                                   (onmf.ONMF_MIXED, 4e-3, 1e-3)])
 def test_served_streams_match_oracle(precision, tol_w, tol_l):
     rng = np.random.default_rng(3)
     F = 129

@@ -4,8 +4,8 @@ frame's h-solve starts from its kept activation, frames are visited in a
 given order (a new permutation per pass), the final h goes back to its row.
 
 Checked against the FP64 oracle run on the same permuted frames and start
-points: FP32 within 1e-5 (W, A, B, H, loss), mixed within the stated 1e-2
-(W, A, B, H) and 1e-3 (loss); the identity order equals no order bit for
+points, element-wise (helpers.parity): FP32 within 1e-5 (W, A, B, H,
+loss), mixed within test_gpu_online.MIXED_TOL; the identity order equals no order bit for
 bit; fresh and warm frames never share a staged minibatch."""
 import numpy as np
 import pytest
