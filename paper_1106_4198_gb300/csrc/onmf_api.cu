@@ -341,11 +341,15 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
         AL(s->Hg, (size_t)(s->prec == PREC_MIXED ? 128 : sh.Kh) * s->betap * 2);
         if (s->prec == PREC_TC || s->prec == PREC_CL) AL(s->Wrow, (size_t)sh.F * sh.Kp * 2);
     }
-    // P and Q: on the mma path one interleaved core-matrix buffer in Pg
-    AL(s->Pg, (size_t)s->betap * sh.Fp16 * elem * (s->prec == PREC_MIXED ? 2 : 1));
+    // P and Q: on the mma path one interleaved core-matrix buffer in Pg,
+    // 2 KB per (64-frequency tile, 8-frame group)
+    const size_t pq_bytes = s->prec == PREC_MIXED
+                                ? (size_t)((sh.Fp16 + 63) / 64) * (s->betap / 8) * 2048
+                                : (size_t)s->betap * sh.Fp16 * elem;
+    AL(s->Pg, pq_bytes);
     AL(s->Qg, (size_t)s->betap * sh.Fp16 * elem);
     AL(s->loss_part, (size_t)nslots * 8);
-    AL(s->bar, 16);
+    AL(s->bar, 16 + 4 * kMaxRanges);
     AL(s->err_d, 16);
     AL(s->staging, (size_t)c.beta * c.F * 4);
     AL(s->Hstage, (size_t)c.beta * c.K * 4);
@@ -361,9 +365,7 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
     if (e == cudaSuccess)
         e = cudaMemsetAsync(s->Hg, 0,
                             (size_t)(s->prec == PREC_MIXED ? 128 : sh.Kh) * s->betap * elem, q);
-    if (e == cudaSuccess)
-        e = cudaMemsetAsync(s->Pg, 0,
-                            (size_t)s->betap * sh.Fp16 * elem * (s->prec == PREC_MIXED ? 2 : 1), q);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->Pg, 0, pq_bytes, q);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->Qg, 0, (size_t)s->betap * sh.Fp16 * elem, q);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->A, 0, FK * 8, q);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->B, 0, FK * 8, q);
@@ -420,7 +422,7 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
     if (s->prec == PREC_MIXED) {
         // partial sums of the frame ranges of a full minibatch (a partial
         // one has no more ranges)
-        const StatsSplit sp = stats_split(c.beta, s->grid, sh.Fp16 / 16);
+        const StatsSplit sp = stats_split(c.beta, s->grid, (sh.Fp16 + 63) / 64);
         if ((e = cudaMalloc((void **)&s->part, (size_t)sp.S * 2 * c.K * sh.Fp16 * 4)) !=
             cudaSuccess) {
             set_msg("cudaMalloc", e);

@@ -77,6 +77,38 @@ __device__ __forceinline__ bool grid_sync(unsigned *counter, unsigned nblocks,
     return s_ok != 0;
 }
 
+// The same barrier in two halves, so that a CTA can do work that no other
+// CTA waits for between its arrival and its wait (prefetching inputs of the
+// next phase). grid_arrive releases the CTA's writes made before it;
+// grid_wait returns false on timeout or a flagged error, like grid_sync.
+__device__ __forceinline__ void grid_arrive(unsigned *counter, unsigned &epoch) {
+    __syncthreads();
+    ++epoch;
+    if (threadIdx.x == 0) red_release_gpu_add(counter, 1u);
+}
+
+__device__ __forceinline__ bool grid_wait(unsigned *counter, unsigned nblocks, unsigned epoch,
+                                          int *err) {
+    __shared__ int s_okw;
+    if (threadIdx.x == 0) {
+        s_okw = 1;
+        const unsigned target = epoch * nblocks;
+        const uint64_t t0 = global_ns();
+        unsigned spins = 0;
+        while (ld_acquire_gpu(counter) < target) {
+            if (++spins > 1024) __nanosleep(32);
+            if ((spins & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
+                flag_error(err, ERR_TIMEOUT);
+                s_okw = 0;
+                break;
+            }
+        }
+        if (read_error(err) != 0) s_okw = 0;
+    }
+    __syncthreads();
+    return s_okw != 0;
+}
+
 // ---------------------------------------------------------------- BF16
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {

@@ -649,9 +649,9 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
     // ---- outputs
     if (t.final_pass && t.Pg && t.pq_core) {
         // core-matrix layout (8 frames x 16 bytes per core): the frames of
-        // this tile are frame group gi; f-tile ft of P and Q is one 512-byte
-        // block [P f 0-7 | P f 8-15 | Q f 0-7 | Q f 8-15], row j = frame; H
-        // is one 2 KB block per group, row k = 8 frames of h_k
+        // this tile are frame group gi; 64-frequency tile ft of P and Q is one
+        // 2 KB block [P f 0-7 | ... | P f 56-63 | Q f 0-7 | ... | Q f 56-63],
+        // row j = frame; H is one 2 KB block per group, row k = 8 frames of h_k
         unsigned char *PQc = reinterpret_cast<unsigned char *>(t.Pg);
         unsigned char *Hc = reinterpret_cast<unsigned char *>(t.Hg);
         const long long G = t.betap / 8, gi = t.j0 / 8;
@@ -661,8 +661,8 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
             for (int c = lane; c < cpr; c += 32) {
                 uint4 v = make_uint4(0, 0, 0, 0);
                 if (j < t.nvalid) v = *reinterpret_cast<const uint4 *>(PQ_s + row * WLD + 8 * c);
-                *reinterpret_cast<uint4 *>(PQc + ((long long)(c >> 1) * G + gi) * 512 +
-                                           (which * 2 + (c & 1)) * 128 + j * 16) = v;
+                *reinterpret_cast<uint4 *>(PQc + ((long long)(c >> 3) * G + gi) * 2048 +
+                                           (which * 8 + (c & 7)) * 128 + j * 16) = v;
             }
         }
         for (int k = tid; k < KS * 16; k += kThreads) {

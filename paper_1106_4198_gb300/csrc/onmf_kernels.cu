@@ -401,7 +401,7 @@ cudaError_t max_coresident_blocks(int prec, int ks, size_t smem, int *blocks_per
 
 cudaError_t launch_online(const StepArgs &a, int prec, int grid, size_t smem,
                           cudaStream_t stream) {
-    cudaError_t e = cudaMemsetAsync(a.bar, 0, sizeof(unsigned), stream);
+    cudaError_t e = cudaMemsetAsync(a.bar, 0, 16 + 4 * kMaxRanges, stream);
     if (e != cudaSuccess) return e;
     StepArgs copy = a;
     void *args[] = {&copy};

@@ -50,17 +50,20 @@ __host__ __device__ inline Shape make_shape(int F, int K) {
 }
 
 // Frame ranges of the tcgen05 statistics of the mma path (onmf_stats_tc.cuh).
+constexpr int kMaxRanges = 256;  // completion counters of the ranges, after the barrier word
 struct StatsSplit {
     int S;    // frame ranges
     int gps;  // 8-frame groups per range (even: whole 16-frame MMA steps)
 };
 
 // Frame ranges of a minibatch of nb frames for a grid of G CTAs and FT
-// 16-frequency tiles: enough ranges that the FT * S units fill the grid,
+// frequency tiles: FT * S units on about half of the grid (each range is one
+// more partial sum for the column pass to add, so fewer, longer ranges),
 // with at least one 16-frame step per range.
 __host__ __device__ inline StatsSplit stats_split(int nb, int G, int FT) {
     const int ng = (nb + 7) / 8;
-    int S = G / FT > 1 ? G / FT : 1;
+    int S = G / (2 * FT) > 1 ? G / (2 * FT) : 1;
+    if (S > kMaxRanges) S = kMaxRanges;
     const int steps = (ng + 1) / 2;
     if (S > steps) S = steps;
     if (S < 1) S = 1;
@@ -107,7 +110,7 @@ struct StepArgs {
     int betap;  // rows of Pg/Qg (and columns of the bf16 Hg)
     float *part;  // mma path: frame-range partial sums of P H^T, Q H^T
     double *loss_part;
-    unsigned *bar;
+    unsigned *bar;  // [0]: grid barrier; [4, 4 + kMaxRanges): frame-range counters
     int *err;
 };
 

@@ -3,10 +3,12 @@
 // tensor cores:
 //
 //   phase 2   a_fk = W_fk^2 sum_j P_jf H_kj,  b_fk = sum_j Q_jf H_kj  as one
-//             contraction per work unit (16 frequencies x one range of frames):
+//             contraction per work unit (64 frequencies x one range of frames):
 //             D[k, n] = sum_j H[k, j] [P | Q][j, n], M = 128 dictionary rows
-//             (K <= 128, rows past K are zero), N = 32 (16 frequencies of P,
-//             16 of Q), 16 frames per instruction; operands bulk-copied into
+//             (K <= 128, rows past K are zero), N = 128 (64 frequencies of P,
+//             64 of Q), 16 frames per instruction. An instruction of this
+//             shape costs about 200 clocks at any N up to 256 (measured on a
+//             GB300), so N is taken wide; operands bulk-copied into
 //             shared memory in core-matrix form (two stages, the copy of one
 //             chunk overlapping the MMAs of the other), the FP32 accumulator
 //             in tensor memory, read back with tcgen05.ld and written as one
@@ -18,16 +20,17 @@
 //             registers (one pass over the column).
 //
 // Global layouts (written by hsolve_tile_mixed with TileJob::pq_core):
-//   PQc  per (16-frequency tile t, 8-frame group g) a 512-byte block at
-//        (t * G + g) * 512: four core matrices [P f0-7 | P f8-15 | Q f0-7 |
-//        Q f8-15] of 8 rows (frames) x 16 bytes (8 bf16 frequencies);
+//   PQc  per (64-frequency tile t, 8-frame group g) a 2 KB block at
+//        (t * G + g) * 2048: sixteen core matrices [P f0-7 | ... | P f56-63 |
+//        Q f0-7 | ... | Q f56-63] of 8 rows (frames) x 16 bytes (8 bf16
+//        frequencies); frequencies past Fp16 stay zero;
 //   Hc   per group g a 2 KB block at g * 2048: 128 rows (k) x 16 bytes
 //        (8 bf16 frames); rows k >= K stay zero;
 //   part [split s][P or Q][k][Fp16] float partial sums (k < K).
 // In shared memory a chunk's groups sit back to back in the same form, so the
 // descriptors are: A (H, K-major) leading byte offset 2048 between 8-frame
 // cores, stride byte offset 128 between 8-row cores; B ([P|Q], MN-major)
-// leading byte offset 512 between 8-frame cores, stride byte offset 128
+// leading byte offset 2048 between 8-frame cores, stride byte offset 128
 // between 8-frequency cores.
 //
 // Included by onmf_step.cuh after the arithmetic of A and B (DF, ACC_*) and
@@ -40,10 +43,10 @@
 
 namespace onmf {
 
-constexpr int kStatsStageGroups = 24;                  // 8-frame groups per stage
-constexpr size_t kStatsStageBytes = (size_t)kStatsStageGroups * (2048 + 512);
+constexpr int kStatsStageGroups = 16;                  // 8-frame groups per stage
+constexpr size_t kStatsStageBytes = (size_t)kStatsStageGroups * (2048 + 2048);
 constexpr size_t kStatsSmemBytes = 2 * kStatsStageBytes;  // two stages
-constexpr uint32_t kStatsTmemCols = 32;
+constexpr uint32_t kStatsTmemCols = 128;
 
 // mbarriers of the statistics and their phase parities: two stages, each
 // with a bulk-copy barrier (ld) and an MMA-commit barrier (mma), tracked by
@@ -54,14 +57,14 @@ struct StatsBars {
     unsigned pl[2], pm[2], pd;
 };
 
-// One work unit of phase 2: f-tile t, frame range s (groups [s*gps, ...)),
-// in chunks of at most kStatsStageGroups groups through two shared-memory
-// stages: the bulk copy of chunk c+1 runs while the MMAs of chunk c do.
-// tcol: the CTA's tensor-memory columns (32).
+// One work unit of phase 2: 64-frequency tile t, frame range s (groups
+// [s*gps, ...)), in chunks of at most kStatsStageGroups groups through two
+// shared-memory stages: the bulk copy of chunk c+1 runs while the MMAs of
+// chunk c do. tcol: the CTA's tensor-memory columns (128).
 static __device__ void stats_unit_tc(int t, int s, int gps, int ng, long long G,
                                      const unsigned char *PQc, const unsigned char *Hc,
                                      float *part, int K, int Fp, unsigned char *smem,
-                                     uint32_t tcol, StatsBars &sb, int *err) {
+                                     uint32_t tcol, StatsBars &sb, unsigned *rcnt, int *err) {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g0 = s * gps, g1 = min(ng, g0 + gps);
     const int nch = (g1 - g0 + kStatsStageGroups - 1) / kStatsStageGroups;
@@ -69,26 +72,43 @@ static __device__ void stats_unit_tc(int t, int s, int gps, int ng, long long G,
     auto PQ_of = [&](int st) { return smem + st * kStatsStageBytes + kStatsStageGroups * 2048; };
     __syncthreads();  // the previous user of this shared memory is done
     if (tid == 0) {
+        // wait until every h-solve tile (8-frame group) of the range has
+        // published its rows (bounded like every wait here)
+        bool ok = true;
+        {
+            const unsigned need = (unsigned)(g1 - g0);
+            const uint64_t t0 = global_ns();
+            unsigned spins = 0;
+            while (ld_acquire_gpu(rcnt + s) < need) {
+                if ((++spins & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
+                    flag_error(err, ERR_TIMEOUT);
+                    ok = false;
+                    break;
+                }
+            }
+        }
         auto issue = [&](int c) {
             const int st = c & 1;
             const int a = g0 + c * kStatsStageGroups, n = min(kStatsStageGroups, g1 - a);
             fence_proxy_async_shared();
-            mbar_arrive_expect_tx(sb.ld[st], (unsigned)n * 2560u);
+            mbar_arrive_expect_tx(sb.ld[st], (unsigned)n * 4096u);
             bulk_g2s(H_of(st), Hc + (long long)a * 2048, (unsigned)n * 2048u, sb.ld[st]);
-            bulk_g2s(PQ_of(st), PQc + ((long long)t * G + a) * 512, (unsigned)n * 512u, sb.ld[st]);
+            bulk_g2s(PQ_of(st), PQc + ((long long)t * G + a) * 2048, (unsigned)n * 2048u,
+                     sb.ld[st]);
         };
-        bool ok = true;
-        issue(0);
-        if (nch > 1) issue(1);
-        const uint32_t id = tc_idesc(128, 32);
+        if (ok) issue(0);
+        if (ok && nch > 1) issue(1);
+        const uint32_t id = tc_idesc(128, 128);
         for (int c = 0; c < nch && ok; ++c) {
             const int st = c & 1;
             const int a = g0 + c * kStatsStageGroups, n = min(kStatsStageGroups, g1 - a);
             if (n & 1) {  // the last 16-frame step has one group: the other reads zero
                 uint4 *hz = reinterpret_cast<uint4 *>(H_of(st) + (size_t)n * 2048);
-                uint4 *pz = reinterpret_cast<uint4 *>(PQ_of(st) + (size_t)n * 512);
-                for (int i = 0; i < 2048 / 16; ++i) hz[i] = make_uint4(0, 0, 0, 0);
-                for (int i = 0; i < 512 / 16; ++i) pz[i] = make_uint4(0, 0, 0, 0);
+                uint4 *pz = reinterpret_cast<uint4 *>(PQ_of(st) + (size_t)n * 2048);
+                for (int i = 0; i < 2048 / 16; ++i) {
+                    hz[i] = make_uint4(0, 0, 0, 0);
+                    pz[i] = make_uint4(0, 0, 0, 0);
+                }
                 fence_proxy_async_shared();
             }
             ok = mbar_wait_bounded(sb.ld[st], sb.pl[st], err);
@@ -97,7 +117,7 @@ static __device__ void stats_unit_tc(int t, int s, int gps, int ng, long long G,
             tc_fence_after();
             for (int ks = 0; ks < (n + 1) / 2; ++ks)
                 tc_mma_smem_a(tcol, tc_desc(H_of(st) + (size_t)ks * 4096, 2048, 128),
-                              tc_desc(PQ_of(st) + (size_t)ks * 1024, 512, 128), id,
+                              tc_desc(PQ_of(st) + (size_t)ks * 4096, 2048, 128), id,
                               (c > 0 || ks > 0) ? 1u : 0u);
             if (c + 2 < nch) {
                 // the stage is refilled once its MMAs have read it
@@ -112,27 +132,46 @@ static __device__ void stats_unit_tc(int t, int s, int gps, int ng, long long G,
     const bool ok = mbar_wait_bounded(sb.done, sb.pd, err);
     sb.pd ^= 1u;
     tc_fence_after();
-    // accumulators: warp w reads lanes 32 (w % 4) .. (k) and the 16 columns of
-    // P (w < 4) or Q (w >= 4)
+    // accumulators: warp w reads lanes 32 (w % 4) .. (k) and the 64 columns of
+    // P (w < 4) or Q (w >= 4) into a shared-memory tile [P|Q][k][64 (+4 pad)]
+    // (both stages are free once the MMAs are done), so that the partial
+    // sums leave in whole rows; the tile's frequencies past Fp are not stored
+    constexpr int kRow = 68;  // floats per row: 16-byte chunks of 8 rows hit 8 bank groups
+    float *T = reinterpret_cast<float *>(smem);
     const int q = warp & 3, which = warp >> 2;
     const int k = 32 * q + lane;
-    uint32_t r0[8], r1[8];
-    const uint32_t ta = tcol + ((uint32_t)(32 * q) << 16) + 16u * which;
-    tmem_ld8_async(ta, r0);
-    tmem_ld8_async(ta + 8, r1);
-    tmem_wait_ld(r0);
-    tmem_wait_ld(r1);
-    if (ok && k < K) {
-        float4 *dst = reinterpret_cast<float4 *>(
-            part + (((long long)s * 2 + which) * K + k) * Fp + 16 * t);
-        dst[0] = make_float4(__uint_as_float(r0[0]), __uint_as_float(r0[1]),
-                             __uint_as_float(r0[2]), __uint_as_float(r0[3]));
-        dst[1] = make_float4(__uint_as_float(r0[4]), __uint_as_float(r0[5]),
-                             __uint_as_float(r0[6]), __uint_as_float(r0[7]));
-        dst[2] = make_float4(__uint_as_float(r1[0]), __uint_as_float(r1[1]),
-                             __uint_as_float(r1[2]), __uint_as_float(r1[3]));
-        dst[3] = make_float4(__uint_as_float(r1[4]), __uint_as_float(r1[5]),
-                             __uint_as_float(r1[6]), __uint_as_float(r1[7]));
+    const int nf = min(64, Fp - 64 * t);  // a multiple of 16
+    const uint32_t ta = tcol + ((uint32_t)(32 * q) << 16) + 64u * which;
+    float *trow = T + ((size_t)which * 128 + k) * kRow;
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 16) {
+        uint32_t r0[8], r1[8];
+        tmem_ld8_async(ta + c0, r0);
+        tmem_ld8_async(ta + c0 + 8, r1);
+        tmem_wait_ld(r0);
+        tmem_wait_ld(r1);
+        float4 *d4 = reinterpret_cast<float4 *>(trow + c0);
+        d4[0] = make_float4(__uint_as_float(r0[0]), __uint_as_float(r0[1]),
+                            __uint_as_float(r0[2]), __uint_as_float(r0[3]));
+        d4[1] = make_float4(__uint_as_float(r0[4]), __uint_as_float(r0[5]),
+                            __uint_as_float(r0[6]), __uint_as_float(r0[7]));
+        d4[2] = make_float4(__uint_as_float(r1[0]), __uint_as_float(r1[1]),
+                            __uint_as_float(r1[2]), __uint_as_float(r1[3]));
+        d4[3] = make_float4(__uint_as_float(r1[4]), __uint_as_float(r1[5]),
+                            __uint_as_float(r1[6]), __uint_as_float(r1[7]));
+    }
+    __syncthreads();
+    if (ok) {
+        // half a warp per row (16 float4 = 64 frequencies), rows (which, k)
+        const int c4 = lane & 15;
+        if (4 * c4 < nf)
+            for (int row = 2 * warp + (lane >> 4); row < 2 * K; row += 2 * kWarps) {
+                const int w2 = row >= K ? 1 : 0, k2 = row - w2 * K;
+                const float4 v =
+                    *reinterpret_cast<const float4 *>(T + ((size_t)w2 * 128 + k2) * kRow + 4 * c4);
+                *reinterpret_cast<float4 *>(part + (((long long)s * 2 + w2) * K + k2) * Fp + 64 * t +
+                                            4 * c4) = v;
+            }
     }
     tc_fence_before();
     __syncthreads();  // every read of the accumulator precedes the next MMA
@@ -183,37 +222,84 @@ __device__ __forceinline__ double ab_rescale(int accm, double raw, float sum, do
     return r;
 }
 
+// W, A, B of one column, in registers (thread tid: rows tid + u * kThreads).
+struct ColVals {
+    float w[kColPer];
+    double A[kColPer], B[kColPer];
+};
+
+// Load W, A, B of column k. They depend on no other CTA's work of this
+// minibatch, so a CTA loads its first column between its arrival at the grid
+// barrier before phase 3 and its wait there.
+__device__ __forceinline__ void col_load(const StepArgs &a, int k, ColVals &v) {
+    const int F = a.s.F;
+#pragma unroll
+    for (int u = 0; u < kColPer; ++u) {
+        const int f = threadIdx.x + u * kThreads;
+        if (f < F && k < a.s.K) {
+            const long long i = f + (long long)k * F;
+            v.w[u] = a.Wcm[i];
+            v.A[u] = a.A[i];
+            v.B[u] = a.B[i];
+        } else {
+            v.w[u] = 0.f;
+            v.A[u] = v.B[u] = 0.0;
+        }
+    }
+}
+
 // WPEN: the dictionary penalty mu * sum W, W' = sqrt(A/(B + mu)).
+// pre: W, A, B of the CTA's first column (k = first), loaded by col_load.
 template <bool WPEN>
 static __device__ void column_step(const StepArgs &a, int S, double rho, float *red8, int first,
-                                   int stride) {
+                                   int stride, const ColVals &pre) {
     const Shape &s = a.s;
     const int F = s.F, K = s.K, Fp = s.Fp16;
     const int tid = threadIdx.x;
     const int accm = a.acc;
+    const long long step = (long long)K * Fp;  // floats between P (or Q) partials of two ranges
     for (int k = first; k < K; k += stride) {
+        ColVals v;
+        if (k == first)
+            v = pre;
+        else
+            col_load(a, k, v);
+        // the frame ranges' partial sums, added in range order (eight ranges'
+        // loads in flight at a time; a missing range adds +0)
+        float ph[kColPer], qh[kColPer];
+#pragma unroll
+        for (int u = 0; u < kColPer; ++u) ph[u] = qh[u] = 0.f;
+        const float *pp = a.part + (long long)k * Fp + tid;
+        for (int r0 = 0; r0 < S; r0 += 8) {
+            float pv[8][kColPer], qv[8][kColPer];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int u = 0; u < kColPer; ++u) {
+                    const int f = tid + u * kThreads;
+                    const bool ok = r0 + j < S && f < F;
+                    const float *q = pp + (2LL * (r0 + j)) * step + u * kThreads;
+                    pv[j][u] = ok ? __ldcg(q) : 0.f;
+                    qv[j][u] = ok ? __ldcg(q + step) : 0.f;
+                }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int u = 0; u < kColPer; ++u) {
+                    ph[u] += pv[j][u];
+                    qh[u] += qv[j][u];
+                }
+        }
         float wn[kColPer];
-        double Ar[kColPer], Br[kColPer];
         float part_sum = 0.f;
 #pragma unroll
         for (int u = 0; u < kColPer; ++u) {
             const int f = tid + u * kThreads;
             wn[u] = 0.f;
             if (f < F) {
-                const long long i = f + (long long)k * F;
-                // the frame ranges' partial sums, added in range order
-                float ph = 0.f, qh = 0.f;
-                const float *pp = a.part + (long long)k * Fp + f;
-                const long long step = (long long)K * Fp;
-                for (int r = 0; r < S; ++r) {
-                    ph += __ldcg(pp + (2LL * r) * step);
-                    qh += __ldcg(pp + (2LL * r + 1) * step);
-                }
-                const float w = a.Wcm[i];
-                Ar[u] = a.A[i];
-                Br[u] = a.B[i];
-                const float An = ab_accumulate(accm, rho, a.rho_on_new, ph * w * w, Ar[u]);
-                const float Bn = ab_accumulate(accm, rho, a.rho_on_new, qh, Br[u]);
+                const float w = v.w[u];
+                const float An = ab_accumulate(accm, rho, a.rho_on_new, ph[u] * w * w, v.A[u]);
+                const float Bn = ab_accumulate(accm, rho, a.rho_on_new, qh[u], v.B[u]);
                 const float Bd = WPEN ? Bn + a.wpen : Bn;
                 wn[u] = (Bd > 0.f) ? sqrtf(__fdiv_rn(An, Bd)) : w;
                 part_sum += wn[u];
@@ -233,8 +319,8 @@ static __device__ void column_step(const StepArgs &a, int S, double rho, float *
                 const float wv = wn[u] * inv;
                 bad |= !isfinite(wv);
                 a.Wcm[i] = wv;
-                a.A[i] = sc ? ab_rescale(accm, Ar[u], sum, invd, sd, true) : Ar[u];
-                a.B[i] = sc ? ab_rescale(accm, Br[u], sum, invd, sd, false) : Br[u];
+                a.A[i] = sc ? ab_rescale(accm, v.A[u], sum, invd, sd, true) : v.A[u];
+                a.B[i] = sc ? ab_rescale(accm, v.B[u], sum, invd, sd, false) : v.B[u];
                 a.Wimg[(long long)k * s.WLD + f] = __float2bfloat16_rn(wv);
             }
         }

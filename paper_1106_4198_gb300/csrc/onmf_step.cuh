@@ -559,6 +559,9 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
     const int FT = s.Fp16 / 16, KT = s.Kh / 32;
     const int nunits = FT * KT;
     float *acc = reinterpret_cast<float *>(smem + stats_smem_bytes(PREC) - 2 * 16 * 32 * 4);
+    // mma path: the frames of this CTA's first tile of a minibatch were
+    // bulk-copied into shared memory during the previous minibatch
+    bool v_prefetched = false;
     for (int m = 0; m < a.nmb; ++m) {
         const bool lastmb = (m == a.nmb - 1);
         const int nb = lastmb ? a.nb_last : a.beta;
@@ -567,6 +570,11 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
         float *Hm = a.H_out ? a.H_out + (long long)m * a.beta * a.ldh : nullptr;
         const float *Him = a.H_in ? a.H_in + (long long)m * a.beta * a.ldh_in : nullptr;
         const int ntiles = ceil_div(nb, TILE);
+        // mma path: frame ranges of the statistics; a tile's range counter
+        // counts its h-solve done (phase 2 waits per range, not for the grid)
+        const int FT64 = (s.Fp16 + 63) / 64;
+        const StatsSplit sp = stats_split(nb, (int)G, FT64);
+        unsigned *rcnt = a.bar + 4;
         // ---- phase 1: h-solve of every tile
         if ((int)blockIdx.x < ntiles) {
             const float sw = sum_w(a.swpart, s.K, &s_tmp);
@@ -599,27 +607,66 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                 t.Qg = a.Qg;
                 t.Hg = a.Hg;
                 t.betap = a.betap;
+                t.v_staged = (PREC == PREC_MIXED && tile == (int)blockIdx.x && v_prefetched) ? 1 : 0;
+                v_prefetched = false;
                 if constexpr (PREC == PREC_TC)
                     hsolve_tile_tc<KS>(s, a.eps, a.gamma, sw, t, smem, tbase, &mbar[2], &mbar[3],
                                        parA, parB, &mbar[1], vpar, a.err);
                 else
                     hsolve_tile<PREC, KS, PEN>(s, a.eps, a.gamma, a.Wcm, a.Wrm, sw, t, smem, ws,
                                           &mbar[1], vpar, a.err);
+                if constexpr (PREC == PREC_MIXED) {
+                    // the tile's P, Q, H rows are written (the h-solve ends
+                    // with a CTA barrier): publish them to its frame range,
+                    // for the bulk copies (async proxy) of phase 2
+                    if (threadIdx.x == 0) {
+                        asm volatile("fence.proxy.async.global;\n" ::: "memory");
+                        red_release_gpu_add(rcnt + tile / sp.gps, 1u);
+                    }
+                }
             }
         }
-        if (!grid_sync(a.bar, G, epoch, a.err)) break;
+        if (PREC != PREC_MIXED && !grid_sync(a.bar, G, epoch, a.err)) break;
         if constexpr (PREC == PREC_MIXED) {
-            // ---- phase 2: [P H^T | Q H^T] partial sums on the tensor cores
-            const StatsSplit sp = stats_split(nb, (int)G, FT);
+            // ---- phase 2: [P H^T | Q H^T] partial sums on the tensor cores,
+            // each unit as soon as the h-solves of its frame range are done
             const int ng = (nb + 7) / 8;
-            for (int u = blockIdx.x; u < FT * sp.S; u += G)
-                stats_unit_tc(u % FT, u / FT, sp.gps, ng, a.betap / 8,
+            for (int u = blockIdx.x; u < FT64 * sp.S; u += G)
+                stats_unit_tc(u % FT64, u / FT64, sp.gps, ng, a.betap / 8,
                               reinterpret_cast<const unsigned char *>(a.Pg),
                               reinterpret_cast<const unsigned char *>(a.Hg), a.part, s.K, s.Fp16,
-                              smem, tbase, sb, a.err);
-            if (!grid_sync(a.bar, G, epoch, a.err)) break;
+                              smem, tbase, sb, rcnt, a.err);
+            // the frames of this CTA's first tile of the next minibatch start
+            // on their way into shared memory (phase 3 uses none of it), and
+            // W, A, B of its column load while the other CTAs finish phase 2
+            if (!lastmb) {
+                const int nbn = (m + 1 == a.nmb - 1) ? a.nb_last : a.beta;
+                const int tn = (int)blockIdx.x;
+                if (tn * TILE < nbn) {
+                    const float *Vt = a.V + ((long long)(m + 1) * a.beta + (long long)tn * TILE) * a.ldv;
+                    const int nv = min(TILE, nbn - tn * TILE);
+                    if (tile_bulk(Vt, a.ldv, s.F, nv)) {
+                        if (threadIdx.x == 0) {
+                            const unsigned bytes = (unsigned)((size_t)nv * s.F * 4);
+                            fence_proxy_async_shared();
+                            mbar_arrive_expect_tx(&mbar[1], bytes);
+                            bulk_g2s(smem + mixed_layout(s).yraw, Vt, bytes, &mbar[1]);
+                        }
+                        v_prefetched = true;
+                    }
+                }
+            }
+            grid_arrive(a.bar, epoch);
+            ColVals pre;
+            col_load(a, blockIdx.x, pre);
+            if (!grid_wait(a.bar, G, epoch, a.err)) break;
             // ---- phase 3: partial sums, A, B, W' = sqrt(A/B), rescale, image
-            column_step<PEN>(a, sp.S, rho, s_red8, blockIdx.x, gridDim.x);
+            column_step<PEN>(a, sp.S, rho, s_red8, blockIdx.x, gridDim.x, pre);
+            // the range counters start from zero in the next minibatch (every
+            // reader of them passed the barrier above; the next barrier
+            // orders these stores before the next increments)
+            if (blockIdx.x == 0)
+                for (int i = threadIdx.x; i < sp.S; i += kThreads) rcnt[i] = 0u;
         } else {
             // ---- phase 2: statistics and W' = sqrt(A/B)
             for (int u = blockIdx.x; u < nunits; u += G) {
@@ -640,6 +687,9 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
         if (PREC != PREC_FP32) asm volatile("fence.proxy.async.global;\n" ::: "memory");
         if (!lastmb && !grid_sync(a.bar, G, epoch, a.err)) break;
     }
+    // leaving early (a flagged error): a prefetched frame tile still in
+    // flight lands before the shared memory goes away
+    if (PREC == PREC_MIXED && v_prefetched) mbar_wait_bounded(&mbar[1], vpar, a.err);
     if (PREC == PREC_TC || PREC == PREC_MIXED) {
         tc_fence_before();
         __syncthreads();
