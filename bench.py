@@ -65,6 +65,9 @@ def parse():
                    help="wall window of the serving replay (0 skips serving)")
     p.add_argument("--serve-direct-seconds", type=float, default=10.0,
                    help="window of a second replay with direct launches (0 skips it)")
+    p.add_argument("--serve-fork-seconds", type=float, default=10.0,
+                   help="window of a replay whose h-solve is one launch per dictionary size "
+                        "(0 skips it)")
     p.add_argument("--serve-streams", type=int, default=256)
     p.add_argument("--serve-budget", type=int, default=1 << 30)
     return p.parse_args()
@@ -234,8 +237,9 @@ def run_ours(args):
     # unless --hsolve names one
     tune_cfg = onmf.onmf_config_default(F, K, precision=onmf.ONMF_MIXED, beta=BETA,
                                         n_inner=N_IN)
+    ranges, tune_ranges_us = 0, None
     if args.hsolve == "auto":
-        hsolve, tune_us, _ = onmf.onmf_autotune(tune_cfg, stream=stream)
+        hsolve, ranges, tune_us, tune_ranges_us, _ = onmf.onmf_autotune(tune_cfg, stream=stream)
     else:
         hsolve = [k for k, v in onmf.HSOLVE_NAMES.items() if v == args.hsolve][0]
         tune_us = None
@@ -252,7 +256,8 @@ def run_ours(args):
         for _ in range(2):
             for mode in (onmf.ONMF_ACC_FP64, onmf.ONMF_ACC_FP32, onmf.ONMF_ACC_FP32_COMP):
                 m = onmf.OnlineISNMF(F, K, W0, stream=stream, beta=BETA, n_inner=N_IN,
-                                     precision=onmf.ONMF_MIXED, hsolve=hsolve, accumulate=mode)
+                                     precision=onmf.ONMF_MIXED, hsolve=hsolve, accumulate=mode,
+                                     stats_ranges=ranges)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -290,7 +295,8 @@ def run_ours(args):
         m = onmf.OnlineISNMF(F, K, W0, stream=stream, beta=BETA, n_inner=N_IN,
                              precision=precision,
                              hsolve=hsolve if precision == onmf.ONMF_MIXED else 0,
-                             accumulate=acc if precision == onmf.ONMF_MIXED else 0)
+                             accumulate=acc if precision == onmf.ONMF_MIXED else 0,
+                             stats_ranges=ranges if precision == onmf.ONMF_MIXED else 0)
         for w in range(args.warmup):
             m.push(chunks[w % len(chunks)])
         m.sync()
@@ -328,7 +334,8 @@ def run_ours(args):
         host[0].copy_(chunks[0])
         host[1].copy_(chunks[1 % len(chunks)])
         m = onmf.OnlineISNMF(F, K, W0, stream=stream, beta=BETA, n_inner=N_IN,
-                             precision=onmf.ONMF_MIXED, hsolve=hsolve, accumulate=acc)
+                             precision=onmf.ONMF_MIXED, hsolve=hsolve, accumulate=acc,
+                             stats_ranges=ranges)
         for w in range(args.warmup):
             m.push(host[w % 2].numpy())
         m.sync()
@@ -434,6 +441,9 @@ def run_ours(args):
                        "hsolve": hname,
                        "accumulate": onmf.ACC_NAMES[acc],
                        "autotune_us_per_minibatch": tune_us,
+                       "stats_ranges": ranges,
+                       "autotune_stats_ranges_us": ({str(k): v for k, v in tune_ranges_us.items()}
+                                                    if tune_ranges_us else None),
                        "parallelism": "replicas" if world > 1 else "single"},
             "fp32_value": (total_frames / (fp32["ms"] / 1e3)) if fp32 else None,
             "fp32_clocks": fp32["clocks"] if fp32 else None,
@@ -641,6 +651,8 @@ def run_serving(args, precision, launch=0, window_s=None):
         "workload": "%d streams, K in {16,32,64,128}, F=513, chunks 8-512 frames, "
                     "Poisson arrivals at 4x real time, %.0f s replay" % (len(Ks), window_s),
         "launch": "cuda graph per batch" if launch == 0 else "direct kernel launches",
+        "hsolve_launches": ("one per dictionary size" if os.environ.get("ONMF_SERVE_FORK") == "1"
+                            else "one over all dictionary sizes"),
         "chunks": len(events), "frames": int(frames_done),
         "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat) else None,
         "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat) else None,
@@ -774,7 +786,13 @@ def run_study(precision):
       - initial dictionary: random Gamma(1,1) columns against 50 training
         frames (normalized), at beta = 1000, r = 0.7;
       - warm restarts: 5 passes with a new permutation each, one h update
-        per visit, kept activations started at the batch start point."""
+        per visit, kept activations started at the batch start point;
+      - forgetting factor over several passes (the small-set protocol of
+        Section 3: warm restarts, one h update per visit, W drawn from the
+        training frames): 2,000 training and 500 held-out frames, 10 passes
+        with a new permutation each, r in {0.5, 0.7, 0.9, 1} x beta in
+        {1, 10, 100, 1000}, rho = r^(beta / 2,000) (the past scaled by r per
+        pass); the held-out score after every pass."""
     import torch
 
     import paper_1106_4198_gb300 as onmf
@@ -843,11 +861,90 @@ def run_study(precision):
         warm.append({"pass": p + 1, "ms": t, "score": score(m.W())})
     m.close()
     best = min((g for g in grid if g["score"] is not None), key=lambda g: g["score"])
+    multipass = run_multipass_study(precision)
     return {"workload": "F=513 K=50 gamma-model spectrogram, 100,000 training and 12,500 "
                         "held-out frames; score = mean d_IS per held-out frame",
             "precision": "mixed" if precision == onmf.ONMF_MIXED else "fp32",
             "score_of_initial_W": score(W0),
-            "r_beta_grid": grid, "best": best, "init": init, "warm_passes": warm}
+            "r_beta_grid": grid, "best": best, "init": init, "warm_passes": warm,
+            "r_beta_grid_multipass": multipass}
+
+
+MP_TRAIN, MP_TEST, MP_PASSES = 2000, 500, 10
+
+
+def run_multipass_study(precision):
+    """Forgetting factor r and minibatch size beta over several passes of a
+    small training set (Section 3, small data set: warm restarts, one update
+    of h per visit, W initialized with training frames). rho = r^(beta/N)
+    with N the training-set size (reading R19), so one pass scales the past
+    by r. A setting is marked unstable when a pass leaves a non-finite W or
+    the held-out score rises by more than 1 % over the best pass before it."""
+    import torch
+
+    import paper_1106_4198_gb300 as onmf
+    import synth
+
+    F_, K_ = C2_F, C2_K
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    seed = synth.DATA_SEED + 5
+    Wstar = torch.as_tensor(synth.dictionary(F_, K_, seed), dtype=torch.float32, device=dev)
+    V = synth.device_frames(F_, K_, MP_TRAIN + MP_TEST, seed=seed, chunk=0, Wstar=Wstar)
+    Vtr, Vte = V[:MP_TRAIN].contiguous(), V[MP_TRAIN:].contiguous()
+    Hte = torch.empty((MP_TEST, K_), device=dev)
+    pick = np.random.default_rng(11).choice(MP_TRAIN, K_, replace=False)
+    W0 = Vtr[torch.as_tensor(pick, device=dev)].cpu().numpy().astype(np.float64)
+    W0 = (W0 / W0.sum(axis=1, keepdims=True)).astype(np.float32)
+
+    def score(W):
+        if not np.all(np.isfinite(W)):
+            return None
+        s = onmf.OnlineISNMF(F_, K_, W, stream=stream, beta=1000, n_inner=N_IN,
+                             precision=precision)
+        obj = s.project(Vte, Hte, n_inner=N_IN, want_obj=True)
+        s.close()
+        return obj / MP_TEST if np.isfinite(obj) else None
+
+    out = {"workload": "F=513 K=50 gamma-model spectrogram, %d training and %d held-out "
+                       "frames, %d permuted passes, warm restarts, one h update per visit, "
+                       "W0 = normalized training frames" % (MP_TRAIN, MP_TEST, MP_PASSES),
+           "score_of_initial_W": score(W0), "settings": []}
+    for r in STUDY_R:
+        for beta in STUDY_BETA:
+            m = onmf.OnlineISNMF(F_, K_, W0, stream=stream, beta=beta, n_inner=1,
+                                 precision=precision, r=r, n_ref=MP_TRAIN)
+            Wt = torch.as_tensor(W0, device=dev).contiguous()
+            Hk = torch.zeros((MP_TRAIN, K_), device=dev)
+            onmf.nmf_batch_init_H(Vtr, Wt, Hk, stream=stream)
+            rng = np.random.default_rng(12)
+            scores, ms, err = [], 0.0, None
+            for p in range(MP_PASSES):
+                order = torch.as_tensor(rng.permutation(MP_TRAIN), dtype=torch.int64, device=dev)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                try:
+                    m.push_warm(Vtr, Hk, order)
+                    m.flush()
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms += e0.elapsed_time(e1)
+                    scores.append(score(m.W()))
+                except onmf.OnmfError as x:  # a non-finite W stops the run
+                    err = str(x)
+                    break
+            m.close()
+            def rose(i):
+                before = [x for x in scores[:i] if x is not None]
+                return scores[i] is not None and bool(before) and scores[i] > 1.01 * min(before)
+
+            unstable = (err is not None or any(x is None for x in scores)
+                        or any(rose(i) for i in range(1, len(scores))))
+            out["settings"].append({"r": r, "beta": beta, "scores_per_pass": scores,
+                                    "ms_total": ms, "error": err, "unstable": bool(unstable),
+                                    "final": scores[-1] if scores else None})
+    return out
 
 
 def cpu_oracle_rate(n_mb, threads):
@@ -936,6 +1033,18 @@ def main():
                     k: d[k] for k in ("workload", "p50_ms", "p99_ms", "max_ms",
                                       "saturation_frames_per_s", "saturation_submit_s",
                                       "saturation_s", "launches")}
+            if args.serve_fork_seconds > 0:
+                # the h-solve as one launch per dictionary size on forked
+                # streams (the library's earlier form), for comparison
+                os.environ["ONMF_SERVE_FORK"] = "1"
+                try:
+                    d = run_serving(args, onmf.ONMF_MIXED, window_s=args.serve_fork_seconds)
+                finally:
+                    del os.environ["ONMF_SERVE_FORK"]
+                out["serving"]["hsolve_launch_per_size"] = {
+                    k: d[k] for k in ("workload", "p50_ms", "p99_ms", "max_ms",
+                                      "saturation_frames_per_s", "saturation_s", "launches",
+                                      "saturation_device_s")}
         print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -107,7 +107,11 @@ typedef struct {
     int32_t precision;  /* onmf_precision                                       */
     int32_t hsolve;     /* onmf_hsolve: h-solve kernel of the mixed path (0 = auto) */
     int32_t accumulate; /* onmf_accumulate: arithmetic of A and B (0 = FP64)    */
-    int32_t reserved;   /* must be 0                                            */
+    int32_t stats_ranges; /* mma h-solve path: frame ranges per frequency tile of
+                             the tcgen05 statistics (each range one partial sum
+                             per entry), 0..256; 0 = automatic (frequency tiles
+                             x ranges about half the CTAs); onmf_autotune
+                             searches it. Ignored elsewhere.                 */
     /* Penalties (Section 2.2, "Extensions"; FP32 path and the mma h-solve of
      * the mixed path, EINVAL with the others; 0 = none):
      * h_penalty lambda >= 0 on each frame's h, lambda * log(a + sum_k h_k)
@@ -329,11 +333,13 @@ void onmf_destroy(onmf_state *s);
  * (continuous batching: chunks that arrive while a batch runs join the next
  * one, and up to `slots` batches are in flight on separate CUDA streams).
  * A batch runs as three phases over all its (chunk, work unit) pairs: the
- * h-solve of every 8-frame tile (one kernel per dictionary size), the
- * statistics of every output tile, the rescale of every column. By default
- * the phases of a batch are one CUDA graph launch: the graph is captured
- * once per slot and set of dictionary sizes present, and reads the batch's
- * layout from device memory, so a batch needs no capture or update. Every
+ * h-solve of every 8-frame tile (one launch for every dictionary size in
+ * the batch; the environment variable ONMF_SERVE_FORK=1 selects one launch
+ * per size on forked streams instead), the statistics of every output tile,
+ * the rescale of every column. By default the phases of a batch are one
+ * CUDA graph launch: the graph is captured once per slot and reads the
+ * batch's layout from device memory, so a batch needs no capture or update
+ * whatever dictionary sizes it mixes. Every
  * work unit is computed in a fixed order of operations, so a chunk's result
  * does not depend on what it is batched with. Streams are admitted by a
  * device-memory budget: a stream whose state does not fit waits (its chunks
@@ -450,15 +456,23 @@ int64_t onmf_kernel_launches(void);
  * EINVAL (which out of range), ENOMEM, ECUDA. */
 onmf_status onmf_selftest_wait(int32_t which, void *stream, int64_t *elapsed_ns);
 
-/* Autotuner (no counterpart in the paper): time every mixed-precision
- * h-solve kernel the shape in *cfg allows (cfg->hsolve is ignored) on a
- * synthetic stream of 23 minibatches on `stream` (3 warm-up, 20 timed with
- * CUDA events) and return the fastest in *hsolve_out (ONMF_HSOLVE_*).
+/* Autotuner (no counterpart in the paper): time every schedule of the
+ * mixed-precision online step that the shape in *cfg allows (cfg->hsolve and
+ * cfg->stats_ranges are ignored) on a synthetic stream of 23 minibatches on
+ * `stream` (3 warm-up, 20 timed with CUDA events) and return the fastest.
+ * The candidates are the h-solve kernels, which fix the frames per tile
+ * (mma 8, tcgen05 16, cluster 32), and with the mma kernel the frame ranges
+ * of the tcgen05 statistics, stats_ranges in {0 (automatic), 2, 4, 8, 16}.
+ *   hsolve_out: the kernel (ONMF_HSOLVE_*); stats_ranges_out: NULL or its
+ *       statistics schedule (for onmf_config.stats_ranges).
  *   cache_path: NULL, or a file of JSON lines keyed by the device name, F,
- *       K, beta and n_inner; a hit returns the stored choice without timing
- *       (*from_cache = 1), a miss appends the new result.
- *   us_out: NULL or 4 doubles, microseconds per minibatch indexed by
- *       ONMF_HSOLVE_* (-1 for kernels not timed).
+ *       K, beta and n_inner (each line also records tile_frames); a hit
+ *       returns the stored choice without timing (*from_cache = 1), a miss
+ *       appends the new result.
+ *   us_out: NULL or 4 doubles, the best microseconds per minibatch of each
+ *       kernel, indexed by ONMF_HSOLVE_* (-1 for kernels not timed).
+ *   ranges_us_out: NULL or 5 doubles, the mma kernel's time for each
+ *       stats_ranges candidate in the order above (-1 if not timed).
  * On the FP32 path it returns AUTO without timing. Blocks until done.
  * A kernel whose run ends with an error that leaves the CUDA context usable
  * (a device wait that timed out, a launch its entry check refused) is left
@@ -466,7 +480,8 @@ onmf_status onmf_selftest_wait(int32_t which, void *stream, int64_t *elapsed_ns)
  * Errors: EINVAL (no kernel fits the shape), ENOMEM, ECUDA, ETIMEOUT (every
  * kernel that fits failed: the status of the last one). */
 onmf_status onmf_autotune(const onmf_config *cfg, void *stream, const char *cache_path,
-                          int32_t *hsolve_out, double *us_out, int32_t *from_cache);
+                          int32_t *hsolve_out, int32_t *stats_ranges_out, double *us_out,
+                          double *ranges_us_out, int32_t *from_cache);
 
 /* ABI version (ONMF_ABI_VERSION). */
 int32_t onmf_abi_version(void);

@@ -61,7 +61,7 @@ class onmf_config(ctypes.Structure):
         ("n_ref", ctypes.c_int64), ("h_exponent", ctypes.c_double),
         ("normalize", ctypes.c_int32), ("rho_on_new", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("hsolve", ctypes.c_int32),
-        ("accumulate", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("accumulate", ctypes.c_int32), ("stats_ranges", ctypes.c_int32),
         ("h_penalty", ctypes.c_double), ("h_penalty_a", ctypes.c_double),
         ("w_penalty", ctypes.c_double),
     ]
@@ -127,7 +127,8 @@ def lib():
     L.onmf_push_frames.argtypes = [_vp, _vp, _i64, _i64, _vp, _i64]
     L.onmf_push_frames_warm.argtypes = [_vp, _vp, _i64, _i64, _vp, _vp, _i64]
     L.onmf_autotune.argtypes = [ctypes.POINTER(onmf_config), _vp, ctypes.c_char_p,
-                                ctypes.POINTER(_i32), ctypes.POINTER(_d * 4),
+                                ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                ctypes.POINTER(_d * 4), ctypes.POINTER(_d * 5),
                                 ctypes.POINTER(_i32)]
     L.onmf_flush.argtypes = [_vp]
     L.onmf_synchronize.argtypes = [_vp]
@@ -299,18 +300,27 @@ def onmf_push_frames_warm(state, V, H, order=None):
     _check(lib().onmf_push_frames_warm(state, pv, ldv, n, po, ph, ldh), "onmf_push_frames_warm")
 
 
+STATS_RANGE_CANDIDATES = (0, 2, 4, 8, 16)
+
+
 def onmf_autotune(cfg, cache_path=None, stream=None):
-    """Time every mixed h-solve kernel the shape of cfg allows; returns
-    (hsolve, {name: us per minibatch}, from_cache)."""
+    """Time every schedule of the mixed online step the shape of cfg allows
+    (h-solve kernel; with the mma kernel, the statistics' frame ranges).
+    Returns (hsolve, stats_ranges, {kernel name: best us per minibatch},
+    {stats_ranges: us per minibatch of the mma kernel}, from_cache)."""
     h = _i32(0)
+    sr = _i32(0)
     us = (_d * 4)()
+    rus = (_d * 5)()
     fc = _i32(0)
     _check(lib().onmf_autotune(ctypes.byref(cfg), _stream_handle(stream),
                                cache_path.encode() if cache_path else None,
-                               ctypes.byref(h), ctypes.byref(us), ctypes.byref(fc)),
+                               ctypes.byref(h), ctypes.byref(sr), ctypes.byref(us),
+                               ctypes.byref(rus), ctypes.byref(fc)),
            "onmf_autotune")
     times = {HSOLVE_NAMES[i]: us[i] for i in (1, 2, 3) if us[i] >= 0}
-    return int(h.value), times, bool(fc.value)
+    ranges = {STATS_RANGE_CANDIDATES[i]: rus[i] for i in range(5) if rus[i] >= 0}
+    return int(h.value), int(sr.value), times, ranges, bool(fc.value)
 
 
 def onmf_flush(state):

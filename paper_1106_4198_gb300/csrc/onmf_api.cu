@@ -279,7 +279,8 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
         c.n_inner < 0 || c.n_inner > 100000 || !(c.eps >= 0.0) || !std::isfinite(c.eps) ||
         !(c.r >= 0.0 && c.r <= 1.0) || !(c.h_exponent > 0.0) || c.hsolve < 0 || c.hsolve > 3 ||
         (c.precision != ONMF_FP32 && c.precision != ONMF_MIXED) || c.accumulate < 0 ||
-        c.accumulate > 2 || c.reserved || !(c.h_penalty >= 0.0) || !std::isfinite(c.h_penalty) ||
+        c.accumulate > 2 || c.stats_ranges < 0 || c.stats_ranges > kMaxRanges ||
+        !(c.h_penalty >= 0.0) || !std::isfinite(c.h_penalty) ||
         !(c.h_penalty_a > 0.0) || !std::isfinite(c.h_penalty_a) || !(c.w_penalty >= 0.0) ||
         !std::isfinite(c.w_penalty))
         return ONMF_EINVAL;
@@ -422,7 +423,7 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
     if (s->prec == PREC_MIXED) {
         // partial sums of the frame ranges of a full minibatch (a partial
         // one has no more ranges)
-        const StatsSplit sp = stats_split(c.beta, s->grid, (sh.Fp16 + 63) / 64);
+        const StatsSplit sp = stats_split(c.beta, s->grid, (sh.Fp16 + 63) / 64, c.stats_ranges);
         if ((e = cudaMalloc((void **)&s->part, (size_t)sp.S * 2 * c.K * sh.Fp16 * 4)) !=
             cudaSuccess) {
             set_msg("cudaMalloc", e);
@@ -458,6 +459,7 @@ static onmf_status run_minibatches(onmf_state *s, const float *V, long long ldv,
     a.normalize = c.normalize;
     a.rho_on_new = c.rho_on_new;
     a.acc = c.accumulate;
+    a.stats_ranges = c.stats_ranges;
     a.hpen = (float)c.h_penalty;
     a.hpen_a = (float)c.h_penalty_a;
     a.wpen = (float)c.w_penalty;

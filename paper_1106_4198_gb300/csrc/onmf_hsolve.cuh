@@ -394,7 +394,9 @@ struct WStage {
     bool pending;
 };
 
-// The tensor-core h-solve of one tile (KS = Kp/16 k16 steps). W^T is in
+// The tensor-core h-solve of one tile (KS = Kp/16 k16 steps; KS = 0 takes
+// the count from the shape at run time, one instantiation for every
+// dictionary size, as the one-launch serving kernel uses). W^T is in
 // shared memory as bf16 (row k = column k of W). Per iteration:
 //   step A  x = eps + W h: each warp owns m16 row tiles (interleaved
 //           accumulator chains over the KS k-steps), then p = y/x^2 and
@@ -426,6 +428,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
     // sum_k h_k of the h before each update (Section 2.2, "Extensions")
     float *hpart = misc + 32;
     const int FT = Fp / 16;
+    const int NKS = KS > 0 ? KS : s.Kp / 16;  // k16 steps
 
 
     // ---- frame tile -> shared memory (bulk copy when contiguous and aligned;
@@ -482,7 +485,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
 
     // ---- h in registers: warp w < KS owns k = 16w + {2tq, 2tq+1, 8+2tq, 9+2tq}, frame g
     float hr[4] = {0.f, 0.f, 0.f, 0.f};
-    const bool hown = warp < KS;
+    const bool hown = warp < NKS;
     // PEN: this warp's share of frame g's sum_k h_k (the four lanes of frame
     // g add their entries; the tq = 0 lane writes)
     auto put_hsum = [&](int buf) {
@@ -534,7 +537,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
                 for (int e = 0; e < 4; ++e) d[i][e] = eps;
             const __nv_bfloat16 *wa = W_s + (r8 + 8 * (mi >> 1)) * WLD + 8 * (mi & 1) + 16 * mg;
 #pragma unroll
-            for (int ks = 0; ks < KS; ++ks) {
+            for (int ks = 0; ks < NKS; ++ks) {
                 const uint32_t b0 =
                     *reinterpret_cast<const uint32_t *>(H_s + g * HLD + 16 * ks + 2 * tq);
                 const uint32_t b1 =
@@ -626,7 +629,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
             if constexpr (PEN) {
                 // lambda psi'(s~) joins the denominator, s~ = sum_k h_k of frame g
                 float hs = 0.f;
-                for (int w = 0; w < KS; ++w) hs += hpart[((it & 1) * kWarps + w) * kTile + g];
+                for (int w = 0; w < NKS; ++w) hs += hpart[((it & 1) * kWarps + w) * kTile + g];
                 const float pen = t.hpen > 0.f ? __fdiv_rn(t.hpen, t.hpen_a + hs) : 0.f;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) den[e] += pen;
@@ -665,7 +668,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
                                            (which * 8 + (c & 7)) * 128 + j * 16) = v;
             }
         }
-        for (int k = tid; k < KS * 16; k += kThreads) {
+        for (int k = tid; k < NKS * 16; k += kThreads) {
             uint32_t w[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -692,7 +695,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
                 *reinterpret_cast<uint4 *>(dst + 8 * c) = v;
             }
         }
-        for (int k = tid; k < KS * 16; k += kThreads) {
+        for (int k = tid; k < NKS * 16; k += kThreads) {
             uint32_t w[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {

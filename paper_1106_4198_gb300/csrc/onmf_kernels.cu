@@ -335,6 +335,7 @@ cudaError_t configure_kernels() {
         fns.push_back(tile_fn(PREC_MIXED, ks, true));
     }
     for (int p = PREC_FP32; p <= PREC_MIXED; ++p) fns.push_back(serve_stats_fn(p));
+    fns.push_back(serve_any_fn());
     for (int ks = 1; ks <= 16; ++ks) {
         fns.push_back(cluster_online_fn(ks));
         fns.push_back(cluster_tile_fn(ks));

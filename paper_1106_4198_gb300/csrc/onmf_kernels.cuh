@@ -60,9 +60,10 @@ struct StatsSplit {
 // frequency tiles: FT * S units on about half of the grid (each range is one
 // more partial sum for the column pass to add, so fewer, longer ranges),
 // with at least one 16-frame step per range.
-__host__ __device__ inline StatsSplit stats_split(int nb, int G, int FT) {
+// S_req > 0 asks for that many ranges instead (onmf_config.stats_ranges).
+__host__ __device__ inline StatsSplit stats_split(int nb, int G, int FT, int S_req = 0) {
     const int ng = (nb + 7) / 8;
-    int S = G / (2 * FT) > 1 ? G / (2 * FT) : 1;
+    int S = S_req > 0 ? S_req : (G / (2 * FT) > 1 ? G / (2 * FT) : 1);
     if (S > kMaxRanges) S = kMaxRanges;
     const int steps = (ng + 1) / 2;
     if (S > steps) S = steps;
@@ -84,6 +85,7 @@ struct StepArgs {
     int normalize;
     int rho_on_new;
     int acc;  // arithmetic of A and B (ACC_*)
+    int stats_ranges;  // frame ranges of the tcgen05 statistics (0: automatic)
     float hpen, hpen_a, wpen;  // penalties (FP32 path): lambda, a, mu
     // frames
     const float *V;

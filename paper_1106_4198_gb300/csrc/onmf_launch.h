@@ -25,6 +25,7 @@ cudaError_t launch_prepare(const Shape &s, const float *Wcm, float *Wrm, __nv_bf
 bool tc_shape_supported(const Shape &s);
 const void *serve_gather_fn();                // serving phase 0 (frames to the device)
 const void *serve_fn(int prec, int ks);       // serving phase 1 (h-solve)
+const void *serve_any_fn();                   // phase 1 over every dictionary size at once
 const void *serve_stats_fn(int prec);         // serving phase 2 (statistics, W')
 const void *serve_rescale_fn(int prec);       // serving phase 3 (rescale, loss)
 cudaError_t launch_sum(const double *x, long long n, double *out, int accumulate,

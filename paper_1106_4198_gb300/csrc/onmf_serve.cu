@@ -4,11 +4,11 @@
 // Device side (onmf_serve.cuh): a batch of chunks of different streams,
 // dictionary sizes and lengths runs as three phases, each one launch over
 // all (chunk, work unit) pairs so even one chunk spreads over the GPU: the
-// h-solve of every 8-frame tile (one launch per dictionary size, on forked
-// streams), the statistics and W' of every (16 x 32) output tile, and the
-// column rescale with the chunk's loss. They use the tile functions of the
-// persistent single-stream kernel in the same order, so a chunk's result
-// does not depend on the batch it runs in.
+// h-solve of every 8-frame tile (one launch over every dictionary size: the
+// mma h-solve reads each chunk's size at run time), the statistics and W'
+// of every (16 x 32) output tile, and the column rescale with the chunk's
+// loss. Every (chunk, work unit) pair is computed in a fixed order of
+// operations, so a chunk's result does not depend on the batch it runs in.
 //
 // Host side: onmf_server_submit copies a chunk's frames once, into a buffer
 // of a pinned host arena mapped into the device's address space. A worker
@@ -16,9 +16,8 @@
 // nothing in flight (oldest chunk first), copies the batch's item table and
 // a header of its layout to the device and launches, on one of `slots` CUDA
 // streams, the gather of the frames from the arena and the three phases, by
-// default as one CUDA graph captured once per slot and set of dictionary
-// sizes (the kernels read the layout from the header, so the graph serves
-// every such batch unchanged); it records an event, and completed batches
+// default as one CUDA graph captured once per slot (the kernels read the
+// layout from the header, so the graph serves every batch unchanged); it records an event, and completed batches
 // give their arena buffers back and are turned into completion records with
 // submit/done timestamps. Stream states live in a device pool of
 // budget_bytes reserved at creation (first-fit free list); a stream that
@@ -250,6 +249,9 @@ struct onmf_server {
     onmf_server_config cfg;
     HostArena arena;  // declared before the slots and streams that hold its buffers
     int prec;
+    // mixed path: one h-solve launch over every dictionary size of a batch
+    // (default), or one launch per size on forked streams (ONMF_SERVE_FORK=1)
+    bool fork_sizes = false;
     int nsm = 1;
     size_t smem = 0;
     size_t cap_frames = 0;
@@ -367,10 +369,13 @@ static bool enqueue_phases(onmf_server *sv, Slot &sl, unsigned mask, const int *
     bool ok = cudaMemsetAsync(sl.d_err, 0, sizeof(int), q) == cudaSuccess;
     // phase 0: the frames from mapped host memory to the device
     if (ok) ok = launch(serve_gather_fn(), grid(work[11], 4 * nsm), 0, q, dg, dr);
-    // phase 1: the h-solve; on the mixed path one launch per dictionary size
-    // on its own stream (the kernels are specialized by size), then join
-    if (ok && sv->prec == PREC_FP32) {
-        ok = launch(serve_fn(PREC_FP32, 0), grid(work[0], nsm), sv->smem, q, dt, dr);
+    // phase 1: the h-solve, one launch over every chunk (the mixed kernel
+    // reads each chunk's dictionary size at run time); with fork_sizes, one
+    // launch per dictionary size (kernels specialized by size) on its own
+    // stream, then join
+    if (ok && (sv->prec == PREC_FP32 || !sv->fork_sizes)) {
+        ok = launch(sv->prec == PREC_FP32 ? serve_fn(PREC_FP32, 0) : serve_any_fn(),
+                    grid(work[0], nsm), sv->smem, q, dt, dr);
     } else if (ok) {
         ok = cudaEventRecord(sl.ev_fork, q) == cudaSuccess;
         for (int ks = 1; ok && ks <= 8; ++ks) {
@@ -564,8 +569,10 @@ static bool launch_batch_(onmf_server *sv, Slot &sl, std::unique_lock<std::mutex
     const int64_t form_ns = std::chrono::duration_cast<std::chrono::nanoseconds>(
                                 std::chrono::steady_clock::now() - t_form).count();
     int nlaunch = 0;
+    // one graph serves every batch unless the h-solve forks by size
+    const unsigned gkey = sv->fork_sizes ? mask : 0u;
     if (ok)
-        ok = sv->cfg.launch == ONMF_SERVE_GRAPH ? launch_graph(sv, sl, mask, nlaunch)
+        ok = sv->cfg.launch == ONMF_SERVE_GRAPH ? launch_graph(sv, sl, gkey, nlaunch)
                                                 : enqueue_phases(sv, sl, mask, work, false, nlaunch);
     if (ok) ok = cudaMemcpyAsync(sl.h_loss, sl.d_loss, n * 8, cudaMemcpyDeviceToHost, q) == cudaSuccess;
     if (ok && hoff) ok = cudaMemcpyAsync(sl.h_H, sl.d_H, hoff * 4, cudaMemcpyDeviceToHost, q) == cudaSuccess;
@@ -689,6 +696,10 @@ onmf_status onmf_server_create(const onmf_server_config *cfg, onmf_server **out)
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sv->nsm, cudaDevAttrMultiProcessorCount, dev);
     sv->smem = serve_smem(c.F, sv->prec);
+    {
+        const char *fk = getenv("ONMF_SERVE_FORK");
+        sv->fork_sizes = sv->prec != PREC_FP32 && fk && strcmp(fk, "1") == 0;
+    }
     if (sv->smem > max_dynamic_smem()) {
         delete sv;
         return ONMF_EINVAL;
@@ -751,7 +762,8 @@ onmf_status onmf_server_open_stream(onmf_server *sv, const onmf_config *cfg, con
     if (c.F != sv->cfg.F || c.K < 1 || c.K > 128 || c.n_inner < 0 || !(c.eps >= 0.0) ||
         !(c.h_exponent > 0.0) || !(c.r >= 0.0 && c.r <= 1.0) ||
         (c.hsolve != ONMF_HSOLVE_AUTO && c.hsolve != ONMF_HSOLVE_MMA) ||
-        c.accumulate != ONMF_ACC_FP64 || c.reserved || c.h_penalty != 0.0 || c.w_penalty != 0.0)
+        c.accumulate != ONMF_ACC_FP64 || c.stats_ranges < 0 || c.stats_ranges > kMaxRanges ||
+        c.h_penalty != 0.0 || c.w_penalty != 0.0)
         return ONMF_EINVAL;
     StreamRec r;
     r.cfg = c;

@@ -143,6 +143,65 @@ __global__ void __launch_bounds__(kThreads, 1) serve_hsolve_kernel(const ServeIt
     }
 }
 
+// Phase 1 of the mixed path over chunks of every dictionary size in ONE
+// launch: the mma h-solve with the k16-slab count read from each chunk's
+// shape at run time (the same operations in the same order as the per-size
+// instantiations serve_hsolve_kernel<PREC_MIXED, KS>), so a batch that mixes
+// dictionary sizes needs no launch per size.
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1) serve_hsolve_any_kernel(const ServeItem *items,
+                                                                      const int *off,
+                                                                      const int *range) {
+    static_assert(PREC == PREC_MIXED, "the FP32 h-solve is not specialized by size");
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ float s_tmp;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned wpar = 0, vpar = 0;
+    WStage ws{&mbar[0], &wpar, false};
+    int staged = -1;  // item whose W^T image is in shared memory
+    const int i0 = range[0], nitems = range[1] - i0;
+    items += i0;
+    off += i0;
+    const int base = off[0], total = off[nitems] - base;
+    for (int p = blockIdx.x; p < total; p += gridDim.x) {
+        const int i = serve_item_of(off, nitems, base + p);
+        const ServeItem &it = items[i];
+        const Shape s = it.s;
+        const int tile = base + p - off[i];
+        const float sw = sum_w(it.swpart, s.K, &s_tmp);
+        if (i != staged) {
+            issue_wimg(s, it.Wimg, smem, &mbar[0]);
+            ws.pending = true;
+            staged = i;
+        }
+        TileJob t;
+        t.Vt = it.V + (long long)tile * kTile * s.F;
+        t.ldv = s.F;
+        t.nvalid = min(kTile, it.n - tile * kTile);
+        t.j0 = (long long)tile * kTile;
+        t.H_in = nullptr;
+        t.ldh_in = 0;
+        t.H_out = it.H_out;
+        t.ldh = s.K;
+        t.n_in = it.n_in;
+        t.loss_first = 0;
+        t.final_pass = 1;
+        t.loss_slot = it.loss_part + tile;
+        t.Pg = it.Pg;
+        t.Qg = it.Qg;
+        t.Hg = it.Hg;
+        t.betap = it.betap;
+        hsolve_tile<PREC_MIXED, 0>(s, it.eps, it.gamma, it.Wcm, it.Wrm, sw, t, smem, ws, &mbar[1],
+                                   vpar, it.err);
+    }
+}
+
 // Phase 2: statistics, A, B and W' = sqrt(A/B) of (chunk, output tile) pairs.
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1) serve_stats_kernel(const ServeItem *items,

@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
         // mma path: frame ranges of the statistics; a tile's range counter
         // counts its h-solve done (phase 2 waits per range, not for the grid)
         const int FT64 = (s.Fp16 + 63) / 64;
-        const StatsSplit sp = stats_split(nb, (int)G, FT64);
+        const StatsSplit sp = stats_split(nb, (int)G, FT64, a.stats_ranges);
         unsigned *rcnt = a.bar + 4;
         // ---- phase 1: h-solve of every tile
         if ((int)blockIdx.x < ntiles) {

@@ -38,7 +38,7 @@ def test_config_layout_and_defaults():
     assert c.eps == 1e-12 and c.r == 1.0 and c.n_ref == 0
     assert c.h_exponent == 0.5 and c.normalize == 1 and c.rho_on_new == 0
     assert c.precision == onmf.ONMF_FP32 and c.hsolve == onmf.ONMF_HSOLVE_AUTO
-    assert c.accumulate == onmf.ONMF_ACC_FP64 and c.reserved == 0
+    assert c.accumulate == onmf.ONMF_ACC_FP64 and c.stats_ranges == 0
     assert c.h_penalty == 0.0 and c.h_penalty_a == 1.0 and c.w_penalty == 0.0
     assert onmf.onmf_abi_version() == 6
 
@@ -51,7 +51,7 @@ def test_status_strings():
 @pytest.mark.parametrize("field,value", [
     ("F", 0), ("K", 0), ("K", 257), ("beta", 0), ("n_inner", -1),
     ("eps", -1.0), ("r", 1.5), ("h_exponent", 0.0), ("precision", 7),
-    ("hsolve", 9), ("accumulate", 3), ("accumulate", -1), ("reserved", 1),
+    ("hsolve", 9), ("accumulate", 3), ("accumulate", -1), ("stats_ranges", -1), ("stats_ranges", 257),
     ("h_penalty", -0.1), ("h_penalty_a", 0.0), ("w_penalty", -1.0),
     ("h_penalty", float("nan")), ("w_penalty", float("inf")),
 ])

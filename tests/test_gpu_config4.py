@@ -30,10 +30,10 @@ def frames():
 @pytest.mark.parametrize("K", [64, 100, 256])
 def test_setting_full_pass(K, beta, frames, tmp_path):
     cfg = onmf.onmf_config_default(F, K, precision=onmf.ONMF_MIXED, beta=beta, n_inner=N_IN)
-    h, times, _ = onmf.onmf_autotune(cfg, str(tmp_path / "tune.jsonl"))
+    h, sr, times, _, _ = onmf.onmf_autotune(cfg, str(tmp_path / "tune.jsonl"))
     W0 = synth.init_dictionary(F, K)
     g = run_gpu(frames, W0, beta=beta, n_inner=N_IN, precision=onmf.ONMF_MIXED, hsolve=h,
-                want_H=False)
+                stats_ranges=sr, want_H=False)
     o = run_oracle(frames, W0, beta, N_IN)
     print("K=%d beta=%d h-solve %s (%s): objective %.6f" % (
         K, beta, onmf.HSOLVE_NAMES[h], {k: round(v, 1) for k, v in times.items()},

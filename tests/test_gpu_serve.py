@@ -155,6 +155,25 @@ def test_served_streams_match_oracle(precision, tol_w, tol_l):
         parity("served stream K=%d prec=%d" % (W0.shape[0], precision), dict(W=(W, Wo)), tol_w)
 
 
+def test_one_launch_equals_launch_per_size_bitwise(monkeypatch):
+    """The h-solve of a batch mixing dictionary sizes runs as one launch
+    (the mma h-solve reads each chunk's size at run time) or, with
+    ONMF_SERVE_FORK=1, as one launch per size of kernels specialized by
+    size: the same operations in the same order, the same bits."""
+    rng = np.random.default_rng(9)
+    F = 129
+    streams = []
+    for i, K in enumerate([16, 48, 100, 128, 24]):
+        V, W0 = problem(F, K, 200, seed=70 + i)
+        streams.append((V, W0, chunks_of(200, rng, 8, 120), dict(n_inner=4)))
+    one, _ = serve(streams, onmf.ONMF_MIXED)
+    monkeypatch.setenv("ONMF_SERVE_FORK", "1")
+    fork, _ = serve(streams, onmf.ONMF_MIXED)
+    for (Wa, la), (Wb, lb) in zip(one, fork):
+        assert np.array_equal(Wa, Wb)
+        assert la == lb
+
+
 def test_admission_by_budget():
     F, K = 129, 64
     srv = onmf.onmf_server_create(F, max_chunk=128, max_batch=16, slots=2,
