@@ -68,6 +68,15 @@ def parse():
     p.add_argument("--serve-fork-seconds", type=float, default=10.0,
                    help="window of a replay whose h-solve is one launch per dictionary size "
                         "(0 skips it)")
+    p.add_argument("--phase-timing", action="store_true",
+                   help="measurement build of the library (clock64 stamps at the phase "
+                        "boundaries of the online step): print the per-phase table and exit")
+    p.add_argument("--probe-tcgen05", action="store_true",
+                   help="build and run the tcgen05 issue-cost probe "
+                        "(paper_1106_4198_gb300/probes/tcgen05_issue.cu) and exit")
+    p.add_argument("--stats-ranges", type=int, default=-1,
+                   help="statistics schedule of the mma path (onmf_config.stats_ranges); "
+                        "-1: the autotuner's choice (or automatic with --hsolve given)")
     p.add_argument("--serve-streams", type=int, default=256)
     p.add_argument("--serve-budget", type=int, default=1 << 30)
     return p.parse_args()
@@ -237,9 +246,10 @@ def run_ours(args):
     # unless --hsolve names one
     tune_cfg = onmf.onmf_config_default(F, K, precision=onmf.ONMF_MIXED, beta=BETA,
                                         n_inner=N_IN)
-    ranges, tune_ranges_us = 0, None
+    ranges, tune_ranges_us = max(0, args.stats_ranges), None
     if args.hsolve == "auto":
-        hsolve, ranges, tune_us, tune_ranges_us, _ = onmf.onmf_autotune(tune_cfg, stream=stream)
+        hsolve, tuned, tune_us, tune_ranges_us, _ = onmf.onmf_autotune(tune_cfg, stream=stream)
+        ranges = tuned if args.stats_ranges < 0 else args.stats_ranges
     else:
         hsolve = [k for k, v in onmf.HSOLVE_NAMES.items() if v == args.hsolve][0]
         tune_us = None
@@ -996,8 +1006,95 @@ def run_reference(args):
     }
 
 
+PHASE_NAMES = ["h-solve", "wait after the h-solve", "statistics (tcgen05)",
+               "barrier before the column pass", "column pass + loss", "barrier before the next minibatch"]
+UNIT_NAMES = ["range wait -> first chunk in shared memory", "first chunk -> MMAs issued",
+              "MMAs done", "accumulators to shared memory", "partial-sum stores", "unit end"]
+
+
+def run_phase_timing(args):
+    """Per-phase timing of the online step (F=513, K=100, beta=1000, 10 inner
+    iterations, mixed, mma h-solve, compensated sums) from the measurement
+    build: 100 minibatches in one launch after a warm-up launch; per phase
+    the mean over all CTAs of the launch and the slowest CTA (averaged over
+    minibatches 1-98), in us at the SM clock measured from the launch's
+    CUDA-event time; the steps of the statistics units averaged over the
+    CTAs that run one."""
+    import ctypes
+
+    import torch
+
+    import paper_1106_4198_gb300 as onmf
+    import synth
+    L = onmf.lib()
+    L.onmf_phase_stamps.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                    ctypes.POINTER(ctypes.c_int32)]
+    ranges = max(0, args.stats_ranges)
+    nmb = 100
+    Wstar = torch.as_tensor(synth.dictionary(F, K, synth.DATA_SEED), dtype=torch.float32,
+                            device="cuda")
+    V = synth.device_frames(F, K, nmb * BETA, seed=synth.DATA_SEED, chunk=0, Wstar=Wstar)
+    m = onmf.OnlineISNMF(F, K, synth.init_dictionary(F, K), beta=BETA, n_inner=N_IN,
+                         precision=onmf.ONMF_MIXED, hsolve=onmf.ONMF_HSOLVE_MMA,
+                         accumulate=onmf.ONMF_ACC_FP32_COMP, stats_ranges=ranges)
+    buf = np.zeros(128 * 256 * 16, dtype=np.int64)
+    grid = ctypes.c_int32(0)
+    m.push(V)
+    assert L.onmf_phase_stamps(m.state, buf.ctypes.data, buf.size, ctypes.byref(grid)) == 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    m.push(V)
+    e1.record()
+    m.sync()
+    ms = e0.elapsed_time(e1)
+    assert L.onmf_phase_stamps(m.state, buf.ctypes.data, buf.size, ctypes.byref(grid)) == 0
+    m.close()
+    G = grid.value
+    st = buf[:nmb * G * 16].reshape(nmb, G, 16)
+    mb = slice(1, nmb - 1)
+    # SM clock: CTA 0's clock span of minibatches 1..98 against the event time
+    span = st[nmb - 1, 0, 0] - st[1, 0, 0]
+    ghz = float(span / (ms * 1e6 * (nmb - 2) / nmb))
+    out = {"workload": "F=513 K=100 beta=1000 n_inner=10, mixed, mma h-solve, compensated A/B, "
+                       "100 minibatches in one launch", "stats_ranges": ranges, "grid": G,
+           "us_per_minibatch": 1e3 * ms / nmb, "sm_ghz_from_clock64": ghz, "phases": {},
+           "statistics_unit": {}}
+    for i, nm in enumerate(PHASE_NAMES):
+        d = (st[mb, :, i + 1] - st[mb, :, i]) / ghz / 1e3
+        out["phases"][nm] = {"mean_us": float(d.mean()), "slowest_cta_us": float(d.max(axis=1).mean())}
+    u = st[mb, :, 8:15]
+    has = u[:, :, 0] != 0
+    for i, nm in enumerate(UNIT_NAMES):
+        d = np.where(has, (u[:, :, i + 1] - u[:, :, i]) / ghz / 1e3, np.nan)
+        out["statistics_unit"][nm] = float(np.nanmean(d))
+    return out
+
+
+def run_probe_tcgen05():
+    """Compile the tcgen05 issue-cost probe for sm_103a and run it; one JSON
+    object per configuration."""
+    here = os.path.dirname(os.path.abspath(__file__))
+    pkg = os.path.join(here, "paper_1106_4198_gb300")
+    src = os.path.join(pkg, "probes", "tcgen05_issue.cu")
+    exe = os.path.join(pkg, "probes", "tcgen05_issue")
+    nvcc = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "bin", "nvcc")
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                    "-I" + os.path.join(pkg, "csrc"), "-I" + os.path.join(here, "include"),
+                    src, "-o", exe], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, check=True)
+    return [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+
+
 def main():
     args = parse()
+    if args.probe_tcgen05:
+        print(json.dumps({"probe": "tcgen05.mma issue cost, one CTA", "rows": run_probe_tcgen05()}),
+              flush=True)
+        return
+    if args.phase_timing:
+        os.environ["ONMF_LIB_VARIANT"] = "phase"
+        print(json.dumps(run_phase_timing(args)), flush=True)
+        return
     if args.impl == "reference":
         out = run_reference(args)
         if out is not None:

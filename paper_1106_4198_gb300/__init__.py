@@ -114,11 +114,14 @@ def build(force=False):
 
 
 def lib():
-    """Load libonmf.so, building it first if it is missing or stale."""
+    """Load libonmf.so, building it first if it is missing or stale. With
+    ONMF_LIB_VARIANT=phase in the environment, the phase-timing build
+    (identical kernels plus clock64 stamps at the phase boundaries)."""
     global _LIB
     if _LIB is not None:
         return _LIB
-    path = _build_lib()
+    variant = os.environ.get("ONMF_LIB_VARIANT") or None
+    path = _build_lib(variant=variant)
     L = ctypes.CDLL(path)
     L.onmf_config_default.argtypes = [ctypes.POINTER(onmf_config), _i32, _i32]
     L.onmf_config_default.restype = None

@@ -35,16 +35,27 @@ def _deps():
             + [os.path.join(ROOT, "include", "onmf.h"), __file__])
 
 
-def stale():
-    if not os.path.exists(LIB):
+# Build variants: the library proper, and a measurement build whose online
+# kernel records clock64 stamps at its phase boundaries (ONMF_PHASE_STAMPS;
+# exported onmf_phase_stamps, used by bench.py --phase-timing).
+VARIANTS = {None: (LIB, BUILD, []),
+            "phase": (os.path.join(HERE, "libonmf_phase.so"), os.path.join(HERE, "_build_phase"),
+                      ["-DONMF_PHASE_STAMPS"])}
+
+
+def stale(variant=None):
+    lib = VARIANTS[variant][0]
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force=False, verbose=False):
-    """Compile every .cu under csrc/ and link libonmf.so; return its path."""
-    if not force and not stale():
+def build(force=False, verbose=False, variant=None):
+    """Compile every .cu under csrc/ and link libonmf.so (or the named
+    variant); return its path."""
+    LIB, BUILD, defs = VARIANTS[variant]
+    if not force and not stale(variant):
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
@@ -53,7 +64,7 @@ def build(force=False, verbose=False):
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         objs.append(obj)
-        cmd = [nvcc] + ARCH + FLAGS + ["-c", src, "-o", obj]
+        cmd = [nvcc] + ARCH + FLAGS + defs + ["-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd))
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE,

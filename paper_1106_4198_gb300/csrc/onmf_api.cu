@@ -118,6 +118,7 @@ struct onmf_state {
     // scratch
     void *Pg = nullptr, *Qg = nullptr, *Hg = nullptr;
     float *part = nullptr;  // frame-range partial sums of the tcgen05 statistics
+    long long *stamps = nullptr;  // phase-timing builds only
     int betap = 0;
     double *loss_part = nullptr, *tmp_sum = nullptr;
     unsigned *bar = nullptr;
@@ -254,7 +255,7 @@ void onmf_destroy(onmf_state *s) {
     cudaStreamSynchronize(s->stream);
     if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
     void *dev[] = {s->Wcm, s->Wrm, s->Wn, s->swpart, s->Wimg, s->Wrow, s->A, s->B, s->loss_sum, s->Pg,
-                   s->Qg, s->Hg, s->part, s->loss_part, s->tmp_sum, s->bar, s->err_d, s->staging,
+                   s->Qg, s->Hg, s->part, s->stamps, s->loss_part, s->tmp_sum, s->bar, s->err_d, s->staging,
                    s->Hstage, s->vring[0], s->vring[1], s->hring[0], s->hring[1],
                    s->gV,     s->gH,       s->Hin_stage, s->stage_idx};
     for (void *p : dev)
@@ -420,6 +421,16 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
         s->grid = std::min(want, per_sm * s->num_sms);
     }
     s->tile_grid = s->num_sms;
+#ifdef ONMF_PHASE_STAMPS
+    {
+        const size_t sb = (size_t)kStampMb * kStampCtas * kStampPts * 8;
+        if ((e = cudaMalloc((void **)&s->stamps, sb)) != cudaSuccess ||
+            (e = cudaMemsetAsync(s->stamps, 0, sb, q)) != cudaSuccess) {
+            set_msg("cudaMalloc", e);
+            return fail(ONMF_ENOMEM);
+        }
+    }
+#endif
     if (s->prec == PREC_MIXED) {
         // partial sums of the frame ranges of a full minibatch (a partial
         // one has no more ranges)
@@ -491,6 +502,7 @@ static onmf_status run_minibatches(onmf_state *s, const float *V, long long ldv,
     a.loss_part = s->loss_part;
     a.bar = s->bar;
     a.err = s->err_d;
+    a.stamps = s->stamps;
     if (s->prec == PREC_CL)
         CK(launch_online_cluster(a, s->C, s->grid, s->smem, s->stream));
     else
@@ -1183,5 +1195,23 @@ onmf_status nmf_batch_step(const float *V, int64_t ldv, float *W, float *H, int3
     batch_plan_free(p);
     return st;
 }
+
+#ifdef ONMF_PHASE_STAMPS
+// Phase-timing builds only (not part of the ABI in include/onmf.h): copies
+// the clock64 stamps of the state's last launch (kStampMb x kStampCtas x
+// kStampPts long longs, see onmf_kernels.cuh) to host memory and clears
+// them; *grid receives the CTAs of the online launch. Synchronizes.
+onmf_status onmf_phase_stamps(onmf_state *s, long long *host, int64_t n, int32_t *grid) {
+    if (!s || !host || !s->stamps) return ONMF_EINVAL;
+    const size_t sb = (size_t)kStampMb * kStampCtas * kStampPts * 8;
+    if ((size_t)n * 8 < sb) return ONMF_EINVAL;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess ||
+        cudaMemcpy(host, s->stamps, sb, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(s->stamps, 0, sb) != cudaSuccess)
+        return ONMF_ECUDA;
+    if (grid) *grid = s->grid;
+    return ONMF_OK;
+}
+#endif
 
 }  // extern "C"

@@ -114,7 +114,15 @@ struct StepArgs {
     double *loss_part;
     unsigned *bar;  // [0]: grid barrier; [4, 4 + kMaxRanges): frame-range counters
     int *err;
+    long long *stamps;  // phase-timing build only (ONMF_PHASE_STAMPS), else NULL
 };
+
+// Phase timing (a build option for measurement, ONMF_PHASE_STAMPS): thread 0
+// of every CTA writes clock64() at kStampPts points of each of the first
+// kStampMb minibatches of a launch, [minibatch][CTA][point]; points 0-6 are
+// the phase boundaries of the online step, 8-15 the steps of a statistics
+// unit (the CTA's last unit of the minibatch).
+constexpr int kStampMb = 128, kStampCtas = 256, kStampPts = 16;
 
 // Arguments of the projection / batch h-step kernels (no state update).
 struct TileArgs {

@@ -64,7 +64,19 @@ struct StatsBars {
 static __device__ void stats_unit_tc(int t, int s, int gps, int ng, long long G,
                                      const unsigned char *PQc, const unsigned char *Hc,
                                      float *part, int K, int Fp, unsigned char *smem,
-                                     uint32_t tcol, StatsBars &sb, unsigned *rcnt, int *err) {
+                                     uint32_t tcol, StatsBars &sb, unsigned *rcnt, int *err,
+                                     long long *ust) {
+    // ust: 8 clock64 slots of this unit (phase-timing builds), else NULL
+#ifdef ONMF_PHASE_STAMPS
+#define ONMF_USTAMP(i)                                     \
+    do {                                                   \
+        if (ust && threadIdx.x == 0) ust[(i)] = clock64(); \
+    } while (0)
+#else
+#define ONMF_USTAMP(i) \
+    do {               \
+    } while (0)
+#endif
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int g0 = s * gps, g1 = min(ng, g0 + gps);
     const int nch = (g1 - g0 + kStatsStageGroups - 1) / kStatsStageGroups;
@@ -87,6 +99,7 @@ static __device__ void stats_unit_tc(int t, int s, int gps, int ng, long long G,
                 }
             }
         }
+        ONMF_USTAMP(0);
         auto issue = [&](int c) {
             const int st = c & 1;
             const int a = g0 + c * kStatsStageGroups, n = min(kStatsStageGroups, g1 - a);
@@ -113,6 +126,7 @@ static __device__ void stats_unit_tc(int t, int s, int gps, int ng, long long G,
             }
             ok = mbar_wait_bounded(sb.ld[st], sb.pl[st], err);
             sb.pl[st] ^= 1u;
+            if (c == 0) ONMF_USTAMP(1);
             if (!ok) break;
             tc_fence_after();
             for (int ks = 0; ks < (n + 1) / 2; ++ks)
@@ -127,10 +141,12 @@ static __device__ void stats_unit_tc(int t, int s, int gps, int ng, long long G,
                 if (ok) issue(c + 2);
             }
         }
+        ONMF_USTAMP(2);
         tc_commit(sb.done);  // arrives once every MMA above is done
     }
     const bool ok = mbar_wait_bounded(sb.done, sb.pd, err);
     sb.pd ^= 1u;
+    ONMF_USTAMP(3);
     tc_fence_after();
     // accumulators: warp w reads lanes 32 (w % 4) .. (k) and the 64 columns of
     // P (w < 4) or Q (w >= 4) into a shared-memory tile [P|Q][k][64 (+4 pad)]
@@ -161,6 +177,7 @@ static __device__ void stats_unit_tc(int t, int s, int gps, int ng, long long G,
                             __uint_as_float(r1[6]), __uint_as_float(r1[7]));
     }
     __syncthreads();
+    ONMF_USTAMP(4);
     if (ok) {
         // half a warp per row (16 float4 = 64 frequencies), rows (which, k)
         const int c4 = lane & 15;
@@ -173,8 +190,11 @@ static __device__ void stats_unit_tc(int t, int s, int gps, int ng, long long G,
                                             4 * c4) = v;
             }
     }
+    ONMF_USTAMP(5);
     tc_fence_before();
     __syncthreads();  // every read of the accumulator precedes the next MMA
+    ONMF_USTAMP(6);
+#undef ONMF_USTAMP
 }
 
 // ---- phase 3: one dictionary column per CTA (strided), every value of the

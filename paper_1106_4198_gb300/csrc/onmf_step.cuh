@@ -570,6 +570,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
         float *Hm = a.H_out ? a.H_out + (long long)m * a.beta * a.ldh : nullptr;
         const float *Him = a.H_in ? a.H_in + (long long)m * a.beta * a.ldh_in : nullptr;
         const int ntiles = ceil_div(nb, TILE);
+        ONMF_STAMP(a.stamps, m, 0);
         // mma path: frame ranges of the statistics; a tile's range counter
         // counts its h-solve done (phase 2 waits per range, not for the grid)
         const int FT64 = (s.Fp16 + 63) / 64;
@@ -626,7 +627,9 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                 }
             }
         }
+        ONMF_STAMP(a.stamps, m, 1);
         if (PREC != PREC_MIXED && !grid_sync(a.bar, G, epoch, a.err)) break;
+        ONMF_STAMP(a.stamps, m, 2);
         if constexpr (PREC == PREC_MIXED) {
             // ---- phase 2: [P H^T | Q H^T] partial sums on the tensor cores,
             // each unit as soon as the h-solves of its frame range are done
@@ -635,7 +638,10 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                 stats_unit_tc(u % FT64, u / FT64, sp.gps, ng, a.betap / 8,
                               reinterpret_cast<const unsigned char *>(a.Pg),
                               reinterpret_cast<const unsigned char *>(a.Hg), a.part, s.K, s.Fp16,
-                              smem, tbase, sb, rcnt, a.err);
+                              smem, tbase, sb, rcnt, a.err,
+                              a.stamps ? a.stamps + ((long long)m * G + blockIdx.x) * 16 + 8
+                                       : nullptr);
+            ONMF_STAMP(a.stamps, m, 3);
             // the frames of this CTA's first tile of the next minibatch start
             // on their way into shared memory (phase 3 uses none of it), and
             // W, A, B of its column load while the other CTAs finish phase 2
@@ -660,6 +666,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
             ColVals pre;
             col_load(a, blockIdx.x, pre);
             if (!grid_wait(a.bar, G, epoch, a.err)) break;
+            ONMF_STAMP(a.stamps, m, 4);
             // ---- phase 3: partial sums, A, B, W' = sqrt(A/B), rescale, image
             column_step<PEN>(a, sp.S, rho, s_red8, blockIdx.x, gridDim.x, pre);
             // the range counters start from zero in the next minibatch (every
@@ -685,7 +692,9 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
             if (threadIdx.x == 0) *a.loss_sum += l;
         }
         if (PREC != PREC_FP32) asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        ONMF_STAMP(a.stamps, m, 5);
         if (!lastmb && !grid_sync(a.bar, G, epoch, a.err)) break;
+        ONMF_STAMP(a.stamps, m, 6);
     }
     // leaving early (a flagged error): a prefetched frame tile still in
     // flight lands before the shared memory goes away
