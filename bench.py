@@ -800,9 +800,10 @@ def run_study(precision):
       - forgetting factor over several passes (the small-set protocol of
         Section 3: warm restarts, one h update per visit, W drawn from the
         training frames): 2,000 training and 500 held-out frames, 10 passes
-        with a new permutation each, r in {0.5, 0.7, 0.9, 1} x beta in
-        {1, 10, 100, 1000}, rho = r^(beta / 2,000) (the past scaled by r per
-        pass); the held-out score after every pass."""
+        with a new permutation each, r in {0.1, 0.3, 0.5, 0.7, 0.9, 1} x beta
+        in {1, 10, 100, 1000}, rho = r^(beta / 2,000) (the past scaled by r
+        per pass), and the literal placement of rho (on the new statistics)
+        at r in {0.1, 0.5}; the held-out score after every pass."""
     import torch
 
     import paper_1106_4198_gb300 as onmf
@@ -881,6 +882,7 @@ def run_study(precision):
 
 
 MP_TRAIN, MP_TEST, MP_PASSES = 2000, 500, 10
+MP_R = (0.1, 0.3, 0.5, 0.7, 0.9, 1.0)
 
 
 def run_multipass_study(precision):
@@ -920,40 +922,43 @@ def run_multipass_study(precision):
                        "frames, %d permuted passes, warm restarts, one h update per visit, "
                        "W0 = normalized training frames" % (MP_TRAIN, MP_TEST, MP_PASSES),
            "score_of_initial_W": score(W0), "settings": []}
-    for r in STUDY_R:
-        for beta in STUDY_BETA:
-            m = onmf.OnlineISNMF(F_, K_, W0, stream=stream, beta=beta, n_inner=1,
-                                 precision=precision, r=r, n_ref=MP_TRAIN)
-            Wt = torch.as_tensor(W0, device=dev).contiguous()
-            Hk = torch.zeros((MP_TRAIN, K_), device=dev)
-            onmf.nmf_batch_init_H(Vtr, Wt, Hk, stream=stream)
-            rng = np.random.default_rng(12)
-            scores, ms, err = [], 0.0, None
-            for p in range(MP_PASSES):
-                order = torch.as_tensor(rng.permutation(MP_TRAIN), dtype=torch.int64, device=dev)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                try:
-                    m.push_warm(Vtr, Hk, order)
-                    m.flush()
-                    e1.record(stream)
-                    e1.synchronize()
-                    ms += e0.elapsed_time(e1)
-                    scores.append(score(m.W()))
-                except onmf.OnmfError as x:  # a non-finite W stops the run
-                    err = str(x)
-                    break
-            m.close()
-            def rose(i):
-                before = [x for x in scores[:i] if x is not None]
-                return scores[i] is not None and bool(before) and scores[i] > 1.01 * min(before)
+    cases = [(r, beta, 0) for r in MP_R for beta in STUDY_BETA]
+    cases += [(r, beta, 1) for r in (0.1, 0.5) for beta in STUDY_BETA]
+    for r, beta, on_new in cases:
+        m = onmf.OnlineISNMF(F_, K_, W0, stream=stream, beta=beta, n_inner=1,
+                             precision=precision, r=r, n_ref=MP_TRAIN, rho_on_new=on_new)
+        Wt = torch.as_tensor(W0, device=dev).contiguous()
+        Hk = torch.zeros((MP_TRAIN, K_), device=dev)
+        onmf.nmf_batch_init_H(Vtr, Wt, Hk, stream=stream)
+        rng = np.random.default_rng(12)
+        scores, ms, err = [], 0.0, None
+        for p in range(MP_PASSES):
+            order = torch.as_tensor(rng.permutation(MP_TRAIN), dtype=torch.int64, device=dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            try:
+                m.push_warm(Vtr, Hk, order)
+                m.flush()
+                e1.record(stream)
+                e1.synchronize()
+                ms += e0.elapsed_time(e1)
+                scores.append(score(m.W()))
+            except onmf.OnmfError as x:  # a non-finite W stops the run
+                err = str(x)
+                break
+        m.close()
 
-            unstable = (err is not None or any(x is None for x in scores)
-                        or any(rose(i) for i in range(1, len(scores))))
-            out["settings"].append({"r": r, "beta": beta, "scores_per_pass": scores,
-                                    "ms_total": ms, "error": err, "unstable": bool(unstable),
-                                    "final": scores[-1] if scores else None})
+        def rose(i):
+            before = [x for x in scores[:i] if x is not None]
+            return scores[i] is not None and bool(before) and scores[i] > 1.01 * min(before)
+
+        unstable = (err is not None or any(x is None for x in scores)
+                    or any(rose(i) for i in range(1, len(scores))))
+        out["settings"].append({"r": r, "beta": beta, "rho_on_new": on_new,
+                                "scores_per_pass": scores,
+                                "ms_total": ms, "error": err, "unstable": bool(unstable),
+                                "final": scores[-1] if scores else None})
     return out
 
 
