@@ -1057,21 +1057,39 @@ def run_phase_timing(args):
     G = grid.value
     st = buf[:nmb * G * 16].reshape(nmb, G, 16)
     mb = slice(1, nmb - 1)
-    # SM clock: CTA 0's clock span of minibatches 1..98 against the event time
-    span = st[nmb - 1, 0, 0] - st[1, 0, 0]
-    ghz = float(span / (ms * 1e6 * (nmb - 2) / nmb))
+    ns = st[:, :, :7]   # %globaltimer, ns
+    clk = st[:, :, 8:15]  # clock64 of the statistics units
+    # SM clock: CTA 0's unit clock against its globaltimer over the units
+    has = clk[mb, :, 0] != 0
     out = {"workload": "F=513 K=100 beta=1000 n_inner=10, mixed, mma h-solve, compensated A/B, "
                        "100 minibatches in one launch", "stats_ranges": ranges, "grid": G,
-           "us_per_minibatch": 1e3 * ms / nmb, "sm_ghz_from_clock64": ghz, "phases": {},
-           "statistics_unit": {}}
+           "us_per_minibatch": 1e3 * ms / nmb, "critical_path_us": {}, "per_cta_mean_us": {},
+           "statistics_unit_us": {}}
+    # critical path of a minibatch (all CTAs on one clock): the h-solve from
+    # the first CTA's start to the last CTA's end, then each later step from
+    # the end of the one before it (the last CTA) to its own end (the last
+    # CTA), the barriers from the last arrival to the first CTA through
+    first = lambda i: ns[mb, :, i].min(axis=1)
+    last = lambda i: ns[mb, :, i].max(axis=1)
+    nxt = ns[2:nmb, :, 0].min(axis=1)  # start of the next minibatch
+    cp = {"h-solve": last(1) - first(0),
+          "statistics (tcgen05, after the last h-solve)": last(3) - last(1),
+          "barrier before the column pass": first(4) - last(3),
+          "column pass + loss": last(5) - first(4),
+          "barrier before the next minibatch": nxt - last(5)}
+    for k, v in cp.items():
+        out["critical_path_us"][k] = float(np.mean(v)) / 1e3
+    out["critical_path_us"]["sum"] = float(sum(np.mean(v) for v in cp.values())) / 1e3
     for i, nm in enumerate(PHASE_NAMES):
-        d = (st[mb, :, i + 1] - st[mb, :, i]) / ghz / 1e3
-        out["phases"][nm] = {"mean_us": float(d.mean()), "slowest_cta_us": float(d.max(axis=1).mean())}
-    u = st[mb, :, 8:15]
-    has = u[:, :, 0] != 0
+        d = (ns[mb, :, i + 1] - ns[mb, :, i]) / 1e3
+        out["per_cta_mean_us"][nm] = float(d.mean())
+    span_clk = clk[mb, :, 6] - clk[mb, :, 0]
+    span_ns = st[mb, :, 15] - st[mb, :, 7]
+    ghz = float(np.median(span_clk[has] / np.maximum(span_ns[has], 1)))
+    out["sm_ghz_estimate"] = ghz
     for i, nm in enumerate(UNIT_NAMES):
-        d = np.where(has, (u[:, :, i + 1] - u[:, :, i]) / ghz / 1e3, np.nan)
-        out["statistics_unit"][nm] = float(np.nanmean(d))
+        d = np.where(has, (clk[mb, :, i + 1] - clk[mb, :, i]) / ghz / 1e3, np.nan)
+        out["statistics_unit_us"][nm] = float(np.nanmean(d))
     return out
 
 

@@ -109,13 +109,15 @@ __device__ __forceinline__ bool grid_wait(unsigned *counter, unsigned nblocks, u
     return s_okw != 0;
 }
 
-// clock64 of thread 0 into stamps[(m * gridDim.x + blockIdx.x) * 16 + i]
-// (phase-timing builds; compiled out otherwise).
+// %globaltimer (ns, one clock for all SMs) of thread 0 into
+// stamps[(m * gridDim.x + blockIdx.x) * 16 + i] (phase-timing builds;
+// compiled out otherwise).
 #ifdef ONMF_PHASE_STAMPS
 #define ONMF_STAMP(stamps, m, i)                                                              \
     do {                                                                                      \
         if ((stamps) && threadIdx.x == 0 && (m) < 128)                                        \
-            (stamps)[((long long)(m) * gridDim.x + blockIdx.x) * 16 + (i)] = clock64();        \
+            (stamps)[((long long)(m) * gridDim.x + blockIdx.x) * 16 + (i)] =                  \
+                (long long)global_ns();                                                       \
     } while (0)
 #else
 #define ONMF_STAMP(stamps, m, i) \

@@ -118,10 +118,11 @@ struct StepArgs {
 };
 
 // Phase timing (a build option for measurement, ONMF_PHASE_STAMPS): thread 0
-// of every CTA writes clock64() at kStampPts points of each of the first
+// of every CTA writes a time at kStampPts points of each of the first
 // kStampMb minibatches of a launch, [minibatch][CTA][point]; points 0-6 are
-// the phase boundaries of the online step, 8-15 the steps of a statistics
-// unit (the CTA's last unit of the minibatch).
+// the phase boundaries of the online step (%globaltimer, ns), 8-14 the steps
+// of a statistics unit (clock64, the CTA's last unit of the minibatch), 7
+// and 15 the %globaltimer at the unit's first and last step.
 constexpr int kStampMb = 128, kStampCtas = 256, kStampPts = 16;
 
 // Arguments of the projection / batch h-step kernels (no state update).

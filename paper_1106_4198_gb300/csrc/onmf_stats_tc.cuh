@@ -100,6 +100,9 @@ static __device__ void stats_unit_tc(int t, int s, int gps, int ng, long long G,
             }
         }
         ONMF_USTAMP(0);
+#ifdef ONMF_PHASE_STAMPS
+        if (ust) ust[-1] = (long long)global_ns();  // clock64 and ns at both ends
+#endif
         auto issue = [&](int c) {
             const int st = c & 1;
             const int a = g0 + c * kStatsStageGroups, n = min(kStatsStageGroups, g1 - a);
@@ -194,6 +197,9 @@ static __device__ void stats_unit_tc(int t, int s, int gps, int ng, long long G,
     tc_fence_before();
     __syncthreads();  // every read of the accumulator precedes the next MMA
     ONMF_USTAMP(6);
+#ifdef ONMF_PHASE_STAMPS
+    if (ust && threadIdx.x == 0) ust[7] = (long long)global_ns();
+#endif
 #undef ONMF_USTAMP
 }
 
