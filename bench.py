@@ -1042,7 +1042,7 @@ def run_phase_timing(args):
     m = onmf.OnlineISNMF(F, K, synth.init_dictionary(F, K), beta=BETA, n_inner=N_IN,
                          precision=onmf.ONMF_MIXED, hsolve=onmf.ONMF_HSOLVE_MMA,
                          accumulate=onmf.ONMF_ACC_FP32_COMP, stats_ranges=ranges)
-    buf = np.zeros(128 * 256 * 16, dtype=np.int64)
+    buf = np.zeros(128 * 256 * 32, dtype=np.int64)
     grid = ctypes.c_int32(0)
     m.push(V)
     assert L.onmf_phase_stamps(m.state, buf.ctypes.data, buf.size, ctypes.byref(grid)) == 0
@@ -1055,7 +1055,7 @@ def run_phase_timing(args):
     assert L.onmf_phase_stamps(m.state, buf.ctypes.data, buf.size, ctypes.byref(grid)) == 0
     m.close()
     G = grid.value
-    st = buf[:nmb * G * 16].reshape(nmb, G, 16)
+    st = buf[:nmb * G * 32].reshape(nmb, G, 32)
     mb = slice(1, nmb - 1)
     ns = st[:, :, :7]   # %globaltimer, ns
     clk = st[:, :, 8:15]  # clock64 of the statistics units
@@ -1090,6 +1090,21 @@ def run_phase_timing(args):
     for i, nm in enumerate(UNIT_NAMES):
         d = np.where(has, (clk[mb, :, i + 1] - clk[mb, :, i]) / ghz / 1e3, np.nan)
         out["statistics_unit_us"][nm] = float(np.nanmean(d))
+    # the h-solve tile of every CTA that has one (clock64)
+    hs = st[mb, :, 16:31]
+    hh = hs[:, :, 0] != 0
+    steps = {"frames staged and converted": (0, 1), "W^T image in shared memory": (1, 2),
+             "inner iteration 1": (2, 3), "inner iterations 2-10 (mean)": None,
+             "final ratios and loss": (12, 13), "P, Q, H rows written": (13, 14)}
+    out["hsolve_tile_us"] = {}
+    for nm, ij in steps.items():
+        if ij is None:
+            d = (hs[:, :, 12] - hs[:, :, 3]) / 9.0
+        else:
+            d = hs[:, :, ij[1]] - hs[:, :, ij[0]]
+        out["hsolve_tile_us"][nm] = float(np.mean(d[hh])) / ghz / 1e3
+    out["hsolve_tile_us"]["clocks per inner iteration 2-10"] = float(
+        np.mean(((hs[:, :, 12] - hs[:, :, 3]) / 9.0)[hh]))
     return out
 
 

@@ -110,13 +110,13 @@ __device__ __forceinline__ bool grid_wait(unsigned *counter, unsigned nblocks, u
 }
 
 // %globaltimer (ns, one clock for all SMs) of thread 0 into
-// stamps[(m * gridDim.x + blockIdx.x) * 16 + i] (phase-timing builds;
+// stamps[(m * gridDim.x + blockIdx.x) * 32 + i] (phase-timing builds;
 // compiled out otherwise).
 #ifdef ONMF_PHASE_STAMPS
 #define ONMF_STAMP(stamps, m, i)                                                              \
     do {                                                                                      \
         if ((stamps) && threadIdx.x == 0 && (m) < 128)                                        \
-            (stamps)[((long long)(m) * gridDim.x + blockIdx.x) * 16 + (i)] =                  \
+            (stamps)[((long long)(m) * gridDim.x + blockIdx.x) * 32 + (i)] =                  \
                 (long long)global_ns();                                                       \
     } while (0)
 #else

@@ -45,7 +45,20 @@ struct TileJob {
     // mixed path: write P, Q and H in the core-matrix layout of the tcgen05
     // statistics (stats_tc.cuh) instead of frame rows
     int pq_core = 0;
+    // phase-timing builds: 16 clock64 slots of this tile's steps, or NULL
+    long long *hst = nullptr;
 };
+
+#ifdef ONMF_PHASE_STAMPS
+#define ONMF_HSTAMP(t, i)                                      \
+    do {                                                       \
+        if ((t).hst && threadIdx.x == 0) (t).hst[(i)] = clock64(); \
+    } while (0)
+#else
+#define ONMF_HSTAMP(t, i) \
+    do {                  \
+    } while (0)
+#endif
 
 // Whether a tile's frames go to shared memory by one bulk copy: contiguous
 // rows (ld = F), a 16-byte aligned start and a multiple of 16 bytes.
@@ -431,6 +444,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
     const int NKS = KS > 0 ? KS : s.Kp / 16;  // k16 steps
 
 
+    ONMF_HSTAMP(t, 0);
     // ---- frame tile -> shared memory (bulk copy when contiguous and aligned;
     //      possibly issued already by the previous tile)
     {
@@ -475,6 +489,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
         }
     }
     __syncthreads();
+    ONMF_HSTAMP(t, 1);
     // the raw frames are no longer needed: the next tile's go into the buffer
     if (t.Vnext && tid == 0) {
         const unsigned nb = (unsigned)((size_t)t.nvalid_next * F * 4);
@@ -520,6 +535,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
         ws.pending = false;
     }
     __syncthreads();
+    ONMF_HSTAMP(t, 2);
 
     float lacc = 0.f;
     for (int it = 0;; ++it) {
@@ -591,7 +607,10 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
                 ratios(IntTag<0>{});
         }
         __syncthreads();
-        if (last) break;
+        if (last) {
+            ONMF_HSTAMP(t, 13);
+            break;
+        }
 
         // ---- step B: [W^T p | W^T q] and the h update
         if (hown) {
@@ -647,6 +666,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
             if constexpr (PEN) put_hsum((it + 1) & 1);
         }
         __syncthreads();
+        if (it < 10) ONMF_HSTAMP(t, 3 + it);
     }
 
     // ---- outputs
@@ -711,6 +731,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
                 make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
+    ONMF_HSTAMP(t, 14);
     if (t.H_out && hown && g < t.nvalid) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {

@@ -123,7 +123,11 @@ struct StepArgs {
 // the phase boundaries of the online step (%globaltimer, ns), 8-14 the steps
 // of a statistics unit (clock64, the CTA's last unit of the minibatch), 7
 // and 15 the %globaltimer at the unit's first and last step.
-constexpr int kStampMb = 128, kStampCtas = 256, kStampPts = 16;
+// Points 16-31: the CTA's first h-solve tile of the minibatch (clock64):
+// 16 tile start, 17 frames in shared memory and converted, 18 W^T image in
+// shared memory, 19 + i end of inner iteration i (up to 10), 29 final ratios
+// and loss, 30 P, Q, H rows written.
+constexpr int kStampMb = 128, kStampCtas = 256, kStampPts = 32;
 
 // Arguments of the projection / batch h-step kernels (no state update).
 struct TileArgs {

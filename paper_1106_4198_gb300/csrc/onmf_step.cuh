@@ -609,6 +609,11 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                 t.Hg = a.Hg;
                 t.betap = a.betap;
                 t.v_staged = (PREC == PREC_MIXED && tile == (int)blockIdx.x && v_prefetched) ? 1 : 0;
+#ifdef ONMF_PHASE_STAMPS
+                t.hst = (a.stamps && tile == (int)blockIdx.x && m < kStampMb)
+                            ? a.stamps + ((long long)m * G + blockIdx.x) * 32 + 16
+                            : nullptr;
+#endif
                 v_prefetched = false;
                 if constexpr (PREC == PREC_TC)
                     hsolve_tile_tc<KS>(s, a.eps, a.gamma, sw, t, smem, tbase, &mbar[2], &mbar[3],
@@ -639,7 +644,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                               reinterpret_cast<const unsigned char *>(a.Pg),
                               reinterpret_cast<const unsigned char *>(a.Hg), a.part, s.K, s.Fp16,
                               smem, tbase, sb, rcnt, a.err,
-                              a.stamps ? a.stamps + ((long long)m * G + blockIdx.x) * 16 + 8
+                              a.stamps ? a.stamps + ((long long)m * G + blockIdx.x) * 32 + 8
                                        : nullptr);
             ONMF_STAMP(a.stamps, m, 3);
             // the frames of this CTA's first tile of the next minibatch start
