@@ -47,6 +47,8 @@ struct TileJob {
     int pq_core = 0;
     // phase-timing builds: 16 clock64 slots of this tile's steps, or NULL
     long long *hst = nullptr;
+    // mma path: frames already staged and converted (mixed_stage_frames)
+    int v_ready = 0;
 };
 
 #ifdef ONMF_PHASE_STAMPS
@@ -400,6 +402,67 @@ __device__ __forceinline__ void issue_wimg(const Shape &s, const __nv_bfloat16 *
     }
 }
 
+// The frames of a tile of the mma h-solve into shared memory (bulk copy
+// when contiguous and aligned, possibly issued already: TileJob::v_staged),
+// then each frame's sum_f y_f (the start point's numerator), the input check
+// and the f-major copy y = eps + v. It needs V alone, so the online step
+// runs it for a CTA's next tile while the CTA waits at a grid barrier
+// (TileJob::v_ready then skips it in the h-solve).
+static __device__ void mixed_stage_frames(const Shape &s, float eps, const TileJob &t,
+                                          unsigned char *smem, uint64_t *vbar,
+                                          unsigned &vparity, int *err) {
+    const int F = s.F, Fp = s.Fp16;
+    const MixedLayout L = mixed_layout(s);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float *y_raw = reinterpret_cast<float *>(smem + L.yraw);
+    float *yT = reinterpret_cast<float *>(smem + L.yt);
+    float *sy = reinterpret_cast<float *>(smem + L.misc);
+    // ---- frame tile -> shared memory (bulk copy when contiguous and aligned;
+    //      possibly issued already by the previous tile)
+    {
+        const size_t bytes = (size_t)t.nvalid * F * 4;
+        const bool bulk = tile_bulk(t.Vt, t.ldv, F, t.nvalid);
+        __syncthreads();
+        if (bulk) {
+            if (tid == 0 && !t.v_staged) {
+                fence_proxy_async_shared();
+                mbar_arrive_expect_tx(vbar, (unsigned)bytes);
+                bulk_g2s(y_raw, t.Vt, (unsigned)bytes, vbar);
+            }
+        } else {
+            for (int i = tid; i < t.nvalid * F; i += kThreads) {
+                int j = i / F, f = i - j * F;
+                y_raw[i] = __ldg(t.Vt + (long long)j * t.ldv + f);
+            }
+        }
+        if (bulk) {
+            mbar_wait_bounded(vbar, vparity, err);
+            vparity ^= 1u;
+        }
+        __syncthreads();
+    }
+    // frame sums and input check (warp j: frame j), f-major copy of y
+    {
+        float a = 0.f;
+        if (warp < t.nvalid) {
+            for (int f = lane; f < F; f += 32) {
+                float v = y_raw[warp * F + f];
+                if (bad_value(v)) flag_error(err, ERR_INPUT);
+                a += eps + v;
+            }
+        } else {
+            a = (float)F;  // placeholder frames: y = 1
+        }
+        a = warp_sum(a);
+        if (lane == 0) sy[warp] = a;
+        for (int i = tid; i < Fp * kTile; i += kThreads) {
+            const int f = i >> 3, j = i & 7;
+            yT[i] = (j < t.nvalid && f < F) ? eps + y_raw[j * F + f] : 1.f;
+        }
+    }
+    __syncthreads();
+}
+
 // Pending bulk copy of W^T that a tile must wait for before its first use.
 struct WStage {
     uint64_t *bar;
@@ -445,50 +508,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
 
 
     ONMF_HSTAMP(t, 0);
-    // ---- frame tile -> shared memory (bulk copy when contiguous and aligned;
-    //      possibly issued already by the previous tile)
-    {
-        const size_t bytes = (size_t)t.nvalid * F * 4;
-        const bool bulk = tile_bulk(t.Vt, t.ldv, F, t.nvalid);
-        __syncthreads();
-        if (bulk) {
-            if (tid == 0 && !t.v_staged) {
-                fence_proxy_async_shared();
-                mbar_arrive_expect_tx(vbar, (unsigned)bytes);
-                bulk_g2s(y_raw, t.Vt, (unsigned)bytes, vbar);
-            }
-        } else {
-            for (int i = tid; i < t.nvalid * F; i += kThreads) {
-                int j = i / F, f = i - j * F;
-                y_raw[i] = __ldg(t.Vt + (long long)j * t.ldv + f);
-            }
-        }
-        if (bulk) {
-            mbar_wait_bounded(vbar, vparity, err);
-            vparity ^= 1u;
-        }
-        __syncthreads();
-    }
-    // frame sums and input check (warp j: frame j), f-major copy of y
-    {
-        float a = 0.f;
-        if (warp < t.nvalid) {
-            for (int f = lane; f < F; f += 32) {
-                float v = y_raw[warp * F + f];
-                if (bad_value(v)) flag_error(err, ERR_INPUT);
-                a += eps + v;
-            }
-        } else {
-            a = (float)F;  // placeholder frames: y = 1
-        }
-        a = warp_sum(a);
-        if (lane == 0) sy[warp] = a;
-        for (int i = tid; i < Fp * kTile; i += kThreads) {
-            const int f = i >> 3, j = i & 7;
-            yT[i] = (j < t.nvalid && f < F) ? eps + y_raw[j * F + f] : 1.f;
-        }
-    }
-    __syncthreads();
+    if (!t.v_ready) mixed_stage_frames(s, eps, t, smem, vbar, vparity, err);
     ONMF_HSTAMP(t, 1);
     // the raw frames are no longer needed: the next tile's go into the buffer
     if (t.Vnext && tid == 0) {

@@ -559,9 +559,35 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
     const int FT = s.Fp16 / 16, KT = s.Kh / 32;
     const int nunits = FT * KT;
     float *acc = reinterpret_cast<float *>(smem + stats_smem_bytes(PREC) - 2 * 16 * 32 * 4);
-    // mma path: the frames of this CTA's first tile of a minibatch were
-    // bulk-copied into shared memory during the previous minibatch
-    bool v_prefetched = false;
+    // mma path: the frames of this CTA's first tile of the next minibatch
+    // are bulk-copied into shared memory during the current one (right after
+    // the CTA's h-solve when that buffer lies outside the statistics' shared
+    // memory, else after the statistics) and staged and converted while the
+    // CTA waits at the barrier before the column pass
+    bool v_prefetched = false, v_ready = false;
+    const bool early_v = PREC == PREC_MIXED && mixed_layout(a.s).yraw >= kStatsSmemBytes;
+    // the CTA's first tile of minibatch mb (false: none, or not one bulk copy)
+    auto first_tile = [&](int mb, TileJob &tn) -> bool {
+        const int nbn = (mb == a.nmb - 1) ? a.nb_last : a.beta;
+        const int tn0 = (int)blockIdx.x;
+        if (tn0 * TILE >= nbn) return false;
+        tn.Vt = a.V + ((long long)mb * a.beta + (long long)tn0 * TILE) * a.ldv;
+        tn.ldv = a.ldv;
+        tn.nvalid = min(TILE, nbn - tn0 * TILE);
+        tn.v_staged = 1;
+        return tile_bulk(tn.Vt, a.ldv, a.s.F, tn.nvalid);
+    };
+    auto prefetch = [&](int mb) {
+        TileJob tn;
+        if (!first_tile(mb, tn)) return;
+        if (threadIdx.x == 0) {
+            const unsigned bytes = (unsigned)((size_t)tn.nvalid * a.s.F * 4);
+            fence_proxy_async_shared();
+            mbar_arrive_expect_tx(&mbar[1], bytes);
+            bulk_g2s(smem + mixed_layout(a.s).yraw, tn.Vt, bytes, &mbar[1]);
+        }
+        v_prefetched = true;
+    };
     for (int m = 0; m < a.nmb; ++m) {
         const bool lastmb = (m == a.nmb - 1);
         const int nb = lastmb ? a.nb_last : a.beta;
@@ -608,7 +634,8 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                 t.Qg = a.Qg;
                 t.Hg = a.Hg;
                 t.betap = a.betap;
-                t.v_staged = (PREC == PREC_MIXED && tile == (int)blockIdx.x && v_prefetched) ? 1 : 0;
+                t.v_ready = (PREC == PREC_MIXED && tile == (int)blockIdx.x && v_ready) ? 1 : 0;
+                v_ready = false;
 #ifdef ONMF_PHASE_STAMPS
                 t.hst = (a.stamps && tile == (int)blockIdx.x && m < kStampMb)
                             ? a.stamps + ((long long)m * G + blockIdx.x) * 32 + 16
@@ -632,6 +659,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                 }
             }
         }
+        if (early_v && !lastmb) prefetch(m + 1);
         ONMF_STAMP(a.stamps, m, 1);
         if (PREC != PREC_MIXED && !grid_sync(a.bar, G, epoch, a.err)) break;
         ONMF_STAMP(a.stamps, m, 2);
@@ -647,29 +675,21 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                               a.stamps ? a.stamps + ((long long)m * G + blockIdx.x) * 32 + 8
                                        : nullptr);
             ONMF_STAMP(a.stamps, m, 3);
-            // the frames of this CTA's first tile of the next minibatch start
-            // on their way into shared memory (phase 3 uses none of it), and
-            // W, A, B of its column load while the other CTAs finish phase 2
-            if (!lastmb) {
-                const int nbn = (m + 1 == a.nmb - 1) ? a.nb_last : a.beta;
-                const int tn = (int)blockIdx.x;
-                if (tn * TILE < nbn) {
-                    const float *Vt = a.V + ((long long)(m + 1) * a.beta + (long long)tn * TILE) * a.ldv;
-                    const int nv = min(TILE, nbn - tn * TILE);
-                    if (tile_bulk(Vt, a.ldv, s.F, nv)) {
-                        if (threadIdx.x == 0) {
-                            const unsigned bytes = (unsigned)((size_t)nv * s.F * 4);
-                            fence_proxy_async_shared();
-                            mbar_arrive_expect_tx(&mbar[1], bytes);
-                            bulk_g2s(smem + mixed_layout(s).yraw, Vt, bytes, &mbar[1]);
-                        }
-                        v_prefetched = true;
-                    }
-                }
-            }
+            // the frames of this CTA's first tile of the next minibatch (if
+            // not on their way yet: phase 3 uses no dynamic shared memory);
+            // then, while the other CTAs finish phase 2, W, A, B of the CTA's
+            // column load and those frames are staged and converted
+            if (!lastmb && !early_v) prefetch(m + 1);
             grid_arrive(a.bar, epoch);
             ColVals pre;
             col_load(a, blockIdx.x, pre);
+            if (v_prefetched) {
+                TileJob tn;
+                first_tile(m + 1, tn);
+                mixed_stage_frames(s, a.eps, tn, smem, &mbar[1], vpar, a.err);
+                v_prefetched = false;
+                v_ready = true;
+            }
             if (!grid_wait(a.bar, G, epoch, a.err)) break;
             ONMF_STAMP(a.stamps, m, 4);
             // ---- phase 3: partial sums, A, B, W' = sqrt(A/B), rescale, image
