@@ -1126,7 +1126,8 @@ def run_probe_tcgen05():
 def main():
     args = parse()
     if args.probe_tcgen05:
-        print(json.dumps({"probe": "tcgen05.mma issue cost, one CTA", "rows": run_probe_tcgen05()}),
+        print(json.dumps({"probe": "tcgen05.mma issue cost and mma.sync throughput, one CTA",
+                          "rows": run_probe_tcgen05()}),
               flush=True)
         return
     if args.phase_timing:

@@ -3,8 +3,10 @@
 // function of N, with A in shared memory or in tensor memory and one or four
 // accumulators. One CTA, one issuing thread; clock64 around `iters` MMAs
 // issued back to back and around their completion (one commit). Operands
-// are zeros (the cost does not depend on the values). Prints one JSON line
-// per configuration. Built and run by `python bench.py --probe-tcgen05`.
+// are zeros (the cost does not depend on the values). Then the throughput of
+// the warp-level mma.sync m16n8k16 (bf16 -> f32) from registers: W warps per
+// SM, each with C independent accumulator chains. Prints one JSON line per
+// configuration. Built and run by `python bench.py --probe-tcgen05`.
 #include <cstdio>
 
 #include "onmf_tc.cuh"
@@ -60,6 +62,44 @@ __global__ void __launch_bounds__(128, 1) probe(int N, int tmemA, int nacc, int 
     if (threadIdx.x < 32) tmem_dealloc(tb, 512);
 }
 
+// mma.sync throughput: every warp runs `iters` rounds of C independent
+// m16n8k16 products (operands in registers); clock64 of warp 0.
+template <int C>
+__global__ void mma_sync_probe(int iters, long long *out, float *sink) {
+    uint32_t a[4] = {threadIdx.x, threadIdx.x + 1, threadIdx.x + 2, threadIdx.x + 3};
+    float d[C][4];
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) d[c][e] = 0.f;
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int c = 0; c < C; ++c) mma_bf16_16816(d[c], a, a[0] ^ (uint32_t)c, a[1]);
+    __syncthreads();
+    const long long t1 = clock64();
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < C; ++c) s += d[c][0] + d[c][1] + d[c][2] + d[c][3];
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = s;  // keeps the products
+    if (threadIdx.x == 0) out[0] = t1 - t0;
+}
+
+template <int C>
+static int run_mma_sync(int warps, long long *d_out, float *d_sink) {
+    const int iters = 4096;
+    mma_sync_probe<C><<<1, 32 * warps>>>(iters, d_out, d_sink);
+    if (cudaDeviceSynchronize() != cudaSuccess) return 1;
+    long long h = 0;
+    cudaMemcpy(&h, d_out, 8, cudaMemcpyDeviceToHost);
+    const double n = (double)warps * C * iters;
+    printf("{\"mma_sync\": \"m16n8k16 bf16\", \"warps\": %d, \"chains\": %d, "
+           "\"clk_per_mma_per_sm\": %.2f, \"mac_per_clk\": %.0f}\n",
+           warps, C, (double)h / n, n * 16 * 8 * 16 / (double)h);
+    return 0;
+}
+
 int main() {
     long long *d_out = nullptr;
     int *d_err = nullptr;
@@ -88,5 +128,10 @@ int main() {
                        N, tmemA ? "tmem" : "smem", nacc, (double)h[0] / iters,
                        (double)h[1] / iters, 128.0 * N * 16 * iters / (double)h[1]);
             }
+    float *d_sink = nullptr;
+    if (cudaMalloc(&d_sink, 16 * 32 * 4) != cudaSuccess) return 1;
+    if (run_mma_sync<1>(1, d_out, d_sink) || run_mma_sync<4>(4, d_out, d_sink) ||
+        run_mma_sync<8>(8, d_out, d_sink) || run_mma_sync<8>(16, d_out, d_sink))
+        return 1;
     return 0;
 }
