@@ -3,17 +3,25 @@
 // projection and the batch H step, and the split-N statistics of the batch
 // W step. Included by the translation units that instantiate them.
 //
-// One online minibatch is three grid-wide phases separated by bounded grid
-// barriers (the launch is cooperative, so all CTAs are co-resident):
+// One online minibatch of the persistent kernel (the launch is cooperative,
+// so all CTAs are co-resident and every grid-wide wait is bounded):
 //   1. h-solve of every 8-frame tile (frames are independent given W); each
 //      tile leaves its final P = Y/X^2, Q = 1/X and H rows in L2-resident
 //      scratch and its d_IS sum in a per-tile slot;
-//   2. statistics a = (P H^T) o W^2, b = Q H^T on (16 rows x 32 columns)
-//      output tiles, then A <- rho A + a, B <- rho B + b and W' = sqrt(A/B)
-//      for the tile's entries;
-//   3. one CTA per dictionary column: s_k = sum_f W'_fk (warp shuffles and
-//      a fixed-order combine), W = W'/s, A /= s, B *= s, the derived images
-//      of W, and the running loss.
+//   2. statistics a = (P H^T) o W^2, b = Q H^T;
+//   3. A <- rho A + a, B <- rho B + b, W' = sqrt(A/B), the L1 rescale of every
+//      column (W = W'/s, A /= s, B *= s), the derived images of W, and the
+//      running loss.
+// Mixed precision: each h-solve tile releases its frame range (a release
+// increment of the range's counter) instead of a grid barrier; the
+// statistics are tcgen05 MMAs per (64-frequency tile, frame range) unit that
+// wait only for their range and leave FP32 partial sums; one arrive/wait
+// grid barrier (the next minibatch's frames are staged and the column's
+// W, A, B loaded while it is open), then one pass per dictionary column does
+// all of step 3 with the partial sums reduced in a fixed order; a grid
+// barrier before the next minibatch. FP32: a grid barrier after step 1,
+// step 2 on (16 rows x 32 columns) output tiles with A, B and W' updated in
+// their epilogue, a grid barrier, step 3 one CTA per column, a grid barrier.
 #pragma once
 
 #include "onmf_device.cuh"
