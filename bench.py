@@ -71,6 +71,9 @@ def parse():
     p.add_argument("--phase-timing", action="store_true",
                    help="measurement build of the library (clock64 stamps at the phase "
                         "boundaries of the online step): print the per-phase table and exit")
+    p.add_argument("--phase-dump", default=None,
+                   help="with --phase-timing: also save the raw stamps "
+                        "[minibatch][CTA][point] to this .npy file")
     p.add_argument("--probe-tcgen05", action="store_true",
                    help="build and run the tcgen05 issue-cost probe "
                         "(paper_1106_4198_gb300/probes/tcgen05_issue.cu) and exit")
@@ -1016,6 +1019,7 @@ def run_reference(args):
 
 PHASE_NAMES = ["h-solve", "wait after the h-solve", "statistics (tcgen05)",
                "barrier before the column pass", "column pass + loss", "barrier before the next minibatch"]
+STAMP_PTS = 40  # points per (minibatch, CTA) record of the measurement build
 UNIT_NAMES = ["range wait -> first chunk in shared memory", "first chunk -> MMAs issued",
               "MMAs done", "accumulators to shared memory", "partial-sum stores", "unit end"]
 
@@ -1045,7 +1049,7 @@ def run_phase_timing(args):
     m = onmf.OnlineISNMF(F, K, synth.init_dictionary(F, K), beta=BETA, n_inner=N_IN,
                          precision=onmf.ONMF_MIXED, hsolve=onmf.ONMF_HSOLVE_MMA,
                          accumulate=onmf.ONMF_ACC_FP32_COMP, stats_ranges=ranges)
-    buf = np.zeros(128 * 256 * 32, dtype=np.int64)
+    buf = np.zeros(128 * 256 * STAMP_PTS, dtype=np.int64)
     grid = ctypes.c_int32(0)
     m.push(V)
     assert L.onmf_phase_stamps(m.state, buf.ctypes.data, buf.size, ctypes.byref(grid)) == 0
@@ -1058,7 +1062,9 @@ def run_phase_timing(args):
     assert L.onmf_phase_stamps(m.state, buf.ctypes.data, buf.size, ctypes.byref(grid)) == 0
     m.close()
     G = grid.value
-    st = buf[:nmb * G * 32].reshape(nmb, G, 32)
+    st = buf[:nmb * G * STAMP_PTS].reshape(nmb, G, STAMP_PTS)
+    if args.phase_dump:
+        np.save(args.phase_dump, st)
     mb = slice(1, nmb - 1)
     ns = st[:, :, :7]   # %globaltimer, ns
     clk = st[:, :, 8:15]  # clock64 of the statistics units
@@ -1086,18 +1092,42 @@ def run_phase_timing(args):
     for i, nm in enumerate(PHASE_NAMES):
         d = (ns[mb, :, i + 1] - ns[mb, :, i]) / 1e3
         out["per_cta_mean_us"][nm] = float(d.mean())
+    # the window of the barrier before the column pass, per CTA: arrival
+    # (point 3) -> W, A, B loaded (32) -> next frames staged (33) -> through (4)
+    win = st[mb, :, 32:34]
+    out["barrier_window_us"] = {
+        "column W, A, B loads": float(np.mean(win[:, :, 0] - ns[mb, :, 3])) / 1e3,
+        "next minibatch's frames staged": float(np.mean(win[:, :, 1] - win[:, :, 0])) / 1e3,
+        "wait for the last arrival": float(np.mean(ns[mb, :, 4] - win[:, :, 1])) / 1e3,
+        "last CTA out of the window after the last arrival":
+            float(np.mean(win[:, :, 1].max(axis=1) - last(3))) / 1e3}
     span_clk = clk[mb, :, 6] - clk[mb, :, 0]
     span_ns = st[mb, :, 15] - st[mb, :, 7]
     ghz = float(np.median(span_clk[has] / np.maximum(span_ns[has], 1)))
     out["sm_ghz_estimate"] = ghz
+    tl = st[mb, :, 38:40]
+    has_t = tl[:, :, 0] != 0
+    out["hsolve_outside_tile_us"] = {
+        "minibatch start -> tile start (sum of W, W^T image copy issued)":
+            float(np.mean((tl[:, :, 0] - ns[mb, :, 0])[has_t])) / 1e3,
+        "tile end -> frame range released, next frames requested":
+            float(np.mean((ns[mb, :, 1] - tl[:, :, 1])[has_t])) / 1e3}
+    sg = st[mb, :, 34:38]
+    ok = sg[:, :, 0] != 0
+    for nm, (i, j) in {"staging: frames in shared memory": (0, 1),
+                       "staging: frame sums and input check": (1, 2),
+                       "staging: f-major copy y = eps + v": (2, 3)}.items():
+        out["barrier_window_us"][nm] = float(np.mean((sg[:, :, j] - sg[:, :, i])[ok])) / ghz / 1e3
     for i, nm in enumerate(UNIT_NAMES):
         d = np.where(has, (clk[mb, :, i + 1] - clk[mb, :, i]) / ghz / 1e3, np.nan)
         out["statistics_unit_us"][nm] = float(np.nanmean(d))
     # the h-solve tile of every CTA that has one (clock64)
-    hs = st[mb, :, 16:31]
+    hs = st[mb, :, 16:32]
     hh = hs[:, :, 0] != 0
     steps = {"frames staged and converted": (0, 1), "W^T image in shared memory": (1, 2),
              "inner iteration 1": (2, 3), "inner iterations 2-10 (mean)": None,
+             "inner iteration 10, step A (x = W h, ratios)": (11, 15),
+             "inner iteration 10, step B (W^T [p q], h update)": (15, 12),
              "final ratios and loss": (12, 13), "P, Q, H rows written": (13, 14)}
     out["hsolve_tile_us"] = {}
     for nm, ij in steps.items():

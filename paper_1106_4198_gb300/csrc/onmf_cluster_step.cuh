@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_cluster_kernel(StepArgs a,
     float *acc = reinterpret_cast<float *>(smem + stats_smem_bytes(PREC_MIXED) - 2 * 16 * 32 * 4);
     unsigned epoch = 0;
     int vp = 0, seq = 0;
+    cta_err_init(a.err);
     // the launch must carry clusters of exactly C CTAs, or the remote
     // addresses below would name CTAs that do not exist
     if (cluster_nctarank() != (unsigned)C || gridDim.x % C != 0) {

@@ -27,8 +27,16 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
+// Whether this CTA has flagged an error since the kernel started
+// (flag_error sets it; kernels with grid barriers clear it at entry with
+// cta_err_init). A CTA that arrives at a grid barrier with it set also sets
+// the barrier counter's top bit, so that every CTA waiting there learns of
+// the error from the word it polls, with no second read of the error word.
+static __shared__ int s_cta_err;
+
 __device__ __forceinline__ void flag_error(int *err, int bits) {
     atomicOr(err, bits);
+    s_cta_err = 1;
 }
 
 __device__ __forceinline__ int read_error(const int *err) {
@@ -45,78 +53,97 @@ __device__ __forceinline__ void red_release_gpu_add(unsigned *p, unsigned v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Top bit of a grid barrier counter: some CTA arrived with an error (or
+// gave up waiting); the low 31 bits count the arrivals of the launch.
+constexpr unsigned kBarErrBit = 0x80000000u;
+
+// At kernel entry, before any flag_error: an error word that is already set
+// (an earlier launch on the same state) counts as this CTA's own, so the
+// kernel leaves at its first grid barrier.
+__device__ __forceinline__ void cta_err_init(const int *err) {
+    if (threadIdx.x == 0) s_cta_err = read_error(err) != 0 ? 1 : 0;
+    __syncthreads();
+}
+
+// Thread 0: arrive at a grid barrier (after a CTA barrier), carrying this
+// CTA's error state in the top bit. The bit is set before the release add,
+// so a CTA that sees the full count also sees the bit.
+__device__ __forceinline__ void grid_arrive_t0(unsigned *counter) {
+    if (s_cta_err) atomicOr(counter, kBarErrBit);
+    red_release_gpu_add(counter, 1u);
+}
+
+// Thread 0: wait until `target` CTAs have arrived or the error bit is set;
+// false on the error bit or on timeout (the CTA then flags ERR_TIMEOUT and
+// sets the bit, so the others stop waiting too).
+__device__ __forceinline__ bool grid_wait_t0(unsigned *counter, unsigned target, int *err) {
+    const uint64_t t0 = global_ns();
+    unsigned spins = 0;
+    for (;;) {
+        const unsigned c = ld_acquire_gpu(counter);
+        if (c & kBarErrBit) return false;
+        if (c >= target) return true;
+        if (++spins > 1024) __nanosleep(32);
+        if ((spins & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
+            flag_error(err, ERR_TIMEOUT);
+            atomicOr(counter, kBarErrBit);
+            return false;
+        }
+    }
+}
+
 // Grid-wide barrier for a cooperative (co-resident) launch. `epoch` counts
 // the barriers this CTA has passed; the counter must be zero at launch.
 // Thread 0 arrives with a release reduction after the CTA barrier and waits
 // with acquire loads before the next CTA barrier; release and acquire are
 // cumulative, so the writes of the whole CTA before the barrier are visible
-// to every CTA after it. The wait is bounded: on timeout the CTA flags
-// ERR_TIMEOUT and returns false, and callers leave the kernel.
+// to every CTA after it. Every CTA returns false, and callers leave the
+// kernel, when some CTA arrived with an error flagged (the counter's top
+// bit: all of them see it, so all leave at the same barrier); an error this
+// CTA flags after arriving travels with its next arrival. The wait is
+// bounded: on timeout the CTA flags ERR_TIMEOUT and returns false.
 __device__ __forceinline__ bool grid_sync(unsigned *counter, unsigned nblocks,
                                           unsigned &epoch, int *err) {
     __syncthreads();
     ++epoch;
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
-        s_ok = 1;
-        red_release_gpu_add(counter, 1u);
-        const unsigned target = epoch * nblocks;
-        const uint64_t t0 = global_ns();
-        unsigned spins = 0;
-        while (ld_acquire_gpu(counter) < target) {
-            if (++spins > 1024) __nanosleep(32);
-            if ((spins & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
-                flag_error(err, ERR_TIMEOUT);
-                s_ok = 0;
-                break;
-            }
-        }
-        if (read_error(err) != 0) s_ok = 0;  // one read, so every thread agrees
+        grid_arrive_t0(counter);
+        s_ok = grid_wait_t0(counter, epoch * nblocks, err) ? 1 : 0;
     }
     __syncthreads();
     return s_ok != 0;
 }
 
-// The same barrier in two halves, so that a CTA can do work that no other
-// CTA waits for between its arrival and its wait (prefetching inputs of the
-// next phase). grid_arrive releases the CTA's writes made before it;
-// grid_wait returns false on timeout or a flagged error, like grid_sync.
+// The two halves of grid_sync, for a CTA that has work to do between its
+// arrival and its wait (work that reads nothing other CTAs write in this
+// phase). grid_arrive releases the CTA's writes made before it; grid_wait
+// returns false on a reported error or timeout, like grid_sync.
 __device__ __forceinline__ void grid_arrive(unsigned *counter, unsigned &epoch) {
     __syncthreads();
     ++epoch;
-    if (threadIdx.x == 0) red_release_gpu_add(counter, 1u);
+    if (threadIdx.x == 0) grid_arrive_t0(counter);
 }
 
 __device__ __forceinline__ bool grid_wait(unsigned *counter, unsigned nblocks, unsigned epoch,
                                           int *err) {
     __shared__ int s_okw;
-    if (threadIdx.x == 0) {
-        s_okw = 1;
-        const unsigned target = epoch * nblocks;
-        const uint64_t t0 = global_ns();
-        unsigned spins = 0;
-        while (ld_acquire_gpu(counter) < target) {
-            if (++spins > 1024) __nanosleep(32);
-            if ((spins & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) {
-                flag_error(err, ERR_TIMEOUT);
-                s_okw = 0;
-                break;
-            }
-        }
-        if (read_error(err) != 0) s_okw = 0;
-    }
+    if (threadIdx.x == 0) s_okw = grid_wait_t0(counter, epoch * nblocks, err) ? 1 : 0;
     __syncthreads();
     return s_okw != 0;
 }
 
 // %globaltimer (ns, one clock for all SMs) of thread 0 into
-// stamps[(m * gridDim.x + blockIdx.x) * 32 + i] (phase-timing builds;
-// compiled out otherwise).
+// stamps[(m * gridDim.x + blockIdx.x) * ONMF_STAMP_PTS + i] (phase-timing
+// builds; compiled out otherwise).
+#ifndef ONMF_STAMP_PTS
+#define ONMF_STAMP_PTS 40  // points per (minibatch, CTA) record
+#endif
 #ifdef ONMF_PHASE_STAMPS
 #define ONMF_STAMP(stamps, m, i)                                                              \
     do {                                                                                      \
         if ((stamps) && threadIdx.x == 0 && (m) < 128)                                        \
-            (stamps)[((long long)(m) * gridDim.x + blockIdx.x) * 32 + (i)] =                  \
+            (stamps)[((long long)(m) * gridDim.x + blockIdx.x) * ONMF_STAMP_PTS + (i)] =      \
                 (long long)global_ns();                                                       \
     } while (0)
 #else

@@ -45,7 +45,10 @@ struct TileJob {
     // mixed path: write P, Q and H in the core-matrix layout of the tcgen05
     // statistics (stats_tc.cuh) instead of frame rows
     int pq_core = 0;
-    // phase-timing builds: 16 clock64 slots of this tile's steps, or NULL
+    // phase-timing builds: clock64 slots of this tile's steps, or NULL (0-2
+    // staging, 3-12 after each inner iteration, 13 final ratios, 14 outputs,
+    // 15 after step A of the tenth iteration; 18-21 the steps of the frame
+    // staging when it runs in the barrier window)
     long long *hst = nullptr;
     // mma path: frames already staged and converted (mixed_stage_frames)
     int v_ready = 0;
@@ -382,7 +385,10 @@ __host__ __device__ inline MixedLayout mixed_layout(const Shape &s) {
     o += (size_t)s.Fp16 * kTile * 4;
     o = (o + 127) / 128 * 128;
     L.misc = o;
-    o += 768;  // frame sums, loss per warp, the penalty's per-warp h sums [2][8][8]
+    // frame sums [8], loss per warp [8], the penalty's per-warp h sums
+    // [2][8][8] from float 32, the staging's per-warp frame sums [8][8] from
+    // float 160
+    o += 1024;
     L.total = o;
     return L;
 }
@@ -417,6 +423,7 @@ static __device__ void mixed_stage_frames(const Shape &s, float eps, const TileJ
     float *y_raw = reinterpret_cast<float *>(smem + L.yraw);
     float *yT = reinterpret_cast<float *>(smem + L.yt);
     float *sy = reinterpret_cast<float *>(smem + L.misc);
+    ONMF_HSTAMP(t, 18);
     // ---- frame tile -> shared memory (bulk copy when contiguous and aligned;
     //      possibly issued already by the previous tile)
     {
@@ -441,26 +448,56 @@ static __device__ void mixed_stage_frames(const Shape &s, float eps, const TileJ
         }
         __syncthreads();
     }
-    // frame sums and input check (warp j: frame j), f-major copy of y
+    ONMF_HSTAMP(t, 19);
+    // f-major copy y = eps + v, input check and frame sums in one pass:
+    // thread tid always has frame j = tid & 7 (entry f * 8 + j of yT), so it
+    // adds its own entries of frame j; the 32 threads of each frame then
+    // combine theirs (lanes j, j+8, j+16, j+24, then the eight warps in order)
     {
+        constexpr int U = 6;  // independent loads in flight per thread
+        const int j = tid & 7;
+        const bool jv = j < t.nvalid;
+        const float *src = y_raw + j * F;
         float a = 0.f;
-        if (warp < t.nvalid) {
-            for (int f = lane; f < F; f += 32) {
-                float v = y_raw[warp * F + f];
-                if (bad_value(v)) flag_error(err, ERR_INPUT);
-                a += eps + v;
+        // input check on the bits: with -0 taken as +0, a frame value is
+        // valid (finite, not negative, not NaN) iff its bits are below those
+        // of +inf, so the largest bits seen decide (one max per entry)
+        unsigned mx = 0u;
+        for (int f0 = tid >> 3; f0 < Fp; f0 += 32 * U) {
+            float v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int f = f0 + 32 * u;
+                v[u] = (jv && f < F) ? src[f] : 0.f;
             }
-        } else {
-            a = (float)F;  // placeholder frames: y = 1
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int f = f0 + 32 * u;
+                if (f < Fp) {
+                    const bool in = jv && f < F;
+                    const unsigned b = __float_as_uint(v[u]);
+                    mx = max(mx, b == 0x80000000u ? 0u : b);
+                    const float y = eps + v[u];
+                    if (in) a += y;
+                    yT[f * 8 + j] = in ? y : 1.f;
+                }
+            }
         }
-        a = warp_sum(a);
-        if (lane == 0) sy[warp] = a;
-        for (int i = tid; i < Fp * kTile; i += kThreads) {
-            const int f = i >> 3, j = i & 7;
-            yT[i] = (j < t.nvalid && f < F) ? eps + y_raw[j * F + f] : 1.f;
+        if (mx >= 0x7f800000u) flag_error(err, ERR_INPUT);
+        a += __shfl_xor_sync(0xffffffffu, a, 8);
+        a += __shfl_xor_sync(0xffffffffu, a, 16);
+        if (lane < 8) sy[160 + warp * 8 + lane] = a;
+        __syncthreads();
+        ONMF_HSTAMP(t, 20);
+        if (tid < 8) {
+            float sum = 0.f;
+            for (int w = 0; w < kWarps; ++w) sum += sy[160 + w * 8 + tid];
+            // placeholder frames (j >= nvalid): y = 1 at every f
+            sy[tid] = (tid < t.nvalid) ? sum : (float)F;
         }
     }
     __syncthreads();
+    ONMF_HSTAMP(t, 21);
 }
 
 // Pending bulk copy of W^T that a tile must wait for before its first use.
@@ -557,7 +594,17 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
     __syncthreads();
     ONMF_HSTAMP(t, 2);
 
-    float lacc = 0.f;
+    // the loss sum_{valid f, j} r - 1 - log r (r = y/x: d_IS of Section 2,
+    // summed over frames as in Eq. 1) with one logf per thread: for
+    // r = m 2^e (m in [1, 2)), log r = log m + e log 2; the r - 1 are added
+    // (lr1), the mantissas multiplied (lm, brought back to [1, 2) after
+    // every 16-row tile, so the product stays below 32) and the exponents
+    // added as integers (le): no logf per entry
+    float lacc = 0.f, lr1 = 0.f, lm = 1.f;
+    int le = 0;
+    // whether this thread's two frames (2 tq, 2 tq + 1) are real frames, in
+    // registers for the loss (the tile descriptor may live in local memory)
+    const bool fv0 = 2 * tq < t.nvalid, fv1 = 2 * tq + 1 < t.nvalid;
     for (int it = 0;; ++it) {
         const bool last = (it == t.n_in);
         if (last && !t.final_pass) break;
@@ -610,10 +657,25 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
                             const bool ok = f < F;
                             pv[e] = ok ? p : 0.f;
                             qv[e] = ok ? q : 0.f;
-                            if (LOSS && ok && (2 * tq + (e & 1)) < t.nvalid) {
+                            if (LOSS && ok && ((e & 1) ? fv1 : fv0)) {
                                 const float r = yv[e] * q;
-                                lacc += (r - 1.f) - logf(r);
+                                // a subnormal r is scaled by 2^24 first
+                                const bool sub = __float_as_uint(r) < 0x00800000u;
+                                const unsigned b = __float_as_uint(sub ? r * 16777216.f : r);
+                                lr1 += r - 1.f;
+                                le += (int)(b >> 23) - (sub ? 151 : 127);
+                                lm *= __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
+                                // r = 0 (log r = -inf): the loss is +inf;
+                                // r infinite or NaN: NaN
+                                if (b - 0x00800000u >= 0x7f000000u)
+                                    lacc += (b == 0u) ? __int_as_float(0x7f800000)
+                                                      : __int_as_float(0x7fc00000);
                             }
+                        }
+                        if (LOSS) {  // the mantissa product back to [1, 2)
+                            const unsigned b = __float_as_uint(lm);
+                            le += (int)(b >> 23) - 127;
+                            lm = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
                         }
                         stmatrix_x4_trans(PQ_s + (r8 + 8 * (mi >> 1)) * WLD + f0 + 8 * (mi & 1),
                                           pack_bf16(pv[0], pv[1]), pack_bf16(pv[2], pv[3]),
@@ -631,6 +693,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
             ONMF_HSTAMP(t, 13);
             break;
         }
+        if (it == 9) ONMF_HSTAMP(t, 15);
 
         // ---- step B: [W^T p | W^T q] and the h update
         if (hown) {
@@ -698,15 +761,17 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
         unsigned char *PQc = reinterpret_cast<unsigned char *>(t.Pg);
         unsigned char *Hc = reinterpret_cast<unsigned char *>(t.Hg);
         const long long G = t.betap / 8, gi = t.j0 / 8;
-        const int cpr = Fp / 8;  // 16-byte chunks per row
-        for (int row = warp; row < 2 * kTile; row += kWarps) {
-            const int which = row >> 3, j = row & 7;
-            for (int c = lane; c < cpr; c += 32) {
-                uint4 v = make_uint4(0, 0, 0, 0);
-                if (j < t.nvalid) v = *reinterpret_cast<const uint4 *>(PQ_s + row * WLD + 8 * c);
-                *reinterpret_cast<uint4 *>(PQc + ((long long)(c >> 3) * G + gi) * 2048 +
-                                           (which * 8 + (c & 7)) * 128 + j * 16) = v;
-            }
+        const int cpr = Fp / 8;  // 16-byte chunks per row = core matrices per P or Q
+        // eight lanes per core matrix (lane & 7 = frame j): a warp writes four
+        // whole 128-byte core matrices, 512 contiguous bytes within a block
+        const int j = tid & 7;
+        for (int cc = tid >> 3; cc < 2 * cpr; cc += kThreads / 8) {
+            const int which = cc >= cpr ? 1 : 0, c = cc - which * cpr;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (j < t.nvalid)
+                v = *reinterpret_cast<const uint4 *>(PQ_s + (which * 8 + j) * WLD + 8 * c);
+            *reinterpret_cast<uint4 *>(PQc + ((long long)(c >> 3) * G + gi) * 2048 +
+                                       (which * 8 + (c & 7)) * 128 + j * 16) = v;
         }
         for (int k = tid; k < NKS * 16; k += kThreads) {
             uint32_t w[4];
@@ -760,6 +825,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
         }
     }
     if (t.loss_slot) {
+        lacc += (float)((double)lr1 - ((double)logf(lm) + (double)le * 0.6931471805599453));
         float l = warp_sum(lacc);
         if (lane == 0) lw[warp] = l;
         __syncthreads();

@@ -649,6 +649,7 @@ __global__ void __launch_bounds__(kThreads) wait_selftest_kernel(int which, unsi
                                                                  unsigned long long *elapsed) {
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tslot;
+    cta_err_init(err);
     const uint64_t t0 = global_ns();
     if (which == 0) {
         unsigned epoch = 0;

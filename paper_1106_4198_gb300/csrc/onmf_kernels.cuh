@@ -126,8 +126,15 @@ struct StepArgs {
 // Points 16-31: the CTA's first h-solve tile of the minibatch (clock64):
 // 16 tile start, 17 frames in shared memory and converted, 18 W^T image in
 // shared memory, 19 + i end of inner iteration i (up to 10), 29 final ratios
-// and loss, 30 P, Q, H rows written.
-constexpr int kStampMb = 128, kStampCtas = 256, kStampPts = 32;
+// and loss, 30 P, Q, H rows written, 31 end of step A of iteration 10.
+// Points 32-33 (%globaltimer): in the window of the grid barrier before the
+// column pass, 32 after the column's W, A, B loads, 33 after the next
+// minibatch's frames are staged; 34-37 (clock64) the steps of that staging;
+// 38-39 (%globaltimer) the start and end of the CTA's first h-solve tile.
+#ifndef ONMF_STAMP_PTS
+#define ONMF_STAMP_PTS 40  // points per (minibatch, CTA) record
+#endif
+constexpr int kStampMb = 128, kStampCtas = 256, kStampPts = ONMF_STAMP_PTS;
 
 // Arguments of the projection / batch h-step kernels (no state update).
 struct TileArgs {

@@ -547,6 +547,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
     __shared__ float s_red8[kWarps];
     __shared__ double s_red[kThreads];
     __shared__ uint32_t s_tslot;
+    cta_err_init(a.err);
     if (threadIdx.x == 0) {
         for (int i = 0; i < 9; ++i) mbar_init(&mbar[i], 1);
         fence_mbar_init();
@@ -612,12 +613,14 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
         unsigned *rcnt = a.bar + 4;
         // ---- phase 1: h-solve of every tile
         if ((int)blockIdx.x < ntiles) {
-            const float sw = sum_w(a.swpart, s.K, &s_tmp);
+            // the W^T image copy first: its flight overlaps the read of the
+            // column sums below
             WStage ws{&mbar[0], &wpar, false};
             if (PREC == PREC_MIXED) {
                 issue_wimg(s, a.Wimg, smem, &mbar[0]);
                 ws.pending = true;
             }
+            const float sw = sum_w(a.swpart, s.K, &s_tmp);
             if (PREC == PREC_TC) stage_w_tc(s, tc_layout(s), a.Wimg, a.Wrow, a.Wcm, tbase, smem);
             for (int tile = blockIdx.x; tile < ntiles; tile += G) {
                 TileJob t;
@@ -646,16 +649,18 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                 v_ready = false;
 #ifdef ONMF_PHASE_STAMPS
                 t.hst = (a.stamps && tile == (int)blockIdx.x && m < kStampMb)
-                            ? a.stamps + ((long long)m * G + blockIdx.x) * 32 + 16
+                            ? a.stamps + ((long long)m * G + blockIdx.x) * kStampPts + 16
                             : nullptr;
 #endif
                 v_prefetched = false;
+                if (tile == (int)blockIdx.x) ONMF_STAMP(a.stamps, m, 38);
                 if constexpr (PREC == PREC_TC)
                     hsolve_tile_tc<KS>(s, a.eps, a.gamma, sw, t, smem, tbase, &mbar[2], &mbar[3],
                                        parA, parB, &mbar[1], vpar, a.err);
                 else
                     hsolve_tile<PREC, KS, PEN>(s, a.eps, a.gamma, a.Wcm, a.Wrm, sw, t, smem, ws,
                                           &mbar[1], vpar, a.err);
+                if (tile == (int)blockIdx.x) ONMF_STAMP(a.stamps, m, 39);
                 if constexpr (PREC == PREC_MIXED) {
                     // the tile's P, Q, H rows are written (the h-solve ends
                     // with a CTA barrier): publish them to its frame range,
@@ -680,7 +685,7 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
                               reinterpret_cast<const unsigned char *>(a.Pg),
                               reinterpret_cast<const unsigned char *>(a.Hg), a.part, s.K, s.Fp16,
                               smem, tbase, sb, rcnt, a.err,
-                              a.stamps ? a.stamps + ((long long)m * G + blockIdx.x) * 32 + 8
+                              a.stamps ? a.stamps + ((long long)m * G + blockIdx.x) * kStampPts + 8
                                        : nullptr);
             ONMF_STAMP(a.stamps, m, 3);
             // the frames of this CTA's first tile of the next minibatch (if
@@ -691,13 +696,19 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
             grid_arrive(a.bar, epoch);
             ColVals pre;
             col_load(a, blockIdx.x, pre);
+            ONMF_STAMP(a.stamps, m, 32);
             if (v_prefetched) {
                 TileJob tn;
                 first_tile(m + 1, tn);
+#ifdef ONMF_PHASE_STAMPS
+                if (a.stamps && m < kStampMb)  // points 34-37 of this minibatch
+                    tn.hst = a.stamps + ((long long)m * G + blockIdx.x) * kStampPts + 16;
+#endif
                 mixed_stage_frames(s, a.eps, tn, smem, &mbar[1], vpar, a.err);
                 v_prefetched = false;
                 v_ready = true;
             }
+            ONMF_STAMP(a.stamps, m, 33);
             if (!grid_wait(a.bar, G, epoch, a.err)) break;
             ONMF_STAMP(a.stamps, m, 4);
             // ---- phase 3: partial sums, A, B, W' = sqrt(A/B), rescale, image
