@@ -1019,7 +1019,7 @@ def run_reference(args):
 
 PHASE_NAMES = ["h-solve", "wait after the h-solve", "statistics (tcgen05)",
                "barrier before the column pass", "column pass + loss", "barrier before the next minibatch"]
-STAMP_PTS = 40  # points per (minibatch, CTA) record of the measurement build
+STAMP_PTS = 48  # points per (minibatch, CTA) record of the measurement build
 UNIT_NAMES = ["range wait -> first chunk in shared memory", "first chunk -> MMAs issued",
               "MMAs done", "accumulators to shared memory", "partial-sum stores", "unit end"]
 
@@ -1112,6 +1112,13 @@ def run_phase_timing(args):
             float(np.mean((tl[:, :, 0] - ns[mb, :, 0])[has_t])) / 1e3,
         "tile end -> frame range released, next frames requested":
             float(np.mean((ns[mb, :, 1] - tl[:, :, 1])[has_t])) / 1e3}
+    cs = st[mb, :, 40:45]
+    okc = cs[:, :, 0] != 0
+    out["column_step_us"] = {}
+    for nm, (i, j) in {"partial sums of the ranges loaded and added": (0, 1),
+                       "A, B, W' = sqrt(A/B)": (1, 2), "column sum (block reduction)": (2, 3),
+                       "rescale, W, A, B and image stores": (3, 4)}.items():
+        out["column_step_us"][nm] = float(np.mean((cs[:, :, j] - cs[:, :, i])[okc])) / ghz / 1e3
     sg = st[mb, :, 34:38]
     ok = sg[:, :, 0] != 0
     for nm, (i, j) in {"staging: frames in shared memory": (0, 1),

@@ -137,7 +137,7 @@ __device__ __forceinline__ bool grid_wait(unsigned *counter, unsigned nblocks, u
 // stamps[(m * gridDim.x + blockIdx.x) * ONMF_STAMP_PTS + i] (phase-timing
 // builds; compiled out otherwise).
 #ifndef ONMF_STAMP_PTS
-#define ONMF_STAMP_PTS 40  // points per (minibatch, CTA) record
+#define ONMF_STAMP_PTS 48  // points per (minibatch, CTA) record
 #endif
 #ifdef ONMF_PHASE_STAMPS
 #define ONMF_STAMP(stamps, m, i)                                                              \

@@ -130,9 +130,10 @@ struct StepArgs {
 // Points 32-33 (%globaltimer): in the window of the grid barrier before the
 // column pass, 32 after the column's W, A, B loads, 33 after the next
 // minibatch's frames are staged; 34-37 (clock64) the steps of that staging;
-// 38-39 (%globaltimer) the start and end of the CTA's first h-solve tile.
+// 38-39 (%globaltimer) the start and end of the CTA's first h-solve tile;
+// 40-44 (clock64) the steps of the CTA's first column of the column pass.
 #ifndef ONMF_STAMP_PTS
-#define ONMF_STAMP_PTS 40  // points per (minibatch, CTA) record
+#define ONMF_STAMP_PTS 48  // points per (minibatch, CTA) record
 #endif
 constexpr int kStampMb = 128, kStampCtas = 256, kStampPts = ONMF_STAMP_PTS;
 

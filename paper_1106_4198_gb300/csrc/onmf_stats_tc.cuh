@@ -278,7 +278,18 @@ __device__ __forceinline__ void col_load(const StepArgs &a, int k, ColVals &v) {
 // pre: W, A, B of the CTA's first column (k = first), loaded by col_load.
 template <bool WPEN>
 static __device__ void column_step(const StepArgs &a, int S, double rho, float *red8, int first,
-                                   int stride, const ColVals &pre) {
+                                   int stride, const ColVals &pre, long long *cst = nullptr) {
+    // cst: 5 clock64 slots of the first column (phase-timing builds), else NULL
+#ifdef ONMF_PHASE_STAMPS
+#define ONMF_CSTAMP(i)                                                  \
+    do {                                                                \
+        if (cst && k == first && threadIdx.x == 0) cst[(i)] = clock64(); \
+    } while (0)
+#else
+#define ONMF_CSTAMP(i) \
+    do {               \
+    } while (0)
+#endif
     const Shape &s = a.s;
     const int F = s.F, K = s.K, Fp = s.Fp16;
     const int tid = threadIdx.x;
@@ -286,6 +297,7 @@ static __device__ void column_step(const StepArgs &a, int S, double rho, float *
     const long long step = (long long)K * Fp;  // floats between P (or Q) partials of two ranges
     for (int k = first; k < K; k += stride) {
         ColVals v;
+        ONMF_CSTAMP(0);
         if (k == first)
             v = pre;
         else
@@ -316,6 +328,7 @@ static __device__ void column_step(const StepArgs &a, int S, double rho, float *
                     qh[u] += qv[j][u];
                 }
         }
+        ONMF_CSTAMP(1);
         float wn[kColPer];
         float part_sum = 0.f;
 #pragma unroll
@@ -331,7 +344,9 @@ static __device__ void column_step(const StepArgs &a, int S, double rho, float *
                 part_sum += wn[u];
             }
         }
+        ONMF_CSTAMP(2);
         const float sum = block_sum_f(part_sum, red8);
+        ONMF_CSTAMP(3);
         const bool sc = a.normalize && sum > 0.f;
         const float inv = sc ? __frcp_rn(sum) : 1.f;
         const double invd = sc ? 1.0 / (double)sum : 1.0;
@@ -352,7 +367,9 @@ static __device__ void column_step(const StepArgs &a, int S, double rho, float *
         }
         if (bad) flag_error(a.err, ERR_NUMERIC);
         if (tid == 0) a.swpart[k] = sc ? sum * inv : sum;
+        ONMF_CSTAMP(4);
     }
+#undef ONMF_CSTAMP
 }
 
 }  // namespace onmf
