@@ -1092,11 +1092,13 @@ def run_phase_timing(args):
     for i, nm in enumerate(PHASE_NAMES):
         d = (ns[mb, :, i + 1] - ns[mb, :, i]) / 1e3
         out["per_cta_mean_us"][nm] = float(d.mean())
-    # the window of the barrier before the column pass, per CTA: arrival
-    # (point 3) -> W, A, B loaded (32) -> next frames staged (33) -> through (4)
+    # the window of the barrier before the column pass, per CTA: statistics
+    # done (point 3) -> arrived, column loaded (32) -> next frames staged (33)
+    # -> through (4)
     win = st[mb, :, 32:34]
     out["barrier_window_us"] = {
-        "column W, A, B loads": float(np.mean(win[:, :, 0] - ns[mb, :, 3])) / 1e3,
+        "arrival (its release waits for the partial-sum stores), column W, A, B loads":
+            float(np.mean(win[:, :, 0] - ns[mb, :, 3])) / 1e3,
         "next minibatch's frames staged": float(np.mean(win[:, :, 1] - win[:, :, 0])) / 1e3,
         "wait for the last arrival": float(np.mean(ns[mb, :, 4] - win[:, :, 1])) / 1e3,
         "last CTA out of the window after the last arrival":

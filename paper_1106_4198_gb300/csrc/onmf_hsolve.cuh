@@ -825,7 +825,11 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
         }
     }
     if (t.loss_slot) {
-        lacc += (float)((double)lr1 - ((double)logf(lm) + (double)le * 0.6931471805599453));
+        // e log 2 with log 2 split (Cody and Waite) into a leading part of 15
+        // significant bits (its product with e exact for |e| < 2^9) and the
+        // rest; FP32 only
+        const float e = (float)le;
+        lacc += (lr1 - e * 0.693145751953125f) - (logf(lm) + e * 1.428606765330187e-6f);
         float l = warp_sum(lacc);
         if (lane == 0) lw[warp] = l;
         __syncthreads();

@@ -128,8 +128,8 @@ struct StepArgs {
 // shared memory, 19 + i end of inner iteration i (up to 10), 29 final ratios
 // and loss, 30 P, Q, H rows written, 31 end of step A of iteration 10.
 // Points 32-33 (%globaltimer): in the window of the grid barrier before the
-// column pass, 32 after the column's W, A, B loads, 33 after the next
-// minibatch's frames are staged; 34-37 (clock64) the steps of that staging;
+// column pass, 32 after the arrival and the column's W, A, B loads, 33
+// after the next minibatch's frames are staged; 34-37 (clock64) the steps of that staging;
 // 38-39 (%globaltimer) the start and end of the CTA's first h-solve tile;
 // 40-44 (clock64) the steps of the CTA's first column of the column pass.
 #ifndef ONMF_STAMP_PTS

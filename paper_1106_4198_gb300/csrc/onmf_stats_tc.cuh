@@ -211,10 +211,12 @@ constexpr int kColRows = kColPer * kThreads;  // 1024 >= F on the mixed path
 // A <- rho A + a (or A + rho a with rho_on_new) for one entry in the state's
 // arithmetic; `raw` is the stored 8 bytes (a double, a float, or a float
 // pair) and is replaced by the new stored form; returns the new value as a
-// float, the operand of W' = sqrt(A/B).
-__device__ __forceinline__ float ab_accumulate(int accm, double rho, int rho_on_new, float inc,
-                                               double &raw) {
-    const float rhof = (float)rho;
+// float, the operand of W' = sqrt(A/B). rhof = (float)rho, converted once by
+// the caller: the FP32 modes do no FP64 arithmetic at all (the FP64 rate of
+// this GPU is a small fraction of its FP32 rate, so even per-thread
+// conversions and divisions in double show up in the column pass).
+__device__ __forceinline__ float ab_accumulate(int accm, double rho, float rhof, int rho_on_new,
+                                               float inc, double &raw) {
     if (accm == ACC_FP64) {
         const double v = rho_on_new ? fma(rho, (double)inc, raw) : fma(rho, raw, (double)inc);
         raw = v;
@@ -233,16 +235,17 @@ __device__ __forceinline__ float ab_accumulate(int accm, double rho, int rho_on_
 }
 
 // The rescale of one stored entry: A / s (div) or B * s; FP64 sums use the
-// double reciprocal invd = 1/s and the double sd = s.
+// double reciprocal invd = 1/s and the double sd = s; the compensated pairs
+// multiply by the reciprocal pair (ih, il) of s.
 __device__ __forceinline__ double ab_rescale(int accm, double raw, float sum, double invd,
-                                             double sd, bool div) {
+                                             double sd, float ih, float il, bool div) {
     if (accm == ACC_FP64) return div ? raw * invd : raw * sd;
     DF x;
     memcpy(&x, &raw, 8);
     if (accm == ACC_FP32)
         x = {div ? __fdiv_rn(x.hi, sum) : __fmul_rn(x.hi, sum), 0.f};
     else
-        x = div ? df_div(x, sum) : df_mul_add(x, sum, 0.f);
+        x = div ? df_mul_pair(x, ih, il) : df_mul_add(x, sum, 0.f);
     double r;
     memcpy(&r, &x, 8);
     return r;
@@ -294,6 +297,7 @@ static __device__ void column_step(const StepArgs &a, int S, double rho, float *
     const int F = s.F, K = s.K, Fp = s.Fp16;
     const int tid = threadIdx.x;
     const int accm = a.acc;
+    const float rhof = (float)rho;
     const long long step = (long long)K * Fp;  // floats between P (or Q) partials of two ranges
     for (int k = first; k < K; k += stride) {
         ColVals v;
@@ -337,8 +341,9 @@ static __device__ void column_step(const StepArgs &a, int S, double rho, float *
             wn[u] = 0.f;
             if (f < F) {
                 const float w = v.w[u];
-                const float An = ab_accumulate(accm, rho, a.rho_on_new, ph[u] * w * w, v.A[u]);
-                const float Bn = ab_accumulate(accm, rho, a.rho_on_new, qh[u], v.B[u]);
+                const float An =
+                    ab_accumulate(accm, rho, rhof, a.rho_on_new, ph[u] * w * w, v.A[u]);
+                const float Bn = ab_accumulate(accm, rho, rhof, a.rho_on_new, qh[u], v.B[u]);
                 const float Bd = WPEN ? Bn + a.wpen : Bn;
                 wn[u] = (Bd > 0.f) ? sqrtf(__fdiv_rn(An, Bd)) : w;
                 part_sum += wn[u];
@@ -349,8 +354,11 @@ static __device__ void column_step(const StepArgs &a, int S, double rho, float *
         ONMF_CSTAMP(3);
         const bool sc = a.normalize && sum > 0.f;
         const float inv = sc ? __frcp_rn(sum) : 1.f;
-        const double invd = sc ? 1.0 / (double)sum : 1.0;
-        const double sd = sc ? (double)sum : 1.0;
+        const float invl = sc ? __fmul_rn(__fmaf_rn(-inv, sum, 1.f), inv) : 0.f;
+        // the double forms of 1/s and s only where A, B are doubles
+        const bool d64 = sc && accm == ACC_FP64;
+        const double invd = d64 ? 1.0 / (double)sum : 1.0;
+        const double sd = d64 ? (double)sum : 1.0;
         bool bad = false;
 #pragma unroll
         for (int u = 0; u < kColPer; ++u) {
@@ -360,8 +368,8 @@ static __device__ void column_step(const StepArgs &a, int S, double rho, float *
                 const float wv = wn[u] * inv;
                 bad |= !isfinite(wv);
                 a.Wcm[i] = wv;
-                a.A[i] = sc ? ab_rescale(accm, v.A[u], sum, invd, sd, true) : v.A[u];
-                a.B[i] = sc ? ab_rescale(accm, v.B[u], sum, invd, sd, false) : v.B[u];
+                a.A[i] = sc ? ab_rescale(accm, v.A[u], sum, invd, sd, inv, invl, true) : v.A[u];
+                a.B[i] = sc ? ab_rescale(accm, v.B[u], sum, invd, sd, inv, invl, false) : v.B[u];
                 a.Wimg[(long long)k * s.WLD + f] = __float2bfloat16_rn(wv);
             }
         }

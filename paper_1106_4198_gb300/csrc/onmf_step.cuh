@@ -334,6 +334,14 @@ __device__ __forceinline__ DF df_div(DF x, float c) {
     return fast_two_sum(q, __fdiv_rn(__fadd_rn(r, x.lo), c));
 }
 
+// x * (ih + il), ih + il a float pair (a reciprocal: ih = 1/c rounded, il =
+// (1 - ih c) ih its first correction); no division per entry
+__device__ __forceinline__ DF df_mul_pair(DF x, float ih, float il) {
+    const float p = __fmul_rn(x.hi, ih);
+    const float pe = __fmaf_rn(x.hi, ih, -p);
+    return fast_two_sum(p, __fmaf_rn(x.hi, il, __fmaf_rn(x.lo, ih, pe)));
+}
+
 __device__ __forceinline__ DF df_load(const double *p) {
     const float2 v = *reinterpret_cast<const float2 *>(p);
     return {v.x, v.y};
