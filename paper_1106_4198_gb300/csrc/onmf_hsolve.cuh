@@ -595,13 +595,12 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
     ONMF_HSTAMP(t, 2);
 
     // the loss sum_{valid f, j} r - 1 - log r (r = y/x: d_IS of Section 2,
-    // summed over frames as in Eq. 1) with one logf per thread: for
-    // r = m 2^e (m in [1, 2)), log r = log m + e log 2; the r - 1 are added
-    // (lr1), the mantissas multiplied (lm, brought back to [1, 2) after
-    // every 16-row tile, so the product stays below 32) and the exponents
-    // added as integers (le): no logf per entry
-    float lacc = 0.f, lr1 = 0.f, lm = 1.f;
-    int le = 0;
+    // summed over frames as in Eq. 1): the r - 1 (lr1) and the base-2 logs
+    // (ll2, the hardware's approximate log2, absolute error about 2^-22 near
+    // r = 1 and a few ulp elsewhere; zero, infinite and NaN r give the same
+    // +inf or NaN loss as an exact log) are added per thread and combined
+    // once, log r = log2 r * log 2
+    float lacc = 0.f, lr1 = 0.f, ll2 = 0.f;
     // whether this thread's two frames (2 tq, 2 tq + 1) are real frames, in
     // registers for the loss (the tile descriptor may live in local memory)
     const bool fv0 = 2 * tq < t.nvalid, fv1 = 2 * tq + 1 < t.nvalid;
@@ -659,23 +658,9 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
                             qv[e] = ok ? q : 0.f;
                             if (LOSS && ok && ((e & 1) ? fv1 : fv0)) {
                                 const float r = yv[e] * q;
-                                // a subnormal r is scaled by 2^24 first
-                                const bool sub = __float_as_uint(r) < 0x00800000u;
-                                const unsigned b = __float_as_uint(sub ? r * 16777216.f : r);
                                 lr1 += r - 1.f;
-                                le += (int)(b >> 23) - (sub ? 151 : 127);
-                                lm *= __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
-                                // r = 0 (log r = -inf): the loss is +inf;
-                                // r infinite or NaN: NaN
-                                if (b - 0x00800000u >= 0x7f000000u)
-                                    lacc += (b == 0u) ? __int_as_float(0x7f800000)
-                                                      : __int_as_float(0x7fc00000);
+                                ll2 += __log2f(r);
                             }
-                        }
-                        if (LOSS) {  // the mantissa product back to [1, 2)
-                            const unsigned b = __float_as_uint(lm);
-                            le += (int)(b >> 23) - 127;
-                            lm = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
                         }
                         stmatrix_x4_trans(PQ_s + (r8 + 8 * (mi >> 1)) * WLD + f0 + 8 * (mi & 1),
                                           pack_bf16(pv[0], pv[1]), pack_bf16(pv[2], pv[3]),
@@ -825,11 +810,7 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
         }
     }
     if (t.loss_slot) {
-        // e log 2 with log 2 split (Cody and Waite) into a leading part of 15
-        // significant bits (its product with e exact for |e| < 2^9) and the
-        // rest; FP32 only
-        const float e = (float)le;
-        lacc += (lr1 - e * 0.693145751953125f) - (logf(lm) + e * 1.428606765330187e-6f);
+        lacc += lr1 - ll2 * 0.6931471805599453f;
         float l = warp_sum(lacc);
         if (lane == 0) lw[warp] = l;
         __syncthreads();
