@@ -814,10 +814,10 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
         float l = warp_sum(lacc);
         if (lane == 0) lw[warp] = l;
         __syncthreads();
-        if (tid == 0) {
-            double dsum = 0.0;
-            for (int w = 0; w < kWarps; ++w) dsum += (double)lw[w];
-            *t.loss_slot = dsum;
+        if (tid == 0) {  // FP32 like the terms (no FP64 on the critical path)
+            float sum = 0.f;
+            for (int w = 0; w < kWarps; ++w) sum += lw[w];
+            *t.loss_slot = (double)sum;
         }
     }
     __syncthreads();
