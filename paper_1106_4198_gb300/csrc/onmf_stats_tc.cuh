@@ -355,9 +355,17 @@ static __device__ void column_step(const StepArgs &a, int S, double rho, float *
         const bool sc = a.normalize && sum > 0.f;
         const float inv = sc ? __frcp_rn(sum) : 1.f;
         const float invl = sc ? __fmul_rn(__fmaf_rn(-inv, sum, 1.f), inv) : 0.f;
-        // the double forms of 1/s and s only where A, B are doubles
+        // the double forms of 1/s and s only where A, B are doubles; one
+        // thread divides (a double division per thread costs a visible part
+        // of the pass at this GPU's FP64 rate) and shares the quotient
         const bool d64 = sc && accm == ACC_FP64;
-        const double invd = d64 ? 1.0 / (double)sum : 1.0;
+        double invd = 1.0;
+        if (d64) {
+            __shared__ double s_invd;
+            if (tid == 0) s_invd = 1.0 / (double)sum;
+            __syncthreads();
+            invd = s_invd;
+        }
         const double sd = d64 ? (double)sum : 1.0;
         bool bad = false;
 #pragma unroll
