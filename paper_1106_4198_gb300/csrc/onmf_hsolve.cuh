@@ -107,13 +107,16 @@ __device__ __forceinline__ void with_gamma_mode(float gamma, Fn &&f) {
 
 __device__ __forceinline__ bool bad_value(float v) { return !(v >= 0.f) || isinf(v); }
 
-// Sum of the K column sums of the normalized W (the denominator of h0).
+// Sum of the K column sums of the normalized W (the denominator of h0), by
+// warp 1: thread 0 may be busy issuing a bulk copy (and its proxy fence)
+// just before, and the two round trips to L2 then overlap.
 __device__ __forceinline__ float sum_w(const float *swpart, int K, float *s_tmp) {
-    if (threadIdx.x < 32) {
+    if (threadIdx.x >= 32 && threadIdx.x < 64) {
+        const int l = threadIdx.x - 32;
         float a = 0.f;
-        for (int k = threadIdx.x; k < K; k += 32) a += swpart[k];
+        for (int k = l; k < K; k += 32) a += swpart[k];
         a = warp_sum(a);
-        if (threadIdx.x == 0) *s_tmp = a;
+        if (l == 0) *s_tmp = a;
     }
     __syncthreads();
     float r = *s_tmp;
@@ -395,17 +398,24 @@ __host__ __device__ inline MixedLayout mixed_layout(const Shape &s) {
 
 // Issue the bulk copy of W^T (bf16 image) into shared memory; the h-solve
 // waits for it (mbarrier `bar`) after issuing its own frame-tile copy.
-__device__ __forceinline__ void issue_wimg(const Shape &s, const __nv_bfloat16 *Wimg,
-                                           unsigned char *smem, uint64_t *bar) {
+// issue_wimg_nosync: the same without the CTA barrier before it, for a caller
+// whose threads are already past their last use of that shared memory.
+__device__ __forceinline__ void issue_wimg_nosync(const Shape &s, const __nv_bfloat16 *Wimg,
+                                                  unsigned char *smem, uint64_t *bar) {
     const MixedLayout L = mixed_layout(s);
     const unsigned bytes = (unsigned)((size_t)s.Kp * s.WLD * 2);
-    __syncthreads();
     if (threadIdx.x == 0) {
         asm volatile("fence.proxy.async.global;\n" ::: "memory");
         fence_proxy_async_shared();
         mbar_arrive_expect_tx(bar, bytes);
         bulk_g2s(smem + L.w, Wimg, bytes, bar);
     }
+}
+
+__device__ __forceinline__ void issue_wimg(const Shape &s, const __nv_bfloat16 *Wimg,
+                                           unsigned char *smem, uint64_t *bar) {
+    __syncthreads();
+    issue_wimg_nosync(s, Wimg, smem, bar);
 }
 
 // The frames of a tile of the mma h-solve into shared memory (bulk copy

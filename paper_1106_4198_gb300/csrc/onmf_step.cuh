@@ -621,14 +621,36 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
         unsigned *rcnt = a.bar + 4;
         // ---- phase 1: h-solve of every tile
         if ((int)blockIdx.x < ntiles) {
-            // the W^T image copy first: its flight overlaps the read of the
-            // column sums below
             WStage ws{&mbar[0], &wpar, false};
+            float sw;
             if (PREC == PREC_MIXED) {
-                issue_wimg(s, a.Wimg, smem, &mbar[0]);
+                // the loads of the column sums (warp 1) go out before the
+                // W^T image copy (thread 0), with no CTA barrier between
+                // (the grid barrier that ended the last minibatch, or the
+                // kernel's start, leaves the CTA synchronized and the image's
+                // shared memory unused), so that they do not queue behind
+                // the image copies of every CTA; added as sum_w adds them
+                float swr[4] = {0.f, 0.f, 0.f, 0.f};  // K <= 128 on this path
+                if ((threadIdx.x >> 5) == 1)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int k = (int)(threadIdx.x & 31) + 32 * i;
+                        if (k < s.K) swr[i] = a.swpart[k];
+                    }
+                issue_wimg_nosync(s, a.Wimg, smem, &mbar[0]);
                 ws.pending = true;
+                if ((threadIdx.x >> 5) == 1) {
+                    float v = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) v += swr[i];
+                    v = warp_sum(v);
+                    if ((threadIdx.x & 31) == 0) s_tmp = v;
+                }
+                __syncthreads();
+                sw = s_tmp;
+            } else {
+                sw = sum_w(a.swpart, s.K, &s_tmp);
             }
-            const float sw = sum_w(a.swpart, s.K, &s_tmp);
             if (PREC == PREC_TC) stage_w_tc(s, tc_layout(s), a.Wimg, a.Wrow, a.Wcm, tbase, smem);
             for (int tile = blockIdx.x; tile < ntiles; tile += G) {
                 TileJob t;
