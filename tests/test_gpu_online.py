@@ -201,12 +201,18 @@ def test_checkpoint_resume_bitwise():
     assert ls2 == full["loss_sum"]
 
 
-def test_invalid_frames_are_reported_and_sticky():
+@pytest.mark.parametrize("precision", [FP32, MIXED])
+def test_invalid_frames_are_reported_and_sticky(precision):
+    """A NaN or a negative frame value: ONMF_ENUMERIC at the next sync, then
+    ONMF_ESTATE until the state is set again. On the mixed path the check
+    runs while the frames are staged, inside the previous minibatch's grid
+    barrier window; the CTA that saw it carries the error to its next grid
+    barrier, where every CTA leaves the kernel."""
     F, K, beta = 33, 4, 16
     V, W0 = problem(F, K, 48)
     V = V.copy()
     V[20, 5] = np.nan
-    m = onmf.OnlineISNMF(F, K, W0, beta=beta, n_inner=3)
+    m = onmf.OnlineISNMF(F, K, W0, beta=beta, n_inner=3, precision=precision)
     m.push(cuda(V))
     with pytest.raises(onmf.OnmfError) as e:
         m.sync()
@@ -221,7 +227,7 @@ def test_invalid_frames_are_reported_and_sticky():
     m.sync()
     m.close()
     V[20, 5] = -1.0
-    m = onmf.OnlineISNMF(F, K, W0, beta=beta, n_inner=3)
+    m = onmf.OnlineISNMF(F, K, W0, beta=beta, n_inner=3, precision=precision)
     m.push(cuda(V))
     with pytest.raises(onmf.OnmfError):
         m.sync()
