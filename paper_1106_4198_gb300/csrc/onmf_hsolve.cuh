@@ -421,51 +421,67 @@ __device__ __forceinline__ void issue_wimg(const Shape &s, const __nv_bfloat16 *
 // The frames of a tile of the mma h-solve into shared memory (bulk copy
 // when contiguous and aligned, possibly issued already: TileJob::v_staged),
 // then each frame's sum_f y_f (the start point's numerator), the input check
-// and the f-major copy y = eps + v. It needs V alone, so the online step
-// runs it for a CTA's next tile while the CTA waits at a grid barrier
-// (TileJob::v_ready then skips it in the h-solve).
-static __device__ void mixed_stage_frames(const Shape &s, float eps, const TileJob &t,
-                                          unsigned char *smem, uint64_t *vbar,
-                                          unsigned &vparity, int *err) {
+// and the f-major copy y = eps + v. It needs V alone, so the online step runs
+// it for a CTA's next tile while the CTA waits at a grid barrier, or inside
+// its statistics unit while warp 0 issues the MMAs (TileJob::v_ready then
+// skips it in the h-solve).
+//
+// stage_frames_core is the staging proper, run by warps 1-7 alone (named
+// barrier 1): the frame sums come from one fixed partition of those 224
+// threads wherever the staging runs, so every caller forms the same bits.
+// The caller keeps the bulk-copy parity (it flips it in every thread).
+constexpr int kStageThreads = kThreads - 32;
+
+__device__ __forceinline__ void stage_bar() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kStageThreads) : "memory");
+}
+
+#ifdef ONMF_PHASE_STAMPS
+#define ONMF_SSTAMP(t, i)                                       \
+    do {                                                        \
+        if ((t).hst && threadIdx.x == 32) (t).hst[(i)] = clock64(); \
+    } while (0)
+#else
+#define ONMF_SSTAMP(t, i) \
+    do {                  \
+    } while (0)
+#endif
+
+static __device__ __forceinline__ void stage_frames_core(const Shape &s, float eps, const TileJob &t,
+                                         unsigned char *smem, uint64_t *vbar, unsigned vparity,
+                                         int *err) {
     const int F = s.F, Fp = s.Fp16;
     const MixedLayout L = mixed_layout(s);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int u = threadIdx.x - 32, lane = threadIdx.x & 31, w = (threadIdx.x >> 5) - 1;
     float *y_raw = reinterpret_cast<float *>(smem + L.yraw);
     float *yT = reinterpret_cast<float *>(smem + L.yt);
     float *sy = reinterpret_cast<float *>(smem + L.misc);
-    ONMF_HSTAMP(t, 18);
+    ONMF_SSTAMP(t, 18);
     // ---- frame tile -> shared memory (bulk copy when contiguous and aligned;
-    //      possibly issued already by the previous tile)
-    {
-        const size_t bytes = (size_t)t.nvalid * F * 4;
-        const bool bulk = tile_bulk(t.Vt, t.ldv, F, t.nvalid);
-        __syncthreads();
-        if (bulk) {
-            if (tid == 0 && !t.v_staged) {
-                fence_proxy_async_shared();
-                mbar_arrive_expect_tx(vbar, (unsigned)bytes);
-                bulk_g2s(y_raw, t.Vt, (unsigned)bytes, vbar);
-            }
-        } else {
-            for (int i = tid; i < t.nvalid * F; i += kThreads) {
-                int j = i / F, f = i - j * F;
-                y_raw[i] = __ldg(t.Vt + (long long)j * t.ldv + f);
-            }
+    //      possibly issued already)
+    if (tile_bulk(t.Vt, t.ldv, F, t.nvalid)) {
+        if (u == 0 && !t.v_staged) {
+            fence_proxy_async_shared();
+            mbar_arrive_expect_tx(vbar, (unsigned)((size_t)t.nvalid * F * 4));
+            bulk_g2s(y_raw, t.Vt, (unsigned)((size_t)t.nvalid * F * 4), vbar);
         }
-        if (bulk) {
-            mbar_wait_bounded(vbar, vparity, err);
-            vparity ^= 1u;
+        mbar_wait_bounded(vbar, vparity, err);
+    } else {
+        for (int i = u; i < t.nvalid * F; i += kStageThreads) {
+            int j = i / F, f = i - j * F;
+            y_raw[i] = __ldg(t.Vt + (long long)j * t.ldv + f);
         }
-        __syncthreads();
+        stage_bar();
     }
-    ONMF_HSTAMP(t, 19);
+    ONMF_SSTAMP(t, 19);
     // f-major copy y = eps + v, input check and frame sums in one pass:
-    // thread tid always has frame j = tid & 7 (entry f * 8 + j of yT), so it
-    // adds its own entries of frame j; the 32 threads of each frame then
-    // combine theirs (lanes j, j+8, j+16, j+24, then the eight warps in order)
+    // thread u always has frame j = u & 7 (entry f * 8 + j of yT), so it adds
+    // its own entries of frame j; the threads of each frame then combine
+    // theirs (lanes j, j+8, j+16, j+24, then the seven warps in order)
     {
         constexpr int U = 6;  // independent loads in flight per thread
-        const int j = tid & 7;
+        constexpr int FS = kStageThreads / 8;  // frequencies per pass
+        const int j = u & 7;
         const bool jv = j < t.nvalid;
         const float *src = y_raw + j * F;
         float a = 0.f;
@@ -473,21 +489,21 @@ static __device__ void mixed_stage_frames(const Shape &s, float eps, const TileJ
         // valid (finite, not negative, not NaN) iff its bits are below those
         // of +inf, so the largest bits seen decide (one max per entry)
         unsigned mx = 0u;
-        for (int f0 = tid >> 3; f0 < Fp; f0 += 32 * U) {
+        for (int f0 = u >> 3; f0 < Fp; f0 += FS * U) {
             float v[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int f = f0 + 32 * u;
-                v[u] = (jv && f < F) ? src[f] : 0.f;
+            for (int q = 0; q < U; ++q) {
+                const int f = f0 + FS * q;
+                v[q] = (jv && f < F) ? src[f] : 0.f;
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int f = f0 + 32 * u;
+            for (int q = 0; q < U; ++q) {
+                const int f = f0 + FS * q;
                 if (f < Fp) {
                     const bool in = jv && f < F;
-                    const unsigned b = __float_as_uint(v[u]);
+                    const unsigned b = __float_as_uint(v[q]);
                     mx = max(mx, b == 0x80000000u ? 0u : b);
-                    const float y = eps + v[u];
+                    const float y = eps + v[q];
                     if (in) a += y;
                     yT[f * 8 + j] = in ? y : 1.f;
                 }
@@ -496,18 +512,28 @@ static __device__ void mixed_stage_frames(const Shape &s, float eps, const TileJ
         if (mx >= 0x7f800000u) flag_error(err, ERR_INPUT);
         a += __shfl_xor_sync(0xffffffffu, a, 8);
         a += __shfl_xor_sync(0xffffffffu, a, 16);
-        if (lane < 8) sy[160 + warp * 8 + lane] = a;
-        __syncthreads();
-        ONMF_HSTAMP(t, 20);
-        if (tid < 8) {
+        if (lane < 8) sy[160 + w * 8 + lane] = a;
+        stage_bar();
+        ONMF_SSTAMP(t, 20);
+        if (u < 8) {
             float sum = 0.f;
-            for (int w = 0; w < kWarps; ++w) sum += sy[160 + w * 8 + tid];
+            for (int q = 0; q < kStageThreads / 32; ++q) sum += sy[160 + q * 8 + u];
             // placeholder frames (j >= nvalid): y = 1 at every f
-            sy[tid] = (tid < t.nvalid) ? sum : (float)F;
+            sy[u] = (u < t.nvalid) ? sum : (float)F;
         }
     }
+    ONMF_SSTAMP(t, 21);
+}
+
+// The staging by the whole CTA (warp 0 idles): every thread flips the
+// parity of the frame copy.
+static __device__ void mixed_stage_frames(const Shape &s, float eps, const TileJob &t,
+                                          unsigned char *smem, uint64_t *vbar,
+                                          unsigned &vparity, int *err) {
+    __syncthreads();  // the previous user of the frame buffers is done
+    if (threadIdx.x >= 32) stage_frames_core(s, eps, t, smem, vbar, vparity, err);
+    if (tile_bulk(t.Vt, t.ldv, s.F, t.nvalid)) vparity ^= 1u;
     __syncthreads();
-    ONMF_HSTAMP(t, 21);
 }
 
 // Pending bulk copy of W^T that a tile must wait for before its first use.

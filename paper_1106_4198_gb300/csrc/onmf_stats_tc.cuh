@@ -38,6 +38,7 @@
 #pragma once
 
 #include "onmf_device.cuh"
+#include "onmf_hsolve.cuh"
 #include "onmf_kernels.cuh"
 #include "onmf_tc.cuh"
 
@@ -57,6 +58,19 @@ struct StatsBars {
     unsigned pl[2], pm[2], pd;
 };
 
+// Frames of the CTA's next h-solve tile that warps 1-7 stage while a
+// statistics unit's thread 0 waits for its range and issues the MMAs (their
+// bulk copy already issued; the caller flips the copy's parity afterwards).
+struct StageJob {
+    const float *Vt;  // first frame of the tile; NULL: nothing to stage
+    long long ldv;
+    int nvalid;
+    long long *hst;  // phase-timing stamps of the staging, or NULL
+    float eps;
+    uint64_t *vbar;
+    unsigned vparity;
+};
+
 // One work unit of phase 2: 64-frequency tile t, frame range s (groups
 // [s*gps, ...)), in chunks of at most kStatsStageGroups groups through two
 // shared-memory stages: the bulk copy of chunk c+1 runs while the MMAs of
@@ -65,7 +79,7 @@ static __device__ void stats_unit_tc(int t, int s, int gps, int ng, long long G,
                                      const unsigned char *PQc, const unsigned char *Hc,
                                      float *part, int K, int Fp, unsigned char *smem,
                                      uint32_t tcol, StatsBars &sb, unsigned *rcnt, int *err,
-                                     long long *ust) {
+                                     long long *ust, const Shape &sh, const StageJob job) {
     // ust: 8 clock64 slots of this unit (phase-timing builds), else NULL
 #ifdef ONMF_PHASE_STAMPS
 #define ONMF_USTAMP(i)                                     \
@@ -146,6 +160,15 @@ static __device__ void stats_unit_tc(int t, int s, int gps, int ng, long long G,
         }
         ONMF_USTAMP(2);
         tc_commit(sb.done);  // arrives once every MMA above is done
+    } else if (job.Vt && tid >= 32) {
+        // the frame buffers lie past the stages and the accumulator tile
+        TileJob tn;
+        tn.Vt = job.Vt;
+        tn.ldv = job.ldv;
+        tn.nvalid = job.nvalid;
+        tn.v_staged = 1;
+        tn.hst = job.hst;
+        stage_frames_core(sh, job.eps, tn, smem, job.vbar, job.vparity, err);
     }
     const bool ok = mbar_wait_bounded(sb.done, sb.pd, err);
     sb.pd ^= 1u;

@@ -710,13 +710,38 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
             // ---- phase 2: [P H^T | Q H^T] partial sums on the tensor cores,
             // each unit as soon as the h-solves of its frame range are done
             const int ng = (nb + 7) / 8;
-            for (int u = blockIdx.x; u < FT64 * sp.S; u += G)
+            // the next tile's frames, on their way since the h-solve ended,
+            // are staged by warps 1-7 during the CTA's first unit (the
+            // window before the column pass then has nothing left to do)
+            StageJob job{nullptr, 0, 0, nullptr, a.eps, &mbar[1], vpar};
+            const bool stage_in_unit = early_v && v_prefetched && (int)blockIdx.x < FT64 * sp.S;
+            if (stage_in_unit) {
+                const int nbn = (m + 1 == a.nmb - 1) ? a.nb_last : a.beta;  // as first_tile
+                job.Vt = a.V + ((long long)(m + 1) * a.beta + (long long)blockIdx.x * TILE) * a.ldv;
+                job.ldv = a.ldv;
+                job.nvalid = min(TILE, nbn - (int)blockIdx.x * TILE);
+#ifdef ONMF_PHASE_STAMPS
+                if (a.stamps && m < kStampMb)  // points 34-37 of this minibatch
+                    job.hst = a.stamps + ((long long)m * G + blockIdx.x) * kStampPts + 16;
+#endif
+            }
+            for (int u = blockIdx.x; u < FT64 * sp.S; u += G) {
                 stats_unit_tc(u % FT64, u / FT64, sp.gps, ng, a.betap / 8,
                               reinterpret_cast<const unsigned char *>(a.Pg),
                               reinterpret_cast<const unsigned char *>(a.Hg), a.part, s.K, s.Fp16,
                               smem, tbase, sb, rcnt, a.err,
                               a.stamps ? a.stamps + ((long long)m * G + blockIdx.x) * kStampPts + 8
-                                       : nullptr);
+                                       : nullptr,
+                              s, job);
+                job.Vt = nullptr;
+            }
+            if (stage_in_unit) {
+                if (tile_bulk(a.V + ((long long)(m + 1) * a.beta + (long long)blockIdx.x * TILE) * a.ldv,
+                              a.ldv, s.F, job.nvalid))
+                    vpar ^= 1u;
+                v_prefetched = false;
+                v_ready = true;
+            }
             ONMF_STAMP(a.stamps, m, 3);
             // the frames of this CTA's first tile of the next minibatch (if
             // not on their way yet: phase 3 uses no dynamic shared memory);
