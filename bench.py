@@ -1013,7 +1013,10 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic gamma-model spectrogram (host)",
         "config": {"workload": workload(getattr(args, "frames_per_step", 1_000_000)),
-                   "F": F, "K": K, "beta": BETA, "n_inner": N_IN},
+                   "F": F, "K": K, "beta": BETA, "n_inner": N_IN,
+                   "frames_per_step": getattr(args, "frames_per_step", 1_000_000),
+                   "global_batch": getattr(args, "frames_per_step", 1_000_000),
+                   "parallelism": "single"},
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": threads,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
