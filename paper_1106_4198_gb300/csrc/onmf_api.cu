@@ -296,8 +296,9 @@ onmf_status onmf_init(const onmf_config *cfg, const float *W0, int32_t W0_on_dev
         snprintf(g_msg, sizeof g_msg, "h-solve %d does not support F=%d K=%d", c.hsolve, c.F, c.K);
         return ONMF_EINVAL;
     }
-    if ((c.h_penalty > 0.0 || c.w_penalty > 0.0) && prec != PREC_FP32 && prec != PREC_MIXED) {
-        snprintf(g_msg, sizeof g_msg, "penalties run on the FP32 and mma paths");
+    if ((c.h_penalty > 0.0 || c.w_penalty > 0.0) && prec != PREC_FP32 && prec != PREC_MIXED &&
+        prec != PREC_CL) {
+        snprintf(g_msg, sizeof g_msg, "penalties run on the FP32, mma and cluster paths");
         return ONMF_EINVAL;
     }
     onmf_status st = ensure_configured();

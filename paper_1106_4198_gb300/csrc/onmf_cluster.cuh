@@ -326,6 +326,22 @@ static __device__ void hsolve_tile_cluster(const Shape &s, const ClLayout &L, in
         cluster_sync();
         // ---- owners: sum the partials in rank order, update h, broadcast bf16 h
         {
+            // the h penalty lambda psi(s~), psi = log(a + s) (Section 2.2,
+            // "Extensions"): its tangent at the current h adds
+            // lambda / (a + s~) to the denominator, s~ = sum_k h_k of the
+            // frame before the step (warp w: owned frames w, w + 8, ...;
+            // lanes over k, then a warp sum)
+            __shared__ float s_hpen[kClTile];
+            const bool hp = t.hpen > 0.f;
+            if (hp) {
+                for (int jl = warp; jl < OF; jl += kWarps) {
+                    float v = 0.f;
+                    for (int k = lane; k < Kp; k += 32) v += hM[k * OF + jl];
+                    v = warp_sum(v);
+                    if (lane == 0) s_hpen[jl] = __fdiv_rn(t.hpen, t.hpen_a + v);
+                }
+                __syncthreads();
+            }
             // thread: one k, 4 consecutive owned frames (OF >= 4)
             const int lg4 = lgOF - 2;
             for (int item = tid; item < (Kp << lg4); item += kThreads) {
@@ -337,6 +353,12 @@ static __device__ void hsolve_tile_cluster(const Shape &s, const ClLayout &L, in
                         *reinterpret_cast<const float4 *>(recv + ((r * 2 + 1) * Kp + k) * OF + jl);
                     nm.x += a.x; nm.y += a.y; nm.z += a.z; nm.w += a.w;
                     dn.x += b.x; dn.y += b.y; dn.z += b.z; dn.w += b.w;
+                }
+                if (hp) {
+                    dn.x += s_hpen[jl];
+                    dn.y += s_hpen[jl + 1];
+                    dn.z += s_hpen[jl + 2];
+                    dn.w += s_hpen[jl + 3];
                 }
                 float4 h = *reinterpret_cast<const float4 *>(hM + k * OF + jl);
                 with_gamma_mode(gamma, [&](auto gm) {

@@ -58,6 +58,8 @@ __global__ void __launch_bounds__(kThreads, 1) online_cluster_kernel(StepArgs a,
                 t.H_out = Hm;
                 t.ldh = a.ldh;
                 t.n_in = a.n_in;
+                t.hpen = a.hpen;
+                t.hpen_a = a.hpen_a;
                 t.loss_first = 0;
                 t.final_pass = 1;
                 t.loss_slot = a.loss_part + (long long)tile * C + rank;
@@ -73,7 +75,9 @@ __global__ void __launch_bounds__(kThreads, 1) online_cluster_kernel(StepArgs a,
         for (int u = blockIdx.x; u < nunits; u += G) {
             const int mt = u % FT, ks = u / FT;
             stats_unit<PREC_MIXED>(s, mt, ks, a.Pg, a.Qg, a.Hg, a.betap, 0, nb, smem, acc);
-            online_epilogue<PREC_MIXED>(a, mt, ks, rho, acc);
+            // the dictionary penalty's form: W' = sqrt(A/(B + mu)); mu = 0
+            // adds +0 to B, the same bits as the plain form
+            online_epilogue<PREC_MIXED, true>(a, mt, ks, rho, acc);
             __syncthreads();
         }
         if (!cl_grid_sync(a.bar, G, epoch, a.err, s_vote, vp, C, rank)) break;
@@ -117,6 +121,8 @@ __global__ void __launch_bounds__(kThreads, 1) tile_cluster_kernel(TileArgs a, i
             t.H_out = a.H_out;
             t.ldh = a.ldh;
             t.n_in = a.n_in;
+            t.hpen = a.hpen;
+            t.hpen_a = a.hpen_a;
             t.loss_first = a.loss_first;
             t.final_pass = a.final_pass;
             t.loss_slot = a.loss_part ? a.loss_part + tile * C + rank : nullptr;

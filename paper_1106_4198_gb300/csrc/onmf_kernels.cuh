@@ -86,7 +86,7 @@ struct StepArgs {
     int rho_on_new;
     int acc;  // arithmetic of A and B (ACC_*)
     int stats_ranges;  // frame ranges of the tcgen05 statistics (0: automatic)
-    float hpen, hpen_a, wpen;  // penalties (FP32 path): lambda, a, mu
+    float hpen, hpen_a, wpen;  // penalties (FP32, mma, cluster paths): lambda, a, mu
     // frames
     const float *V;
     long long ldv;
@@ -161,7 +161,7 @@ struct TileArgs {
     long long betap;
     double *loss_part;    // [tiles] or NULL
     int *err;
-    float hpen, hpen_a;   // h penalty lambda, a (FP32 path; lambda = 0: none)
+    float hpen, hpen_a;   // h penalty lambda, a (lambda = 0: none)
 };
 
 }  // namespace onmf

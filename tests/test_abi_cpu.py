@@ -67,12 +67,12 @@ def test_invalid_config_rejected_on_host(field, value):
     assert not h.value
 
 
-def test_penalties_rejected_off_the_fp32_and_mma_paths():
-    """The tcgen05 and cluster h-solves take no penalties; the host refuses
-    the combination before any device work."""
+def test_penalties_rejected_on_the_tcgen05_path():
+    """The tcgen05 h-solve takes no penalties (the FP32, mma and cluster
+    paths do); the host refuses the combination before any device work."""
     import numpy as np
     W0 = np.ones((8, 256), dtype=np.float32) / 256
-    for hs in (onmf.ONMF_HSOLVE_TC, onmf.ONMF_HSOLVE_CLUSTER):
+    for hs in (onmf.ONMF_HSOLVE_TC,):
         for kw in (dict(h_penalty=0.5), dict(w_penalty=0.5)):
             c = onmf.onmf_config_default(256, 8, precision=onmf.ONMF_MIXED, hsolve=hs, **kw)
             h = ctypes.c_void_p()

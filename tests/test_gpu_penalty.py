@@ -2,9 +2,11 @@
 against the FP64 oracle: the h penalty lambda * log(a + sum_k h_k) (tangent
 majorization in the h update) and the dictionary penalty mu * sum W
 (W = sqrt(A/(B + mu))). Element-wise (helpers.parity; rows of W, A, B
-including the last): FP32 path 1e-5 on W, A, B, H and the loss; the mma
-h-solve of the mixed path the one-minibatch bounds (test_gpu_online.MIXED_TOL)
-and 1e-3 on the loss. The unpenalized kernels are separate instantiations."""
+including the last): FP32 path 1e-5 on W, A, B, H and the loss; the mma and
+cluster h-solves of the mixed path the one-minibatch bounds
+(test_gpu_online.MIXED_TOL) and 1e-3 on the loss. The unpenalized mma kernels
+are separate instantiations; the cluster kernels take the penalty at run
+time (a zero penalty gives the plain kernel's bits)."""
 import numpy as np
 import pytest
 
@@ -89,3 +91,46 @@ def test_penalized_projection_mixed_mma():
     m.close()
     Ho, _ = oracle.project(V, W0, n_in=8, h_penalty=lam, h_penalty_a=a)
     parity("penalized projection mixed", dict(H=(H.cpu().numpy(), Ho)), MIXED_TOL["H"])
+
+
+@pytest.mark.parametrize("F,K,N,beta,n_in", [(129, 8, 512, 64, 5), (513, 100, 1000, 500, 6),
+                                             (257, 256, 256, 128, 4)])
+@pytest.mark.parametrize("lam,a,mu", [(0.5, 1.0, 0.0), (4.0, 0.3, 0.05)])
+def test_penalized_pass_mixed_cluster(F, K, N, beta, n_in, lam, a, mu):
+    """The cluster h-solve (the only one for K > 128): the h penalty in the
+    owners' update (frame sums over all k before the step), the dictionary
+    penalty in the statistics epilogue."""
+    V, W0 = problem(F, K, N, seed=61 + K)
+    pen = dict(h_penalty=lam, h_penalty_a=a, w_penalty=mu)
+    g = run_gpu(V, W0, beta=beta, n_inner=n_in, precision=onmf.ONMF_MIXED,
+                hsolve=onmf.ONMF_HSOLVE_CLUSTER, **pen)
+    o = oracle_pass(V, W0, beta, n_in, **pen)
+    compare(g, o, MIXED_TOL, label="penalized mixed cluster F=%d K=%d lam=%g a=%g mu=%g"
+            % (F, K, lam, a, mu))
+    ou = oracle_pass(V, W0, beta, n_in)
+    assert relerr(g["H"], o["H"]) < relerr(g["H"], ou["H"])
+
+
+def test_zero_penalty_cluster_is_the_plain_kernel():
+    """With lambda = mu = 0 the cluster kernels take their plain path: the
+    same bits as a run without penalties."""
+    V, W0 = problem(257, 160, 256, seed=67)
+    a = run_gpu(V, W0, beta=128, n_inner=4, precision=onmf.ONMF_MIXED,
+                hsolve=onmf.ONMF_HSOLVE_CLUSTER)
+    b = run_gpu(V, W0, beta=128, n_inner=4, precision=onmf.ONMF_MIXED,
+                hsolve=onmf.ONMF_HSOLVE_CLUSTER, h_penalty=0.0, w_penalty=0.0)
+    assert np.array_equal(a["W"], b["W"]) and np.array_equal(a["H"], b["H"])
+
+
+def test_penalized_projection_mixed_cluster():
+    import torch
+    F, K, N = 257, 160, 300
+    V, W0 = problem(F, K, N, seed=69)
+    lam, a = 2.0, 0.5
+    m = onmf.OnlineISNMF(F, K, W0, precision=onmf.ONMF_MIXED, hsolve=onmf.ONMF_HSOLVE_CLUSTER,
+                         h_penalty=lam, h_penalty_a=a)
+    H = torch.empty((N, K), device="cuda")
+    m.project(cuda(V), H, n_inner=8)
+    m.close()
+    Ho, _ = oracle.project(V, W0, n_in=8, h_penalty=lam, h_penalty_a=a)
+    parity("penalized projection mixed cluster", dict(H=(H.cpu().numpy(), Ho)), MIXED_TOL["H"])
