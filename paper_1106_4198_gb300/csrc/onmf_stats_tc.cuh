@@ -235,19 +235,22 @@ constexpr int kColRows = kColPer * kThreads;  // 1024 >= F on the mixed path
 // arithmetic; `raw` is the stored 8 bytes (a double, a float, or a float
 // pair) and is replaced by the new stored form; returns the new value as a
 // float, the operand of W' = sqrt(A/B). rhof = (float)rho, converted once by
-// the caller: the FP32 modes do no FP64 arithmetic at all (the FP64 rate of
-// this GPU is a small fraction of its FP32 rate, so even per-thread
-// conversions and divisions in double show up in the column pass).
-__device__ __forceinline__ float ab_accumulate(int accm, double rho, float rhof, int rho_on_new,
-                                               float inc, double &raw) {
-    if (accm == ACC_FP64) {
+// the caller. The arithmetic is a template parameter: the FP32 modes then
+// hold no FP64 instruction at all (the FP64 rate of this GPU is a small
+// fraction of its FP32 rate, so even per-thread conversions and divisions in
+// double show up in the column pass, and so do FP64 instructions of an
+// untaken mode that the compiler predicates instead of branching around).
+template <int ACCM>
+__device__ __forceinline__ float ab_accumulate(double rho, float rhof, int rho_on_new, float inc,
+                                               double &raw) {
+    if constexpr (ACCM == ACC_FP64) {
         const double v = rho_on_new ? fma(rho, (double)inc, raw) : fma(rho, raw, (double)inc);
         raw = v;
         return (float)v;
     }
     DF x;
     memcpy(&x, &raw, 8);
-    if (accm == ACC_FP32) {
+    if constexpr (ACCM == ACC_FP32) {
         const float v = rho_on_new ? __fmaf_rn(rhof, inc, x.hi) : __fmaf_rn(rhof, x.hi, inc);
         x = {v, 0.f};
     } else {
@@ -260,12 +263,13 @@ __device__ __forceinline__ float ab_accumulate(int accm, double rho, float rhof,
 // The rescale of one stored entry: A / s (div) or B * s; FP64 sums use the
 // double reciprocal invd = 1/s and the double sd = s; the compensated pairs
 // multiply by the reciprocal pair (ih, il) of s.
-__device__ __forceinline__ double ab_rescale(int accm, double raw, float sum, double invd,
+template <int ACCM>
+__device__ __forceinline__ double ab_rescale(double raw, float sum, double invd,
                                              double sd, float ih, float il, bool div) {
-    if (accm == ACC_FP64) return div ? raw * invd : raw * sd;
+    if constexpr (ACCM == ACC_FP64) return div ? raw * invd : raw * sd;
     DF x;
     memcpy(&x, &raw, 8);
-    if (accm == ACC_FP32)
+    if constexpr (ACCM == ACC_FP32)
         x = {div ? __fdiv_rn(x.hi, sum) : __fmul_rn(x.hi, sum), 0.f};
     else
         x = div ? df_mul_pair(x, ih, il) : df_mul_add(x, sum, 0.f);
@@ -302,7 +306,8 @@ __device__ __forceinline__ void col_load(const StepArgs &a, int k, ColVals &v) {
 
 // WPEN: the dictionary penalty mu * sum W, W' = sqrt(A/(B + mu)).
 // pre: W, A, B of the CTA's first column (k = first), loaded by col_load.
-template <bool WPEN>
+// ACCM: the arithmetic of A and B (ACC_*), fixed at compile time.
+template <bool WPEN, int ACCM>
 static __device__ void column_step(const StepArgs &a, int S, double rho, float *red8, int first,
                                    int stride, const ColVals &pre, long long *cst = nullptr) {
     // cst: 5 clock64 slots of the first column (phase-timing builds), else NULL
@@ -319,7 +324,6 @@ static __device__ void column_step(const StepArgs &a, int S, double rho, float *
     const Shape &s = a.s;
     const int F = s.F, K = s.K, Fp = s.Fp16;
     const int tid = threadIdx.x;
-    const int accm = a.acc;
     const float rhof = (float)rho;
     const long long step = (long long)K * Fp;  // floats between P (or Q) partials of two ranges
     for (int k = first; k < K; k += stride) {
@@ -365,8 +369,8 @@ static __device__ void column_step(const StepArgs &a, int S, double rho, float *
             if (f < F) {
                 const float w = v.w[u];
                 const float An =
-                    ab_accumulate(accm, rho, rhof, a.rho_on_new, ph[u] * w * w, v.A[u]);
-                const float Bn = ab_accumulate(accm, rho, rhof, a.rho_on_new, qh[u], v.B[u]);
+                    ab_accumulate<ACCM>(rho, rhof, a.rho_on_new, ph[u] * w * w, v.A[u]);
+                const float Bn = ab_accumulate<ACCM>(rho, rhof, a.rho_on_new, qh[u], v.B[u]);
                 const float Bd = WPEN ? Bn + a.wpen : Bn;
                 wn[u] = (Bd > 0.f) ? sqrtf(__fdiv_rn(An, Bd)) : w;
                 part_sum += wn[u];
@@ -381,7 +385,7 @@ static __device__ void column_step(const StepArgs &a, int S, double rho, float *
         // the double forms of 1/s and s only where A, B are doubles; one
         // thread divides (a double division per thread costs a visible part
         // of the pass at this GPU's FP64 rate) and shares the quotient
-        const bool d64 = sc && accm == ACC_FP64;
+        const bool d64 = sc && ACCM == ACC_FP64;
         double invd = 1.0;
         if (d64) {
             __shared__ double s_invd;
@@ -399,8 +403,8 @@ static __device__ void column_step(const StepArgs &a, int S, double rho, float *
                 const float wv = wn[u] * inv;
                 bad |= !isfinite(wv);
                 a.Wcm[i] = wv;
-                a.A[i] = sc ? ab_rescale(accm, v.A[u], sum, invd, sd, inv, invl, true) : v.A[u];
-                a.B[i] = sc ? ab_rescale(accm, v.B[u], sum, invd, sd, inv, invl, false) : v.B[u];
+                a.A[i] = sc ? ab_rescale<ACCM>(v.A[u], sum, invd, sd, inv, invl, true) : v.A[u];
+                a.B[i] = sc ? ab_rescale<ACCM>(v.B[u], sum, invd, sd, inv, invl, false) : v.B[u];
                 a.Wimg[(long long)k * s.WLD + f] = __float2bfloat16_rn(wv);
             }
         }

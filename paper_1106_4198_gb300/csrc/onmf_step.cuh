@@ -767,10 +767,18 @@ __global__ void __launch_bounds__(kThreads, 1) online_kernel(StepArgs a) {
             if (!grid_wait(a.bar, G, epoch, a.err)) break;
             ONMF_STAMP(a.stamps, m, 4);
             // ---- phase 3: partial sums, A, B, W' = sqrt(A/B), rescale, image
-            column_step<PEN>(a, sp.S, rho, s_red8, blockIdx.x, gridDim.x, pre,
-                             a.stamps && m < kStampMb
-                                 ? a.stamps + ((long long)m * G + blockIdx.x) * kStampPts + 40
-                                 : nullptr);
+            {
+                long long *cst = a.stamps && m < kStampMb
+                                     ? a.stamps + ((long long)m * G + blockIdx.x) * kStampPts + 40
+                                     : nullptr;
+                if (a.acc == ACC_FP64)
+                    column_step<PEN, ACC_FP64>(a, sp.S, rho, s_red8, blockIdx.x, gridDim.x, pre, cst);
+                else if (a.acc == ACC_FP32)
+                    column_step<PEN, ACC_FP32>(a, sp.S, rho, s_red8, blockIdx.x, gridDim.x, pre, cst);
+                else
+                    column_step<PEN, ACC_FP32C>(a, sp.S, rho, s_red8, blockIdx.x, gridDim.x, pre,
+                                                cst);
+            }
             // the range counters start from zero in the next minibatch (every
             // reader of them passed the barrier above; the next barrier
             // orders these stores before the next increments)
