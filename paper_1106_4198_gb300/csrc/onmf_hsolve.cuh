@@ -725,17 +725,28 @@ static __device__ void hsolve_tile_mixed(const Shape &s, float eps, float gamma,
                 for (int e = 0; e < 4; ++e) c0[u][e] = c1[u][e] = 0.f;
             const __nv_bfloat16 *arow = PQ_s + (r8 + 8 * (mi & 1)) * WLD + 8 * (mi >> 1);
             const __nv_bfloat16 *brow = W_s + (16 * warp + r8 + 8 * (mi >> 1)) * WLD + 8 * (mi & 1);
-            for (int fs = 0; fs < FT; fs += 4) {
+            // a single k16 step left over by the groups of four (F = 16n + 1,
+            // e.g. 513: the step of f = 512 alone) goes first, into the first
+            // accumulator pair, rather than as a ninth group of its own at the end
+            const int FTg = (FT & 3) == 1 ? FT - 1 : FT;
+            if (FTg != FT) {
+                uint32_t a[4], b[4];
+                ldmatrix_x4(a, arow + 16 * FTg);
+                ldmatrix_x4(b, brow + 16 * FTg);
+                mma_bf16_16816(c0[0], a, b[0], b[1]);
+                mma_bf16_16816(c1[0], a, b[2], b[3]);
+            }
+            for (int fs = 0; fs < FTg; fs += 4) {
                 uint32_t a[4][4], b[4][4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    if (fs + u < FT) {
+                    if (fs + u < FTg) {
                         ldmatrix_x4(a[u], arow + 16 * (fs + u));
                         ldmatrix_x4(b[u], brow + 16 * (fs + u));
                     }
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    if (fs + u < FT) {
+                    if (fs + u < FTg) {
                         mma_bf16_16816(c0[u], a[u], b[u][0], b[u][1]);
                         mma_bf16_16816(c1[u], a[u], b[u][2], b[u][3]);
                     }
